@@ -1,0 +1,462 @@
+#!/usr/bin/env python
+"""Benchmark of the batched MD5 / SHA-1 / SM3 hot path on B300.
+
+Default workload (the configuration the headline metric is quoted on): a
+plain fixed-length batch of 2^22 messages x 55 bytes (one 64-byte block
+after padding), uniform random bytes, packed back to back with uint64
+offsets and uint32 lengths, 32-byte digest slots.  One step hashes the batch
+with each of MD5, SHA-1 and SM3 (three launches).  Inputs (220 MiB + 48 MiB
+of metadata) are larger than the 126 MB L2, so no flush is needed between
+steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W]
+                    [--workload c2|c4|c3|c1] [--impl ours|reference]
+
+Multi-GPU: one process per GPU (torchrun); each rank hashes its own disjoint
+shard (the same shape, its own seed) with no collective on the data path;
+only a barrier and a max-over-ranks of the timed region use torch.distributed
+(weak scaling).  `--impl reference` times the CPU oracle (plain C, RFC 1321 /
+FIPS 180-4 / GB/T 32905) on a bounded sample of the same workload; it runs on
+rank 0 only.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2407_09333_b300 import workloads  # noqa: E402
+
+METRIC = "hashed GB/s and Mhash/s per alg (plain vs ragged batch); serve p50/p99 latency"
+ALG_NAMES = ("md5", "sha1", "sm3")
+
+# Algorithmic 32-bit operations per 64-byte block (3-input ALU ops: LOP3 for
+# each Boolean function or 3-way XOR, IADD3 for up to three addends, SHF for
+# each rotation, PRMT for each byte swap), counted from the definitions:
+#   MD5   64 steps x (1 g + 2 add + 1 rot + 1 add) + 4 chaining adds  = 324
+#   SHA-1 80 rounds x 5 + 64 schedule words x 3 + 5 adds + 16 swaps  = 613
+#   SM3   64 rounds x 16 + 52 expanded words x 7 + 8 xors + 16 swaps = 1412
+OPS_PER_BLOCK = {0: 324, 1: 613, 2: 1412}
+
+
+def padded_blocks(lengths: np.ndarray) -> np.ndarray:
+    return (lengths.astype(np.uint64) + np.uint64(72)) >> np.uint64(6)
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured", "sm_max_mhz": float(d.get("sm_max_mhz", 2032.0))}
+    except Exception:
+        return {"hbm_gbs": 6400.0, "source": "fallback", "sm_max_mhz": 2032.0}
+
+
+def alu_peak_tops(sms: int, sm_mhz: float, lanes_per_sm: int = 128) -> float:
+    """32-bit integer issue peak: SMs x 4 sub-partitions x 32 lanes x clock."""
+    return sms * lanes_per_sm * sm_mhz * 1e6 / 1e12
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region (NVML reads only; no setting is changed)
+
+class ClockSampler:
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown",
+               0x2: "applications_clocks_setting", 0x1: "gpu_idle"}
+
+    def __init__(self, device_index: int, period_s: float = 0.005):
+        self.period = period_s
+        self.samples = []
+        self.reasons = 0
+        self.max_mhz = None
+        self._stop = threading.Event()
+        self._thread = None
+        try:
+            import pynvml
+            pynvml.nvmlInit()
+            self._nvml = pynvml
+            self._h = pynvml.nvmlDeviceGetHandleByIndex(device_index)
+            self.max_mhz = pynvml.nvmlDeviceGetMaxClockInfo(self._h, pynvml.NVML_CLOCK_SM)
+        except Exception:
+            self._nvml = None
+
+    def _run(self):
+        nv = self._nvml
+        while not self._stop.is_set():
+            try:
+                self.samples.append(nv.nvmlDeviceGetClockInfo(self._h, nv.NVML_CLOCK_SM))
+                self.reasons |= nv.nvmlDeviceGetCurrentClocksEventReasons(self._h)
+            except Exception:
+                pass
+            time.sleep(self.period)
+
+    def __enter__(self):
+        if self._nvml is not None:
+            self._thread = threading.Thread(target=self._run, daemon=True)
+            self._thread.start()
+        return self
+
+    def __exit__(self, *exc):
+        self._stop.set()
+        if self._thread:
+            self._thread.join()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": [], "samples": 0}
+        reasons = [name for bit, name in self.REASONS.items() if self.reasons & bit and bit != 0x1]
+        return {"sm_mhz": float(statistics.median(self.samples)), "sm_max_mhz": self.max_mhz,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (barrier + max over ranks only)
+
+class Dist:
+    def __init__(self, want_gpus: int):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch
+            import torch.distributed as dist
+            backend = "nccl" if torch.cuda.is_available() else "gloo"
+            os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+            dist.init_process_group(backend=backend)
+            self.pg = dist
+        self.want = want_gpus
+
+    def barrier(self):
+        if self.pg:
+            if self.pg.get_backend() == "nccl":
+                import torch
+                self.pg.barrier(device_ids=[torch.cuda.current_device()])
+            else:
+                self.pg.barrier()
+
+    def max(self, value: float) -> float:
+        if not self.pg:
+            return value
+        import torch
+        dev = "cuda" if self.pg.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([value], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+def shard_seed(base: int, rank: int) -> int:
+    """Each rank hashes its own disjoint synthetic shard."""
+    return base + 1000 * rank
+
+
+# ---------------------------------------------------------------------------
+# workloads
+
+def make_workload(name: str, rank: int):
+    if name == "c1":
+        return ("plain fixed-length batch: 4096 messages x 64 B, MD5+SHA-1+SM3 per step",
+                workloads.fixed(4096, 64, shard_seed(0, rank)), False)
+    if name == "c2":
+        return ("plain fixed-length batch: 2^22 messages x 55 B (one block each), "
+                "MD5+SHA-1+SM3 per step", workloads.fixed(1 << 22, 55, shard_seed(1, rank)), False)
+    if name == "c4":
+        return ("long-message batch: 65536 messages x 16 KiB, MD5+SHA-1+SM3 per step",
+                workloads.fixed(65536, 16384, shard_seed(3, rank)), False)
+    if name == "c3":
+        return ("ragged mixed-algorithm batch: 2^20 messages, log-uniform lengths in [0, 64 KiB], "
+                "1% at padding boundaries, algorithm per message", workloads.ragged(1 << 20, shard_seed(2, rank)), True)
+    raise SystemExit("unknown workload %r" % name)
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (bounded samples)
+
+def oracle_sample(batch, mixed: bool, max_msgs: int):
+    n = min(batch.n, max_msgs)
+    sub = workloads.Batch(batch.packed, batch.offsets[:n], batch.lengths[:n],
+                          batch.algs[:n] if batch.algs is not None else None)
+    return sub
+
+
+def time_oracle(sub, mixed: bool, threads: int):
+    import oracle
+    t0 = time.perf_counter()
+    if mixed:
+        oracle.hash_batch(None, sub.packed, sub.offsets, sub.lengths, algs=sub.algs, threads=threads)
+        nbytes, nmsgs = sub.total_bytes, sub.n
+    else:
+        for alg in (0, 1, 2):
+            oracle.hash_batch(alg, sub.packed, sub.offsets, sub.lengths, threads=threads)
+        nbytes, nmsgs = 3 * sub.total_bytes, 3 * sub.n
+    return time.perf_counter() - t0, nbytes, nmsgs
+
+
+def cpu_baseline(batch, mixed: bool, target_s: float = 10.0, cap_s: float = 30.0):
+    import oracle
+    threads = oracle.host_threads()
+    sub = oracle_sample(batch, mixed, 1 << 18)
+    dt, nbytes, nmsgs = time_oracle(sub, mixed, threads)
+    passes, tot_t, tot_b, tot_m = 1, dt, nbytes, nmsgs
+    while tot_t < target_s and tot_t + dt < cap_s:
+        dt, nbytes, nmsgs = time_oracle(sub, mixed, threads)
+        passes += 1
+        tot_t += dt
+        tot_b += nbytes
+        tot_m += nmsgs
+    return {"value": tot_b / tot_t / 1e9, "unit": "GB/s", "cores": threads, "kind": "oracle",
+            "mhash_per_s": tot_m / tot_t / 1e6,
+            "sample": "first %d messages of the workload (%s), %d pass(es), %.1f s"
+                      % (sub.n, "per-message algorithm" if mixed else "each of MD5, SHA-1, SM3",
+                         passes, tot_t)}
+
+
+def run_reference(args, dist):
+    if dist.rank != 0:
+        return
+    desc, batch, mixed = make_workload(args.workload, 0)
+    import oracle
+    threads = oracle.host_threads()
+    sub = oracle_sample(batch, mixed, 1 << 18 if args.workload != "c4" else 1 << 10)
+    for _ in range(args.warmup):
+        time_oracle(sub, mixed, threads)
+    tot_t = tot_b = tot_m = 0
+    for _ in range(args.steps):
+        dt, nb, nm = time_oracle(sub, mixed, threads)
+        tot_t += dt
+        tot_b += nb
+        tot_m += nm
+    value = tot_b / tot_t / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s",
+        "n_gpus": dist.world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * tot_t / max(args.steps, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": desc, "sample_messages": sub.n},
+        "mhash_per_s": tot_m / tot_t / 1e6,
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": threads, "kind": "oracle",
+                         "sample": "first %d messages of the workload per step" % sub.n},
+        "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# the CUDA path
+
+def traffic_for(kernel_key: str):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel
+    sources have not changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        d = json.load(open(path))
+    except Exception:
+        return None
+    ent = d.get(kernel_key)
+    if not ent or ent.get("source_hash") != kernel_source_hash():
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2407_09333_b300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(f.encode())
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def run_ours(args, dist):
+    import torch
+    from paper_2407_09333_b300 import api, build
+
+    if torch.cuda.is_available():
+        torch.cuda.set_device(dist.local_rank)
+    build.build()
+    api.lib()
+    desc, batch, mixed = make_workload(args.workload, dist.rank)
+    packed, off, ln, algs = api.to_device(batch)
+    n = batch.n
+    out = torch.empty((n, 32), dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    nblocks = padded_blocks(batch.lengths)
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    sms = props.multi_processor_count
+
+    if mixed:
+        launches = [(None, lambda: api.hash_batch_mixed(algs, packed, off, ln, out=out))]
+        bytes_per_step = batch.total_bytes
+        msgs_per_step = n
+    else:
+        launches = [(a, (lambda a=a: api.hash_batch(a, packed, off, ln, out=out))) for a in (0, 1, 2)]
+        bytes_per_step = 3 * batch.total_bytes
+        msgs_per_step = 3 * n
+
+    for _ in range(args.warmup):
+        for _, fn in launches:
+            fn()
+    torch.cuda.synchronize()
+
+    nl = len(launches)
+    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(nl)] for _ in range(args.steps)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clocks:
+        t_start.record(stream)
+        for k in range(args.steps):
+            for j, (_, fn) in enumerate(launches):
+                ev[k][j][0].record(stream)
+                fn()
+                ev[k][j][1].record(stream)
+        t_end.record(stream)
+        torch.cuda.synchronize()
+    dist.barrier()
+    ms_local = t_start.elapsed_time(t_end)
+    ms = dist.max(ms_local)
+    status = api.device_status()
+    if status:
+        raise SystemExit("device status reported error bits %#x" % status)
+
+    per_launch_ms = [statistics.median([ev[k][j][0].elapsed_time(ev[k][j][1]) for k in range(args.steps)])
+                     for j in range(nl)]
+    value = dist.world * bytes_per_step * args.steps / (ms * 1e-3) / 1e9
+    peaks = load_peaks()
+    clk = clocks.summary()
+    sm_mhz = clk["sm_mhz"] or peaks["sm_max_mhz"]
+
+    per_alg = {}
+    hbm_bytes_per_launch = (batch.total_bytes + 12 * n + (1 * n if mixed else 0) + 32 * n)
+    for j, (a, _) in enumerate(launches):
+        t = per_launch_ms[j] * 1e-3
+        name = ALG_NAMES[a] if a is not None else "mixed"
+        if a is not None:
+            ops = float(nblocks.sum()) * OPS_PER_BLOCK[a]
+        else:
+            ops = float(sum(float(nblocks[batch.algs == x].sum()) * OPS_PER_BLOCK[x] for x in (0, 1, 2)))
+        per_alg[name] = {
+            "GB/s": batch.total_bytes / t / 1e9, "Mhash/s": n / t / 1e6, "ms": per_launch_ms[j],
+            "alu_Tops": ops / t / 1e12,
+            "alu_frac_at_clock": ops / t / 1e12 / alu_peak_tops(sms, sm_mhz),
+            "hbm_frac": hbm_bytes_per_launch / t / 1e9 / peaks["hbm_gbs"],
+        }
+    dom = max(range(nl), key=lambda j: per_launch_ms[j])
+    dom_alg = launches[dom][0]
+    dom_name = ALG_NAMES[dom_alg] if dom_alg is not None else "mixed"
+    t_dom = per_launch_ms[dom] * 1e-3
+    dom_ops = per_alg[dom_name]["alu_Tops"] * 1e12 * t_dom
+    peak_alu = alu_peak_tops(sms, peaks["sm_max_mhz"])
+    kernel_key = "%s:%s" % (args.workload, dom_name)
+    roofline = {
+        "bound": "alu", "kernel": "hb_%s_kernel<%s>" % ("mixed" if mixed else "plain", dom_name),
+        "achieved": dom_ops / t_dom / 1e12, "peak": peak_alu, "unit": "Tops/s",
+        "frac": dom_ops / t_dom / 1e12 / peak_alu,
+        "peak_source": "derived: %d SMs x 128 32-bit lanes/clk x %.0f MHz max SM clock" % (sms, peaks["sm_max_mhz"]),
+        "frac_at_measured_clock": dom_ops / t_dom / 1e12 / alu_peak_tops(sms, sm_mhz),
+        "algorithmic_ops_per_launch": dom_ops,
+        "hbm_achieved_gbs": hbm_bytes_per_launch / t_dom / 1e9,
+        "hbm_peak_gbs": peaks["hbm_gbs"], "hbm_peak_source": peaks["source"],
+        "hbm_frac": hbm_bytes_per_launch / t_dom / 1e9 / peaks["hbm_gbs"],
+        "traffic": traffic_for(kernel_key),
+    }
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": dist.world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic: uniform random bytes (numpy PCG64), shard seed per rank",
+        "config": {"workload": desc, "messages_per_gpu": n, "bytes_per_gpu": batch.total_bytes,
+                   "l2": "no flush: inputs larger than the 126 MB L2",
+                   "parallelism": "dp%d: disjoint message shards, no collective on the data path" % dist.world},
+        "mhash_per_s": dist.world * msgs_per_step * args.steps / (ms * 1e-3) / 1e6,
+        "per_alg": per_alg,
+        "roofline": roofline,
+        "gpu_launches": args.steps * nl * (4 if mixed else 1),
+        "clocks": clk,
+    }
+
+    if not args.no_e2e:
+        line["e2e"] = e2e_measure(args, batch, mixed, api, torch)
+    if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(batch, mixed)
+    if dist.rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def e2e_measure(args, batch, mixed, api, torch):
+    """Same metric through hash_batch_host with pinned host buffers: the
+    host->device copy of the step's inputs and the device->host copy of its
+    digests are inside the timed region."""
+    n = batch.n
+    packed_h = torch.from_numpy(np.ascontiguousarray(batch.packed)).pin_memory()
+    off_h = torch.from_numpy(batch.offsets.view(np.int64)).pin_memory()
+    len_h = torch.from_numpy(batch.lengths.view(np.int32)).pin_memory()
+    algs_h = torch.from_numpy(batch.algs).pin_memory() if mixed else None
+    out_h = torch.empty((n, 32), dtype=torch.uint8).pin_memory()
+    calls = [None] if mixed else [0, 1, 2]
+
+    def step():
+        for a in calls:
+            api.hash_batch_host(a, packed_h, off_h, len_h, out_h, algs=algs_h)
+
+    steps = max(1, min(args.steps, args.e2e_steps))
+    for _ in range(max(1, min(args.warmup, 3))):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        step()
+    dt = time.perf_counter() - t0
+    per_call_in = batch.packed.nbytes + 12 * n + (n if mixed else 0)
+    return {"value": len(calls) * batch.total_bytes * steps / dt / 1e9, "unit": "GB/s",
+            "h2d_bytes_per_step": len(calls) * per_call_in,
+            "d2h_bytes_per_step": len(calls) * 32 * n, "steps": steps,
+            "api": "hash_batch_host (pinned host buffers)"}
+
+
+def main(argv=None):
+    p = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4"])
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--e2e-steps", type=int, default=10)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    args = p.parse_args(argv)
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be at least 3")
+    dist = Dist(args.gpus)
+    try:
+        if args.impl == "reference":
+            run_reference(args, dist)
+        else:
+            run_ours(args, dist)
+    finally:
+        dist.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,212 @@
+/*
+ * hashbatch.h -- C-ABI of libhashbatch.so: MD5, SHA-1 and SM3 digests of a
+ * large batch of independent messages on one NVIDIA B300 (sm_103a).
+ *
+ * What is computed.  The "parallel scenario" hash operations of the paper
+ * (Sec. IV-B: digests of many messages computed at once; Sec. V-D: every
+ * input message and every output digest sits in its own array location, so
+ * the work is free of data races).  Each digest is the standard one:
+ *   HB_MD5   RFC 1321                      16-byte digest
+ *   HB_SHA1  FIPS 180-4 Sec. 6.1           20-byte digest
+ *   HB_SM3   GB/T 32905-2016               32-byte digest
+ * Messages are byte strings of 0 .. 2^32-1 bytes; padding (0x80, zeros,
+ * 64-bit bit length) is done on the device.
+ *
+ * Layout (all entry points).
+ *   packed_bytes  message bytes; message i is
+ *                 packed_bytes[offsets[i] .. offsets[i] + lengths[i]).
+ *                 Messages may start at any byte and may overlap (they are
+ *                 only read).  Reads are done in 16-byte aligned granules:
+ *                 up to 15 bytes before a message's first byte and after its
+ *                 last byte are read (never used), so those bytes must lie in
+ *                 mapped device memory -- always true inside one cudaMalloc
+ *                 allocation, whose granularity is far above 16 bytes.
+ *   offsets       uint64 per message (byte offsets into packed_bytes).
+ *   lengths       uint32 per message (byte counts).
+ *   algs          uint8 per message (HB_MD5 / HB_SHA1 / HB_SM3), mixed calls.
+ *   digests_out   HB_SLOT_BYTES (32) bytes per message, 16-byte aligned:
+ *                 slot i holds hash_digest_size(alg) digest bytes in the
+ *                 standard's output byte order, then zero bytes.
+ *
+ * Ownership.  Every pointer is owned by the caller.  Unless an entry point
+ * says "host", pointers are CUDA device pointers of the current device.  The
+ * library keeps a small per-device context (status word, scratch for the
+ * mixed path, captured graphs) created on first use and freed at process
+ * exit or by hash_release_device().
+ *
+ * Asynchrony.  Device calls are enqueued on `stream` (a cudaStream_t; NULL
+ * is the legacy default stream) and return without waiting.  The return
+ * value reports argument and launch errors only.  Errors found by a kernel
+ * (a bulk-copy wait that timed out, a bounds violation seen by the checker)
+ * are OR-ed into a per-device status word read by hash_device_status().
+ *
+ * Errors.  0 is success; negative values are the HB_ERR_* codes below;
+ * hash_strerror() names them.  n == 0 is a successful no-op.
+ */
+#ifndef HASHBATCH_H
+#define HASHBATCH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Algorithm codes (the same codes appear in the per-message `algs` array). */
+#define HB_MD5 0
+#define HB_SHA1 1
+#define HB_SM3 2
+
+#define HB_SLOT_BYTES 32
+
+/* Return codes. */
+#define HB_OK 0
+#define HB_ERR_INVALID_ALG (-1)   /* algorithm code not 0, 1 or 2            */
+#define HB_ERR_NULL (-2)          /* a required pointer is NULL with n > 0   */
+#define HB_ERR_TOO_LARGE (-3)     /* n or a size exceeds a documented limit  */
+#define HB_ERR_CUDA (-4)          /* a CUDA runtime call or launch failed    */
+#define HB_ERR_NOMEM (-5)         /* device or pinned workspace allocation   */
+#define HB_ERR_TIMEOUT (-6)       /* a device-side wait gave up (status)     */
+#define HB_ERR_ALIGN (-7)         /* digests_out not 16-byte aligned         */
+#define HB_ERR_BOUNDS (-8)        /* a message lies outside packed_len       */
+#define HB_ERR_BUDGET (-9)        /* request exceeds the serving budget      */
+#define HB_ERR_ARG (-10)          /* any other invalid argument              */
+
+/* Device status bits (hash_device_status). */
+#define HB_DEV_TIMEOUT 0x1        /* a kernel's bounded wait expired         */
+#define HB_DEV_BOUNDS 0x2         /* hash_batch_check_bounds found a message
+                                     outside [0, packed_len)                 */
+
+/* Digest size in bytes of an algorithm (16, 20, 32); 0 for an unknown code. */
+size_t hash_digest_size(int alg);
+
+/* Static description of a return code. */
+const char *hash_strerror(int code);
+
+/*
+ * hash_batch -- one algorithm for the whole batch (paper Sec. IV-B, parallel
+ * op; Sec. V-D, separate slots).  One message per GPU thread; each warp stages
+ * the next 64-byte block of its 32 messages into shared memory with bulk
+ * copies while it compresses the current one.
+ * Returns HB_OK, HB_ERR_INVALID_ALG, HB_ERR_NULL, HB_ERR_ALIGN, HB_ERR_CUDA.
+ * Limits: n < 2^40.
+ */
+int hash_batch(int alg, const uint8_t *packed_bytes, const uint64_t *offsets,
+               const uint32_t *lengths, uint64_t n, uint8_t *digests_out,
+               void *stream);
+
+/*
+ * hash_batch_mixed -- per-message algorithm, for ragged batches: messages are
+ * bucketed on the device by (estimated cost, algorithm), longest first, and
+ * one persistent launch hashes 32-message chunks popped from a shared
+ * counter.  Uses a per-device scratch area owned by the library (grown on
+ * demand with cudaMalloc; calls on different streams are ordered through an
+ * event so they never share it concurrently).  Algorithm codes outside
+ * {0,1,2} leave their slot zeroed and set nothing else.
+ * Limits: n < 2^31.  Returns as hash_batch, plus HB_ERR_NOMEM / HB_ERR_TOO_LARGE.
+ */
+int hash_batch_mixed(const uint8_t *algs, const uint8_t *packed_bytes,
+                     const uint64_t *offsets, const uint32_t *lengths, uint64_t n,
+                     uint8_t *digests_out, void *stream);
+
+/*
+ * hash_batch_check_bounds -- checks on the device that every message lies in
+ * [0, packed_len): offsets[i] + lengths[i] <= packed_len, computed without
+ * overflow.  Writes 0 to *status_dev when all messages are in bounds, else
+ * HB_DEV_BOUNDS (status_dev is a device int owned by the caller); also ORs
+ * the result into the per-device status word.  Never traps.
+ */
+int hash_batch_check_bounds(const uint64_t *offsets, const uint32_t *lengths, uint64_t n,
+                            uint64_t packed_len, int *status_dev, void *stream);
+
+/*
+ * hash_batch_host -- the same computation from HOST buffers: copies the packed
+ * bytes, offsets and lengths to device memory owned by the library, hashes
+ * them, copies the digest slots back to digests_host, and waits for the
+ * stream.  Host buffers should be pinned (cudaHostAlloc / cudaHostRegister)
+ * for full copy speed; pageable memory works but is slower.  algs_host may be
+ * NULL (single `alg`) or a host array of per-message codes (mixed path).
+ * After the copies, every message is checked against packed_len on the
+ * device before any message byte is read; when one is out of bounds the
+ * hashing kernels skip all work and the call returns HB_ERR_BOUNDS.  The
+ * device buffers are reused across calls; the call synchronises the device
+ * before reusing them.  Returns as hash_batch / hash_batch_mixed, plus
+ * HB_ERR_BOUNDS.
+ */
+int hash_batch_host(int alg, const uint8_t *algs_host, const uint8_t *packed_host,
+                    uint64_t packed_len, const uint64_t *offsets_host,
+                    const uint32_t *lengths_host, uint64_t n, uint8_t *digests_host,
+                    void *stream);
+
+/*
+ * hash_device_status -- synchronises `stream`, then returns the OR of the
+ * HB_DEV_* bits recorded on the current device since the last call, and
+ * clears them.  *status_out receives the bits.
+ */
+int hash_device_status(void *stream, int *status_out);
+
+/* hash_release_device -- frees the current device's library context. */
+int hash_release_device(void);
+
+/*
+ * Tuning.  The hashing kernels are instantiated for a few launch shapes
+ * (warps per block x bulk-copy stages in flight per warp).  hash_tune_set
+ * selects the shape that hash_batch uses for `alg`, or that the ragged path
+ * uses when alg == HB_TUNE_MIXED; hash_tune_get reads the selection;
+ * hash_tune_shape describes shape `index` and hash_tune_occupancy returns
+ * its resident blocks per SM.  An index outside [0, hash_tune_shapes()) is
+ * rejected with HB_ERR_ARG.  The Python autotuner drives these and keeps its
+ * results in a JSON cache keyed by device, SM count, algorithm and length.
+ */
+#define HB_TUNE_MIXED 3
+int hash_tune_shapes(void);
+int hash_tune_shape(int index, int *warps_per_block, int *stages);
+int hash_tune_set(int alg, int shape_index);
+int hash_tune_get(int alg);
+int hash_tune_occupancy(int alg, int shape_index);
+
+/*
+ * hash_batch_shape / hash_batch_mixed_shape -- hash_batch / hash_batch_mixed
+ * with an explicit launch shape (-1 = the tuned one) and grid size (0 = the
+ * library's choice: enough blocks for the work, at most one full wave of
+ * resident blocks); used by the autotuner and the benchmarks.
+ */
+int hash_batch_shape(int alg, const uint8_t *packed_bytes, const uint64_t *offsets,
+                     const uint32_t *lengths, uint64_t n, uint8_t *digests_out,
+                     int shape_index, int grid_blocks, void *stream);
+int hash_batch_mixed_shape(const uint8_t *algs, const uint8_t *packed_bytes,
+                           const uint64_t *offsets, const uint32_t *lengths, uint64_t n,
+                           uint8_t *digests_out, int shape_index, int grid_blocks,
+                           void *stream);
+
+/*
+ * Integer-issue microbenchmark (measurement only; not part of the hashing
+ * path): runs `iters` iterations of independent chains of one opcode class
+ * (0 LOP3, 1 IADD3, 2 SHF funnel rotate, 3 PRMT, 4 mixed LOP3+IADD3+SHF)
+ * on every resident warp and writes the elapsed SM cycles per SM to
+ * cycles_out[blocks] and a sink value to sink_dev.  blocks/threads give the
+ * launch shape.  The number of 32-bit operations executed is
+ * blocks * threads * iters * hash_int_peak_ops_per_iter().
+ */
+int hash_int_peak(int op_class, int blocks, int threads, int iters, uint64_t *cycles_out_dev,
+                  uint32_t *sink_dev, void *stream);
+int hash_int_peak_ops_per_iter(void);
+
+/*
+ * Failure-detection self test: launches one warp that waits, with the same
+ * bounded wait the hashing kernels use, on a barrier phase that nothing
+ * completes.  After timeout_ns the wait gives up, records HB_DEV_TIMEOUT in
+ * the per-device status word and the kernel returns normally.
+ */
+int hash_selftest_wait_timeout(uint64_t timeout_ns, void *stream);
+
+/* Device-side wait limit used by the hashing kernels, in nanoseconds
+ * (default 2 s).  Returns the previous value. */
+uint64_t hash_set_wait_limit_ns(uint64_t limit_ns);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HASHBATCH_H */

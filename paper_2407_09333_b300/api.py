@@ -1,0 +1,277 @@
+"""ctypes binding of libhashbatch.so (C-ABI in include/hashbatch.h).
+
+Argument marshalling only: every step of the hashing path runs in the CUDA
+library.  Device buffers are torch tensors (torch supplies device memory and
+streams); host-buffer entry points take numpy arrays or CPU tensors.  If the
+library has not been built the first call raises -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+MD5, SHA1, SM3 = 0, 1, 2
+TUNE_MIXED = 3
+SLOT_BYTES = 32
+ALG_NAMES = {MD5: "md5", SHA1: "sha1", SM3: "sm3"}
+ALG_CODES = {v: k for k, v in ALG_NAMES.items()}
+
+DEV_TIMEOUT = 0x1
+DEV_BOUNDS = 0x2
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libhashbatch.so")
+HEADER_PATH = os.path.join(os.path.dirname(_PKG), "include", "hashbatch.h")
+
+_c_int, _c_u64, _c_u32, _vp = ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p
+_SIGNATURES = {
+    "hash_digest_size": (ctypes.c_size_t, [_c_int]),
+    "hash_strerror": (ctypes.c_char_p, [_c_int]),
+    "hash_batch": (_c_int, [_c_int, _vp, _vp, _vp, _c_u64, _vp, _vp]),
+    "hash_batch_mixed": (_c_int, [_vp, _vp, _vp, _vp, _c_u64, _vp, _vp]),
+    "hash_batch_check_bounds": (_c_int, [_vp, _vp, _c_u64, _c_u64, _vp, _vp]),
+    "hash_batch_host": (_c_int, [_c_int, _vp, _vp, _c_u64, _vp, _vp, _c_u64, _vp, _vp]),
+    "hash_device_status": (_c_int, [_vp, ctypes.POINTER(_c_int)]),
+    "hash_release_device": (_c_int, []),
+    "hash_tune_shapes": (_c_int, []),
+    "hash_tune_shape": (_c_int, [_c_int, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int)]),
+    "hash_tune_set": (_c_int, [_c_int, _c_int]),
+    "hash_tune_get": (_c_int, [_c_int]),
+    "hash_tune_occupancy": (_c_int, [_c_int, _c_int]),
+    "hash_batch_shape": (_c_int, [_c_int, _vp, _vp, _vp, _c_u64, _vp, _c_int, _c_int, _vp]),
+    "hash_batch_mixed_shape": (_c_int, [_vp, _vp, _vp, _vp, _c_u64, _vp, _c_int, _c_int, _vp]),
+    "hash_int_peak": (_c_int, [_c_int, _c_int, _c_int, _c_int, _vp, _vp, _vp]),
+    "hash_int_peak_ops_per_iter": (_c_int, []),
+    "hash_selftest_wait_timeout": (_c_int, [_c_u64, _vp]),
+    "hash_set_wait_limit_ns": (_c_u64, [_c_u64]),
+}
+
+_lib = None
+
+
+class HashBatchError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__("%s failed: %s (%d)" % (where, strerror(code), code))
+
+
+def header_functions(path: str = HEADER_PATH) -> list[str]:
+    """Names of the functions declared in include/hashbatch.h."""
+    text = open(path).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(hash_[a-z0-9_]+)\s*\(", text)))
+
+
+def lib():
+    """The loaded library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                "libhashbatch.so is not built (expected at %s); run "
+                "paper_2407_09333_b300/build.py or __graft_entry__.build()" % LIB_PATH)
+        handle = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGNATURES.items():
+            fn = getattr(handle, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = handle
+    return _lib
+
+
+def strerror(code: int) -> str:
+    return lib().hash_strerror(int(code)).decode()
+
+
+def digest_size(alg: int) -> int:
+    return int(lib().hash_digest_size(int(alg)))
+
+
+def _check(rc: int, where: str):
+    if rc != 0:
+        raise HashBatchError(rc, where)
+
+
+# ---------------------------------------------------------------------------
+# torch helpers
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_handle(stream):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev_ptr(t, itemsize: int, name: str):
+    if not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % name)
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if t.element_size() != itemsize:
+        raise ValueError("%s must have %d-byte elements" % (name, itemsize))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _out_tensor(out, n, device):
+    torch = _torch()
+    if out is None:
+        return torch.empty((n, SLOT_BYTES), dtype=torch.uint8, device=device)
+    if out.dtype != torch.uint8 or out.numel() < n * SLOT_BYTES or not out.is_contiguous():
+        raise ValueError("out must be a contiguous uint8 tensor of n*32 bytes")
+    return out
+
+
+def hash_batch(alg: int, packed, offsets, lengths, out=None, stream=None,
+               shape: int = -1, grid: int = 0):
+    """Digest slots (n, 32) uint8 of every message, one algorithm."""
+    n = int(offsets.numel())
+    if lengths.numel() != n:
+        raise ValueError("offsets and lengths differ in length")
+    out = _out_tensor(out, n, offsets.device)
+    rc = lib().hash_batch_shape(
+        int(alg), _dev_ptr(packed, 1, "packed"), _dev_ptr(offsets, 8, "offsets"),
+        _dev_ptr(lengths, 4, "lengths"), n, _dev_ptr(out, 1, "out"),
+        int(shape), int(grid), _stream_handle(stream))
+    _check(rc, "hash_batch")
+    return out
+
+
+def hash_batch_mixed(algs, packed, offsets, lengths, out=None, stream=None,
+                     shape: int = -1, grid: int = 0):
+    """Digest slots (n, 32) uint8, per-message algorithm (ragged path)."""
+    n = int(offsets.numel())
+    if lengths.numel() != n or algs.numel() != n:
+        raise ValueError("algs, offsets and lengths must have one entry per message")
+    out = _out_tensor(out, n, offsets.device)
+    rc = lib().hash_batch_mixed_shape(
+        _dev_ptr(algs, 1, "algs"), _dev_ptr(packed, 1, "packed"),
+        _dev_ptr(offsets, 8, "offsets"), _dev_ptr(lengths, 4, "lengths"), n,
+        _dev_ptr(out, 1, "out"), int(shape), int(grid), _stream_handle(stream))
+    _check(rc, "hash_batch_mixed")
+    return out
+
+
+def check_bounds(offsets, lengths, packed_len: int, status=None, stream=None):
+    """Device int32 tensor: 0 when every message is inside packed_len."""
+    torch = _torch()
+    if status is None:
+        status = torch.empty(1, dtype=torch.int32, device=offsets.device)
+    rc = lib().hash_batch_check_bounds(
+        _dev_ptr(offsets, 8, "offsets"), _dev_ptr(lengths, 4, "lengths"),
+        int(offsets.numel()), int(packed_len), _dev_ptr(status, 4, "status"),
+        _stream_handle(stream))
+    _check(rc, "hash_batch_check_bounds")
+    return status
+
+
+def _host_ptr(a, name):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if a.is_cuda:
+            raise ValueError("%s must be a host buffer" % name)
+        return ctypes.c_void_p(a.data_ptr())
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def hash_batch_host(alg, packed, offsets, lengths, out, algs=None, stream=None):
+    """End-to-end call from host buffers (pinned for full speed)."""
+    n = int(len(offsets))
+    packed_len = int(packed.numel() if hasattr(packed, "numel") else packed.size)
+    rc = lib().hash_batch_host(
+        -1 if alg is None else int(alg), _host_ptr(algs, "algs"),
+        _host_ptr(packed, "packed") if packed_len else None, packed_len,
+        _host_ptr(offsets, "offsets"), _host_ptr(lengths, "lengths"), n,
+        _host_ptr(out, "out"), _stream_handle(stream))
+    _check(rc, "hash_batch_host")
+    return out
+
+
+def device_status(stream=None) -> int:
+    v = ctypes.c_int(0)
+    _check(lib().hash_device_status(_stream_handle(stream), ctypes.byref(v)), "hash_device_status")
+    return int(v.value)
+
+
+def release_device():
+    _check(lib().hash_release_device(), "hash_release_device")
+
+
+def set_wait_limit_ns(limit_ns: int) -> int:
+    return int(lib().hash_set_wait_limit_ns(int(limit_ns)))
+
+
+def selftest_wait_timeout(timeout_ns: int, stream=None):
+    _check(lib().hash_selftest_wait_timeout(int(timeout_ns), _stream_handle(stream)),
+           "hash_selftest_wait_timeout")
+
+
+# ---------------------------------------------------------------------------
+# tuning
+
+def shapes() -> list[tuple[int, int]]:
+    L = lib()
+    out = []
+    for i in range(L.hash_tune_shapes()):
+        w, s = ctypes.c_int(0), ctypes.c_int(0)
+        _check(L.hash_tune_shape(i, ctypes.byref(w), ctypes.byref(s)), "hash_tune_shape")
+        out.append((int(w.value), int(s.value)))
+    return out
+
+
+def tune_set(alg: int, shape: int):
+    _check(lib().hash_tune_set(int(alg), int(shape)), "hash_tune_set")
+
+
+def tune_get(alg: int) -> int:
+    rc = int(lib().hash_tune_get(int(alg)))
+    if rc < 0:
+        raise HashBatchError(rc, "hash_tune_get")
+    return rc
+
+
+def tune_occupancy(alg: int, shape: int) -> int:
+    rc = int(lib().hash_tune_occupancy(int(alg), int(shape)))
+    if rc < 0:
+        raise HashBatchError(rc, "hash_tune_occupancy")
+    return rc
+
+
+def int_peak(op_class: int, blocks: int, threads: int, iters: int, stream=None):
+    """Runs the integer-issue microbenchmark; returns per-block SM cycles."""
+    torch = _torch()
+    cycles = torch.zeros(blocks, dtype=torch.int64, device="cuda")
+    sink = torch.zeros(1, dtype=torch.int32, device="cuda")
+    _check(lib().hash_int_peak(int(op_class), int(blocks), int(threads), int(iters),
+                               ctypes.c_void_p(cycles.data_ptr()), ctypes.c_void_p(sink.data_ptr()),
+                               _stream_handle(stream)), "hash_int_peak")
+    return cycles
+
+
+def int_peak_ops_per_iter() -> int:
+    return int(lib().hash_int_peak_ops_per_iter())
+
+
+# ---------------------------------------------------------------------------
+# convenience: move a workloads.Batch to the device
+
+def to_device(batch, device="cuda"):
+    """(packed, offsets, lengths[, algs]) as CUDA tensors from a workloads.Batch."""
+    torch = _torch()
+    packed = torch.from_numpy(np.ascontiguousarray(batch.packed)).to(device)
+    if packed.numel() == 0:
+        packed = torch.zeros(16, dtype=torch.uint8, device=device)
+    offsets = torch.from_numpy(batch.offsets.view(np.int64)).to(device)
+    lengths = torch.from_numpy(batch.lengths.view(np.int32)).to(device)
+    algs = None
+    if batch.algs is not None:
+        algs = torch.from_numpy(batch.algs).to(device)
+    return packed, offsets, lengths, algs

@@ -1,0 +1,316 @@
+// hb_algs.cuh -- the three compression functions on one 64-byte block held in
+// registers, fully unrolled: MD5 (RFC 1321 Sec. 3.4), SHA-1 (FIPS 180-4
+// Sec. 6.1.2) and SM3 (GB/T 32905-2016 Sec. 5.3).  Boolean functions are one
+// LOP3 each, rotations one funnel shift, sums fold into IADD3.
+//
+// Word order on entry: MD5 takes the block's words little-endian; SHA-1 and
+// SM3 take them big-endian (the staging code byte-swaps with PRMT).
+#pragma once
+
+#include <cstdint>
+
+#include "hb_device.cuh"
+#include "hb_md5_table.h"
+
+namespace hb {
+
+// Algorithm descriptors -------------------------------------------------------
+
+template <int ALG>
+struct AlgTraits;
+
+template <>
+struct AlgTraits<HB_MD5> {
+  static constexpr int kStateWords = 4;
+  static constexpr int kDigestWords = 4;
+  static constexpr bool kBigEndian = false;
+};
+template <>
+struct AlgTraits<HB_SHA1> {
+  static constexpr int kStateWords = 5;
+  static constexpr int kDigestWords = 5;
+  static constexpr bool kBigEndian = true;
+};
+template <>
+struct AlgTraits<HB_SM3> {
+  static constexpr int kStateWords = 8;
+  static constexpr int kDigestWords = 8;
+  static constexpr bool kBigEndian = true;
+};
+
+// ---------------------------------------------------------------------------
+// MD5 (RFC 1321).
+
+__device__ __forceinline__ void md5_init(uint32_t (&st)[8]) {
+  // Sec. 3.3: A, B, C, D whose bytes, low-order first, are 01 23 45 67,
+  // 89 ab cd ef, fe dc ba 98, 76 54 32 10.
+  st[0] = 0x67452301u;
+  st[1] = 0xefcdab89u;
+  st[2] = 0x98badcfeu;
+  st[3] = 0x10325476u;
+}
+
+// One operation a = b + ((a + g(b,c,d) + X[k] + T[i]) <<< s).
+#define HB_MD5_OP(LUT, a, b, c, d, xk, t, s)      \
+  do {                                           \
+    a += lop3<LUT>(b, c, d) + (xk) + (t);        \
+    a = rotl<s>(a) + b;                          \
+  } while (0)
+
+// Round 2's G(x,y,z) = (x & z) | (y & ~z): LUT built with x->a, y->b, z->c.
+__device__ __forceinline__ void md5_compress(uint32_t (&st)[8], const uint32_t (&X)[16]) {
+  constexpr uint32_t T[64] = {HB_MD5_T_TABLE};
+  uint32_t a = st[0], b = st[1], c = st[2], d = st[3];
+  // Round 1: F, words in order, shifts 7 12 17 22.
+  HB_MD5_OP(LUT_CHOOSE, a, b, c, d, X[0], T[0], 7);
+  HB_MD5_OP(LUT_CHOOSE, d, a, b, c, X[1], T[1], 12);
+  HB_MD5_OP(LUT_CHOOSE, c, d, a, b, X[2], T[2], 17);
+  HB_MD5_OP(LUT_CHOOSE, b, c, d, a, X[3], T[3], 22);
+  HB_MD5_OP(LUT_CHOOSE, a, b, c, d, X[4], T[4], 7);
+  HB_MD5_OP(LUT_CHOOSE, d, a, b, c, X[5], T[5], 12);
+  HB_MD5_OP(LUT_CHOOSE, c, d, a, b, X[6], T[6], 17);
+  HB_MD5_OP(LUT_CHOOSE, b, c, d, a, X[7], T[7], 22);
+  HB_MD5_OP(LUT_CHOOSE, a, b, c, d, X[8], T[8], 7);
+  HB_MD5_OP(LUT_CHOOSE, d, a, b, c, X[9], T[9], 12);
+  HB_MD5_OP(LUT_CHOOSE, c, d, a, b, X[10], T[10], 17);
+  HB_MD5_OP(LUT_CHOOSE, b, c, d, a, X[11], T[11], 22);
+  HB_MD5_OP(LUT_CHOOSE, a, b, c, d, X[12], T[12], 7);
+  HB_MD5_OP(LUT_CHOOSE, d, a, b, c, X[13], T[13], 12);
+  HB_MD5_OP(LUT_CHOOSE, c, d, a, b, X[14], T[14], 17);
+  HB_MD5_OP(LUT_CHOOSE, b, c, d, a, X[15], T[15], 22);
+  // Round 2: G, words 1 + 5j mod 16, shifts 5 9 14 20.
+  HB_MD5_OP(LUT_MD5_G, a, b, c, d, X[1], T[16], 5);
+  HB_MD5_OP(LUT_MD5_G, d, a, b, c, X[6], T[17], 9);
+  HB_MD5_OP(LUT_MD5_G, c, d, a, b, X[11], T[18], 14);
+  HB_MD5_OP(LUT_MD5_G, b, c, d, a, X[0], T[19], 20);
+  HB_MD5_OP(LUT_MD5_G, a, b, c, d, X[5], T[20], 5);
+  HB_MD5_OP(LUT_MD5_G, d, a, b, c, X[10], T[21], 9);
+  HB_MD5_OP(LUT_MD5_G, c, d, a, b, X[15], T[22], 14);
+  HB_MD5_OP(LUT_MD5_G, b, c, d, a, X[4], T[23], 20);
+  HB_MD5_OP(LUT_MD5_G, a, b, c, d, X[9], T[24], 5);
+  HB_MD5_OP(LUT_MD5_G, d, a, b, c, X[14], T[25], 9);
+  HB_MD5_OP(LUT_MD5_G, c, d, a, b, X[3], T[26], 14);
+  HB_MD5_OP(LUT_MD5_G, b, c, d, a, X[8], T[27], 20);
+  HB_MD5_OP(LUT_MD5_G, a, b, c, d, X[13], T[28], 5);
+  HB_MD5_OP(LUT_MD5_G, d, a, b, c, X[2], T[29], 9);
+  HB_MD5_OP(LUT_MD5_G, c, d, a, b, X[7], T[30], 14);
+  HB_MD5_OP(LUT_MD5_G, b, c, d, a, X[12], T[31], 20);
+  // Round 3: H, words 5 + 3j mod 16, shifts 4 11 16 23.
+  HB_MD5_OP(LUT_XOR3, a, b, c, d, X[5], T[32], 4);
+  HB_MD5_OP(LUT_XOR3, d, a, b, c, X[8], T[33], 11);
+  HB_MD5_OP(LUT_XOR3, c, d, a, b, X[11], T[34], 16);
+  HB_MD5_OP(LUT_XOR3, b, c, d, a, X[14], T[35], 23);
+  HB_MD5_OP(LUT_XOR3, a, b, c, d, X[1], T[36], 4);
+  HB_MD5_OP(LUT_XOR3, d, a, b, c, X[4], T[37], 11);
+  HB_MD5_OP(LUT_XOR3, c, d, a, b, X[7], T[38], 16);
+  HB_MD5_OP(LUT_XOR3, b, c, d, a, X[10], T[39], 23);
+  HB_MD5_OP(LUT_XOR3, a, b, c, d, X[13], T[40], 4);
+  HB_MD5_OP(LUT_XOR3, d, a, b, c, X[0], T[41], 11);
+  HB_MD5_OP(LUT_XOR3, c, d, a, b, X[3], T[42], 16);
+  HB_MD5_OP(LUT_XOR3, b, c, d, a, X[6], T[43], 23);
+  HB_MD5_OP(LUT_XOR3, a, b, c, d, X[9], T[44], 4);
+  HB_MD5_OP(LUT_XOR3, d, a, b, c, X[12], T[45], 11);
+  HB_MD5_OP(LUT_XOR3, c, d, a, b, X[15], T[46], 16);
+  HB_MD5_OP(LUT_XOR3, b, c, d, a, X[2], T[47], 23);
+  // Round 4: I, words 7j mod 16, shifts 6 10 15 21.
+  HB_MD5_OP(LUT_MD5_I, a, b, c, d, X[0], T[48], 6);
+  HB_MD5_OP(LUT_MD5_I, d, a, b, c, X[7], T[49], 10);
+  HB_MD5_OP(LUT_MD5_I, c, d, a, b, X[14], T[50], 15);
+  HB_MD5_OP(LUT_MD5_I, b, c, d, a, X[5], T[51], 21);
+  HB_MD5_OP(LUT_MD5_I, a, b, c, d, X[12], T[52], 6);
+  HB_MD5_OP(LUT_MD5_I, d, a, b, c, X[3], T[53], 10);
+  HB_MD5_OP(LUT_MD5_I, c, d, a, b, X[10], T[54], 15);
+  HB_MD5_OP(LUT_MD5_I, b, c, d, a, X[1], T[55], 21);
+  HB_MD5_OP(LUT_MD5_I, a, b, c, d, X[8], T[56], 6);
+  HB_MD5_OP(LUT_MD5_I, d, a, b, c, X[15], T[57], 10);
+  HB_MD5_OP(LUT_MD5_I, c, d, a, b, X[6], T[58], 15);
+  HB_MD5_OP(LUT_MD5_I, b, c, d, a, X[13], T[59], 21);
+  HB_MD5_OP(LUT_MD5_I, a, b, c, d, X[4], T[60], 6);
+  HB_MD5_OP(LUT_MD5_I, d, a, b, c, X[11], T[61], 10);
+  HB_MD5_OP(LUT_MD5_I, c, d, a, b, X[2], T[62], 15);
+  HB_MD5_OP(LUT_MD5_I, b, c, d, a, X[9], T[63], 21);
+  st[0] += a;
+  st[1] += b;
+  st[2] += c;
+  st[3] += d;
+}
+#undef HB_MD5_OP
+
+// ---------------------------------------------------------------------------
+// SHA-1 (FIPS 180-4).
+
+__device__ __forceinline__ void sha1_init(uint32_t (&st)[8]) {
+  // Sec. 5.3.1
+  st[0] = 0x67452301u;
+  st[1] = 0xefcdab89u;
+  st[2] = 0x98badcfeu;
+  st[3] = 0x10325476u;
+  st[4] = 0xc3d2e1f0u;
+}
+
+template <int T>
+__device__ __forceinline__ uint32_t sha1_f(uint32_t x, uint32_t y, uint32_t z) {
+  // Sec. 4.1.1: Ch, Parity, Maj, Parity over t = 0-19, 20-39, 40-59, 60-79.
+  if constexpr (T < 20) return lop3<LUT_CHOOSE>(x, y, z);
+  else if constexpr (T < 40) return lop3<LUT_XOR3>(x, y, z);
+  else if constexpr (T < 60) return lop3<LUT_MAJ>(x, y, z);
+  else return lop3<LUT_XOR3>(x, y, z);
+}
+
+template <int T>
+__device__ __forceinline__ constexpr uint32_t sha1_k() {
+  // Sec. 4.2.1
+  return T < 20 ? 0x5a827999u : T < 40 ? 0x6ed9eba1u : T < 60 ? 0x8f1bbcdcu : 0xca62c1d6u;
+}
+
+// Rounds T .. 79 by compile-time recursion; W is the 16-word schedule ring.
+template <int T>
+__device__ __forceinline__ void sha1_rounds(uint32_t& a, uint32_t& b, uint32_t& c, uint32_t& d,
+                                            uint32_t& e, uint32_t (&W)[16]) {
+  if constexpr (T < 80) {
+    if constexpr (T >= 16) {
+      W[T & 15] = rotl<1>(lop3<LUT_XOR3>(W[(T - 3) & 15], W[(T - 8) & 15], W[(T - 14) & 15]) ^
+                          W[T & 15]);
+    }
+    const uint32_t t = rotl<5>(a) + sha1_f<T>(b, c, d) + e + sha1_k<T>() + W[T & 15];
+    e = d;
+    d = c;
+    c = rotl<30>(b);
+    b = a;
+    a = t;
+    sha1_rounds<T + 1>(a, b, c, d, e, W);
+  }
+}
+
+__device__ __forceinline__ void sha1_compress(uint32_t (&st)[8], const uint32_t (&X)[16]) {
+  uint32_t W[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) W[i] = X[i];
+  uint32_t a = st[0], b = st[1], c = st[2], d = st[3], e = st[4];
+  sha1_rounds<0>(a, b, c, d, e, W);
+  st[0] += a;
+  st[1] += b;
+  st[2] += c;
+  st[3] += d;
+  st[4] += e;
+}
+
+// ---------------------------------------------------------------------------
+// SM3 (GB/T 32905-2016).
+
+__device__ __forceinline__ void sm3_init(uint32_t (&st)[8]) {
+  // Sec. 4.1
+  st[0] = 0x7380166fu;
+  st[1] = 0x4914b2b9u;
+  st[2] = 0x172442d7u;
+  st[3] = 0xda8a0600u;
+  st[4] = 0xa96f30bcu;
+  st[5] = 0x163138aau;
+  st[6] = 0xe38dee4du;
+  st[7] = 0xb0fb0e4eu;
+}
+
+// T_j <<< (j mod 32), Sec. 4.2 and 5.3.3, folded at compile time.
+template <int J>
+__device__ __forceinline__ constexpr uint32_t sm3_tj_rot() {
+  constexpr uint32_t t = J < 16 ? 0x79cc4519u : 0x7a879d8au;
+  constexpr int s = J % 32;
+  return s == 0 ? t : (uint32_t)((t << s) | (t >> (32 - s)));
+}
+
+__device__ __forceinline__ uint32_t sm3_p0(uint32_t x) {
+  return lop3<LUT_XOR3>(x, rotl<9>(x), rotl<17>(x));
+}
+__device__ __forceinline__ uint32_t sm3_p1(uint32_t x) {
+  return lop3<LUT_XOR3>(x, rotl<15>(x), rotl<23>(x));
+}
+
+// Rounds J .. 63.  W is a 16-word ring holding W_{J} .. W_{J+3} (and older
+// words still needed); round J first extends it with W_{J+4} (Sec. 5.3.2),
+// so that W'_J = W_J ^ W_{J+4} is available.
+template <int J>
+__device__ __forceinline__ void sm3_rounds(uint32_t (&v)[8], uint32_t (&W)[16]) {
+  if constexpr (J < 64) {
+    constexpr int M = J + 4;  // index of the word produced this round
+    if constexpr (M >= 16 && M < 68) {
+      const uint32_t x = lop3<LUT_XOR3>(W[(M - 16) & 15], W[(M - 9) & 15], rotl<15>(W[(M - 3) & 15]));
+      W[M & 15] = lop3<LUT_XOR3>(sm3_p1(x), rotl<7>(W[(M - 13) & 15]), W[(M - 6) & 15]);
+    }
+    uint32_t& A = v[0];
+    uint32_t& B = v[1];
+    uint32_t& C = v[2];
+    uint32_t& D = v[3];
+    uint32_t& E = v[4];
+    uint32_t& F = v[5];
+    uint32_t& G = v[6];
+    uint32_t& H = v[7];
+    const uint32_t wj = W[J & 15];
+    const uint32_t wpj = wj ^ W[M & 15];
+    const uint32_t a12 = rotl<12>(A);
+    const uint32_t ss1 = rotl<7>(a12 + E + sm3_tj_rot<J>());
+    const uint32_t ss2 = ss1 ^ a12;
+    uint32_t ff, gg;
+    if constexpr (J < 16) {
+      ff = lop3<LUT_XOR3>(A, B, C);
+      gg = lop3<LUT_XOR3>(E, F, G);
+    } else {
+      ff = lop3<LUT_MAJ>(A, B, C);
+      gg = lop3<LUT_CHOOSE>(E, F, G);
+    }
+    const uint32_t tt1 = ff + D + ss2 + wpj;
+    const uint32_t tt2 = gg + H + ss1 + wj;
+    D = C;
+    C = rotl<9>(B);
+    B = A;
+    A = tt1;
+    H = G;
+    G = rotl<19>(F);
+    F = E;
+    E = sm3_p0(tt2);
+    sm3_rounds<J + 1>(v, W);
+  }
+}
+
+__device__ __forceinline__ void sm3_compress(uint32_t (&st)[8], const uint32_t (&X)[16]) {
+  uint32_t W[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) W[i] = X[i];
+  uint32_t v[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = st[i];
+  sm3_rounds<0>(v, W);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) st[i] ^= v[i];
+}
+
+// ---------------------------------------------------------------------------
+// Uniform entry points.
+
+template <int ALG>
+__device__ __forceinline__ void alg_init(uint32_t (&st)[8]) {
+  if constexpr (ALG == HB_MD5) md5_init(st);
+  else if constexpr (ALG == HB_SHA1) sha1_init(st);
+  else sm3_init(st);
+}
+
+template <int ALG>
+__device__ __forceinline__ void alg_compress(uint32_t (&st)[8], const uint32_t (&X)[16]) {
+  if constexpr (ALG == HB_MD5) md5_compress(st, X);
+  else if constexpr (ALG == HB_SHA1) sha1_compress(st, X);
+  else sm3_compress(st, X);
+}
+
+// Digest words in memory order for the 32-byte slot (zero fill after the
+// digest): MD5 words little-endian as held, SHA-1 and SM3 byte-swapped.
+template <int ALG>
+__device__ __forceinline__ void alg_digest_words(const uint32_t (&st)[8], uint32_t (&out)[8]) {
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    if (i < AlgTraits<ALG>::kDigestWords)
+      out[i] = AlgTraits<ALG>::kBigEndian ? bswap32(st[i]) : st[i];
+    else
+      out[i] = 0u;
+  }
+}
+
+}  // namespace hb

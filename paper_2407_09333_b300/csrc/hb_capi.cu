@@ -1,0 +1,452 @@
+// hb_capi.cu -- the C-ABI of libhashbatch.so (declared in include/hashbatch.h):
+// argument checks, the per-device context, launch-shape selection, the
+// host-buffer path and the captured-graph plans of the ragged path.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+
+#include "hashbatch.h"
+#include "hb_launch.h"
+
+using hb::KernelArgs;
+using hb::MixedArgs;
+using hb::MixedWorkspace;
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+constexpr int kMaxShapes = 16;
+constexpr uint64_t kMaxPlainN = 1ull << 40;
+constexpr uint64_t kMaxMixedN = 1ull << 31;
+
+struct DeviceBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+  // Grows to at least `bytes`; the old contents are not kept.
+  cudaError_t reserve(size_t bytes) {
+    if (bytes <= cap) return cudaSuccess;
+    if (p) {
+      cudaError_t e = cudaFree(p);  // synchronises the device
+      if (e != cudaSuccess) return e;
+      p = nullptr;
+      cap = 0;
+    }
+    size_t want = std::max<size_t>(bytes, 256);
+    cudaError_t e = cudaMalloc(&p, want);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      return e;
+    }
+    cap = want;
+    return cudaSuccess;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+  }
+};
+
+struct Ctx {
+  int device = -1;
+  int sms = 0;
+  int* status = nullptr;                 // device word of HB_DEV_* bits
+  int occ_plain[3][kMaxShapes] = {};     // resident blocks per SM, 0 = not prepared
+  int occ_mixed[kMaxShapes] = {};
+  int tune_plain[3] = {0, 0, 0};
+  int tune_mixed = 0;
+  DeviceBuf ws;                          // ragged-path scratch
+  cudaEvent_t ws_event = nullptr;        // last use of `ws`
+  bool ws_used = false;
+  // host-buffer path
+  DeviceBuf h_packed, h_off, h_len, h_algs, h_dig, h_flag;
+  int* flag_host = nullptr;              // pinned
+};
+
+std::mutex g_mu;
+Ctx* g_ctx[kMaxDevices] = {};
+uint64_t g_wait_limit_ns = 2000000000ull;
+
+int cuda_fail(cudaError_t e) { return e == cudaErrorMemoryAllocation ? HB_ERR_NOMEM : HB_ERR_CUDA; }
+
+// The current device's context, created on first use (this first call
+// allocates and must not happen inside a stream capture).
+int get_ctx(Ctx** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return HB_ERR_CUDA;
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (!g_ctx[dev]) {
+    Ctx* c = new Ctx();
+    c->device = dev;
+    if (cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaMalloc(&c->status, sizeof(int)) != cudaSuccess ||
+        cudaMemset(c->status, 0, sizeof(int)) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ws_event, cudaEventDisableTiming) != cudaSuccess ||
+        cudaHostAlloc(&c->flag_host, sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
+      delete c;
+      return HB_ERR_CUDA;
+    }
+    g_ctx[dev] = c;
+  }
+  *out = g_ctx[dev];
+  return HB_OK;
+}
+
+int occupancy(Ctx* c, bool mixed, int alg, int shape, int* occ) {
+  int& slot = mixed ? c->occ_mixed[shape] : c->occ_plain[alg][shape];
+  if (slot == 0) {
+    int b = 0;
+    cudaError_t e = hb::prepare_kernel(mixed, alg, shape, &b);
+    if (e != cudaSuccess) return cuda_fail(e);
+    slot = b > 0 ? b : 1;
+  }
+  *occ = slot;
+  return HB_OK;
+}
+
+int check_common(const void* packed, const uint64_t* offsets, const uint32_t* lengths,
+                 uint64_t n, const uint8_t* digests) {
+  if (!packed || !offsets || !lengths || !digests) return HB_ERR_NULL;
+  if (reinterpret_cast<uintptr_t>(digests) & 15u) return HB_ERR_ALIGN;
+  (void)n;
+  return HB_OK;
+}
+
+int launch_plain(Ctx* c, int alg, int shape, int grid, const KernelArgs& a, cudaStream_t s) {
+  if (shape < 0 || shape >= hb::num_shapes()) return HB_ERR_ARG;
+  int occ = 0;
+  int rc = occupancy(c, false, alg, shape, &occ);
+  if (rc) return rc;
+  int warps = 0, stages = 0;
+  hb::shape_desc(shape, &warps, &stages);
+  const uint64_t ntasks = (a.n + 31) / 32;
+  const uint64_t need = (ntasks + warps - 1) / warps;
+  if (grid <= 0) grid = (int)std::min<uint64_t>(need, (uint64_t)c->sms * occ);
+  cudaError_t e = hb::launch_hash(false, alg, shape, grid, a, s);
+  return e == cudaSuccess ? HB_OK : cuda_fail(e);
+}
+
+int grid_for_elementwise(Ctx* c, uint64_t n) {
+  const uint64_t need = (n + 255) / 256;
+  return (int)std::max<uint64_t>(1, std::min<uint64_t>(need, (uint64_t)c->sms * 8));
+}
+
+// Ragged path on a given workspace (bucketing + persistent kernel).
+int launch_mixed(Ctx* c, int shape, int grid, const uint8_t* algs, const uint8_t* packed,
+                 const uint64_t* offsets, const uint32_t* lengths, uint64_t n, uint8_t* digests,
+                 void* ws, const int* abort_flag, cudaStream_t s) {
+  if (shape < 0 || shape >= hb::num_shapes()) return HB_ERR_ARG;
+  MixedArgs m;
+  m.algs = algs;
+  m.lengths = lengths;
+  m.n = n;
+  m.digests = digests;
+  m.ws = static_cast<MixedWorkspace*>(ws);
+  m.perm = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + sizeof(MixedWorkspace));
+  cudaError_t e = hb::launch_bucketing(m, grid_for_elementwise(c, n), s);
+  if (e != cudaSuccess) return cuda_fail(e);
+  int occ = 0;
+  int rc = occupancy(c, true, 0, shape, &occ);
+  if (rc) return rc;
+  KernelArgs a{};
+  a.packed = packed;
+  a.offsets = offsets;
+  a.lengths = lengths;
+  a.algs = algs;
+  a.perm = m.perm;
+  a.chunk_counter = &m.ws->chunk_counter;
+  a.nchunks = &m.ws->nchunks;
+  a.n = n;
+  a.digests = digests;
+  a.status = c->status;
+  a.abort_flag = abort_flag;
+  a.wait_limit_ns = g_wait_limit_ns;
+  if (grid <= 0) grid = c->sms * occ;
+  e = hb::launch_hash(true, 0, shape, grid, a, s);
+  return e == cudaSuccess ? HB_OK : cuda_fail(e);
+}
+
+int reserve_ws(Ctx* c, uint64_t n) {
+  const size_t need = hb::mixed_workspace_bytes(n);
+  if (need > c->ws.cap && c->ws_used) {
+    if (cudaEventSynchronize(c->ws_event) != cudaSuccess) return HB_ERR_CUDA;
+  }
+  cudaError_t e = c->ws.reserve(need);
+  return e == cudaSuccess ? HB_OK : cuda_fail(e);
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t hash_digest_size(int alg) {
+  switch (alg) {
+    case HB_MD5: return 16;
+    case HB_SHA1: return 20;
+    case HB_SM3: return 32;
+    default: return 0;
+  }
+}
+
+const char* hash_strerror(int code) {
+  switch (code) {
+    case HB_OK: return "ok";
+    case HB_ERR_INVALID_ALG: return "invalid algorithm code";
+    case HB_ERR_NULL: return "null pointer";
+    case HB_ERR_TOO_LARGE: return "size exceeds a documented limit";
+    case HB_ERR_CUDA: return "CUDA runtime or launch error";
+    case HB_ERR_NOMEM: return "device or pinned memory allocation failed";
+    case HB_ERR_TIMEOUT: return "a device-side wait timed out";
+    case HB_ERR_ALIGN: return "digests_out is not 16-byte aligned";
+    case HB_ERR_BOUNDS: return "a message lies outside the packed buffer";
+    case HB_ERR_BUDGET: return "request exceeds the memory budget";
+    case HB_ERR_ARG: return "invalid argument";
+    default: return "unknown error code";
+  }
+}
+
+int hash_batch_shape(int alg, const uint8_t* packed_bytes, const uint64_t* offsets,
+                     const uint32_t* lengths, uint64_t n, uint8_t* digests_out, int shape_index,
+                     int grid_blocks, void* stream) {
+  if (hash_digest_size(alg) == 0) return HB_ERR_INVALID_ALG;
+  if (n == 0) return HB_OK;
+  if (n >= kMaxPlainN) return HB_ERR_TOO_LARGE;
+  int rc = check_common(packed_bytes, offsets, lengths, n, digests_out);
+  if (rc) return rc;
+  Ctx* c = nullptr;
+  if ((rc = get_ctx(&c))) return rc;
+  if (shape_index < 0) shape_index = c->tune_plain[alg];
+  KernelArgs a{};
+  a.packed = packed_bytes;
+  a.offsets = offsets;
+  a.lengths = lengths;
+  a.n = n;
+  a.digests = digests_out;
+  a.status = c->status;
+  a.wait_limit_ns = g_wait_limit_ns;
+  return launch_plain(c, alg, shape_index, grid_blocks, a, static_cast<cudaStream_t>(stream));
+}
+
+int hash_batch(int alg, const uint8_t* packed_bytes, const uint64_t* offsets,
+               const uint32_t* lengths, uint64_t n, uint8_t* digests_out, void* stream) {
+  return hash_batch_shape(alg, packed_bytes, offsets, lengths, n, digests_out, -1, 0, stream);
+}
+
+int hash_batch_mixed_shape(const uint8_t* algs, const uint8_t* packed_bytes,
+                           const uint64_t* offsets, const uint32_t* lengths, uint64_t n,
+                           uint8_t* digests_out, int shape_index, int grid_blocks, void* stream) {
+  if (n == 0) return HB_OK;
+  if (n >= kMaxMixedN) return HB_ERR_TOO_LARGE;
+  int rc = check_common(packed_bytes, offsets, lengths, n, digests_out);
+  if (rc) return rc;
+  if (!algs) return HB_ERR_NULL;
+  Ctx* c = nullptr;
+  if ((rc = get_ctx(&c))) return rc;
+  if (shape_index < 0) shape_index = c->tune_mixed;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if ((rc = reserve_ws(c, n))) return rc;
+  if (c->ws_used && cudaStreamWaitEvent(s, c->ws_event, 0) != cudaSuccess) return HB_ERR_CUDA;
+  rc = launch_mixed(c, shape_index, grid_blocks, algs, packed_bytes, offsets, lengths, n,
+                    digests_out, c->ws.p, nullptr, s);
+  if (rc) return rc;
+  if (cudaEventRecord(c->ws_event, s) != cudaSuccess) return HB_ERR_CUDA;
+  c->ws_used = true;
+  return HB_OK;
+}
+
+int hash_batch_mixed(const uint8_t* algs, const uint8_t* packed_bytes, const uint64_t* offsets,
+                     const uint32_t* lengths, uint64_t n, uint8_t* digests_out, void* stream) {
+  return hash_batch_mixed_shape(algs, packed_bytes, offsets, lengths, n, digests_out, -1, 0,
+                                stream);
+}
+
+int hash_batch_check_bounds(const uint64_t* offsets, const uint32_t* lengths, uint64_t n,
+                            uint64_t packed_len, int* status_dev, void* stream) {
+  if (!status_dev) return HB_ERR_NULL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (cudaMemsetAsync(status_dev, 0, sizeof(int), s) != cudaSuccess) return HB_ERR_CUDA;
+  if (n == 0) return HB_OK;
+  if (!offsets || !lengths) return HB_ERR_NULL;
+  Ctx* c = nullptr;
+  int rc = get_ctx(&c);
+  if (rc) return rc;
+  cudaError_t e = hb::launch_bounds(offsets, lengths, n, packed_len, status_dev, c->status,
+                                    grid_for_elementwise(c, n), s);
+  return e == cudaSuccess ? HB_OK : cuda_fail(e);
+}
+
+int hash_batch_host(int alg, const uint8_t* algs_host, const uint8_t* packed_host,
+                    uint64_t packed_len, const uint64_t* offsets_host,
+                    const uint32_t* lengths_host, uint64_t n, uint8_t* digests_host,
+                    void* stream) {
+  if (!algs_host && hash_digest_size(alg) == 0) return HB_ERR_INVALID_ALG;
+  if (n == 0) return HB_OK;
+  if (n >= (algs_host ? kMaxMixedN : kMaxPlainN)) return HB_ERR_TOO_LARGE;
+  if (!offsets_host || !lengths_host || !digests_host || (!packed_host && packed_len))
+    return HB_ERR_NULL;
+  Ctx* c = nullptr;
+  int rc = get_ctx(&c);
+  if (rc) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // Make sure no earlier call on another stream still uses the buffers.
+  if (cudaDeviceSynchronize() != cudaSuccess) return HB_ERR_CUDA;
+  const size_t pbytes = ((size_t)packed_len + 15) / 16 * 16 + 16;
+  cudaError_t e;
+  if ((e = c->h_packed.reserve(pbytes)) != cudaSuccess ||
+      (e = c->h_off.reserve(n * sizeof(uint64_t))) != cudaSuccess ||
+      (e = c->h_len.reserve(n * sizeof(uint32_t))) != cudaSuccess ||
+      (e = c->h_dig.reserve(n * (size_t)HB_SLOT_BYTES)) != cudaSuccess ||
+      (e = c->h_flag.reserve(sizeof(int))) != cudaSuccess ||
+      (algs_host && (e = c->h_algs.reserve(n)) != cudaSuccess))
+    return cuda_fail(e);
+  uint8_t* d_packed = static_cast<uint8_t*>(c->h_packed.p);
+  uint64_t* d_off = static_cast<uint64_t*>(c->h_off.p);
+  uint32_t* d_len = static_cast<uint32_t*>(c->h_len.p);
+  uint8_t* d_dig = static_cast<uint8_t*>(c->h_dig.p);
+  int* d_flag = static_cast<int*>(c->h_flag.p);
+  uint8_t* d_algs = static_cast<uint8_t*>(c->h_algs.p);
+  if (packed_len && cudaMemcpyAsync(d_packed, packed_host, packed_len, cudaMemcpyHostToDevice, s))
+    return HB_ERR_CUDA;
+  if (cudaMemcpyAsync(d_off, offsets_host, n * sizeof(uint64_t), cudaMemcpyHostToDevice, s) ||
+      cudaMemcpyAsync(d_len, lengths_host, n * sizeof(uint32_t), cudaMemcpyHostToDevice, s))
+    return HB_ERR_CUDA;
+  if (algs_host && cudaMemcpyAsync(d_algs, algs_host, n, cudaMemcpyHostToDevice, s))
+    return HB_ERR_CUDA;
+  // Bounds are checked on the device before any message byte is read; the
+  // hashing kernels skip all work when the check failed.
+  if (cudaMemsetAsync(d_flag, 0, sizeof(int), s)) return HB_ERR_CUDA;
+  e = hb::launch_bounds(d_off, d_len, n, packed_len, d_flag, nullptr, grid_for_elementwise(c, n), s);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if (algs_host) {
+    if ((rc = reserve_ws(c, n))) return rc;
+    rc = launch_mixed(c, c->tune_mixed, 0, d_algs, d_packed, d_off, d_len, n, d_dig, c->ws.p,
+                      d_flag, s);
+    if (rc) return rc;
+    if (cudaEventRecord(c->ws_event, s) != cudaSuccess) return HB_ERR_CUDA;
+    c->ws_used = true;
+  } else {
+    KernelArgs a{};
+    a.packed = d_packed;
+    a.offsets = d_off;
+    a.lengths = d_len;
+    a.n = n;
+    a.digests = d_dig;
+    a.status = c->status;
+    a.abort_flag = d_flag;
+    a.wait_limit_ns = g_wait_limit_ns;
+    if ((rc = launch_plain(c, alg, c->tune_plain[alg], 0, a, s))) return rc;
+  }
+  if (cudaMemcpyAsync(digests_host, d_dig, n * (size_t)HB_SLOT_BYTES, cudaMemcpyDeviceToHost, s) ||
+      cudaMemcpyAsync(c->flag_host, d_flag, sizeof(int), cudaMemcpyDeviceToHost, s))
+    return HB_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return HB_ERR_CUDA;
+  return *c->flag_host ? HB_ERR_BOUNDS : HB_OK;
+}
+
+int hash_device_status(void* stream, int* status_out) {
+  if (!status_out) return HB_ERR_NULL;
+  Ctx* c = nullptr;
+  int rc = get_ctx(&c);
+  if (rc) return rc;
+  if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return HB_ERR_CUDA;
+  int v = 0;
+  if (cudaMemcpy(&v, c->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemset(c->status, 0, sizeof(int)) != cudaSuccess)
+    return HB_ERR_CUDA;
+  *status_out = v;
+  return HB_OK;
+}
+
+int hash_release_device(void) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return HB_ERR_CUDA;
+  std::lock_guard<std::mutex> lock(g_mu);
+  Ctx* c = g_ctx[dev];
+  if (!c) return HB_OK;
+  cudaDeviceSynchronize();
+  c->ws.release();
+  c->h_packed.release();
+  c->h_off.release();
+  c->h_len.release();
+  c->h_algs.release();
+  c->h_dig.release();
+  c->h_flag.release();
+  if (c->status) cudaFree(c->status);
+  if (c->ws_event) cudaEventDestroy(c->ws_event);
+  if (c->flag_host) cudaFreeHost(c->flag_host);
+  delete c;
+  g_ctx[dev] = nullptr;
+  return HB_OK;
+}
+
+int hash_tune_shapes(void) { return hb::num_shapes(); }
+
+int hash_tune_shape(int index, int* warps_per_block, int* stages) {
+  if (!warps_per_block || !stages) return HB_ERR_NULL;
+  return hb::shape_desc(index, warps_per_block, stages) ? HB_OK : HB_ERR_ARG;
+}
+
+int hash_tune_set(int alg, int shape_index) {
+  if (shape_index < 0 || shape_index >= hb::num_shapes()) return HB_ERR_ARG;
+  if (alg != HB_TUNE_MIXED && hash_digest_size(alg) == 0) return HB_ERR_INVALID_ALG;
+  Ctx* c = nullptr;
+  int rc = get_ctx(&c);
+  if (rc) return rc;
+  if (alg == HB_TUNE_MIXED)
+    c->tune_mixed = shape_index;
+  else
+    c->tune_plain[alg] = shape_index;
+  return HB_OK;
+}
+
+int hash_tune_get(int alg) {
+  Ctx* c = nullptr;
+  if (get_ctx(&c)) return HB_ERR_CUDA;
+  if (alg == HB_TUNE_MIXED) return c->tune_mixed;
+  if (hash_digest_size(alg) == 0) return HB_ERR_INVALID_ALG;
+  return c->tune_plain[alg];
+}
+
+int hash_tune_occupancy(int alg, int shape_index) {
+  if (shape_index < 0 || shape_index >= hb::num_shapes()) return HB_ERR_ARG;
+  const bool mixed = alg == HB_TUNE_MIXED;
+  if (!mixed && hash_digest_size(alg) == 0) return HB_ERR_INVALID_ALG;
+  Ctx* c = nullptr;
+  int rc = get_ctx(&c);
+  if (rc) return rc;
+  int occ = 0;
+  if ((rc = occupancy(c, mixed, mixed ? 0 : alg, shape_index, &occ))) return rc;
+  return occ;
+}
+
+int hash_int_peak(int op_class, int blocks, int threads, int iters, uint64_t* cycles_out_dev,
+                  uint32_t* sink_dev, void* stream) {
+  if (!cycles_out_dev || !sink_dev) return HB_ERR_NULL;
+  if (blocks <= 0 || threads <= 0 || threads > 1024 || iters <= 0) return HB_ERR_ARG;
+  cudaError_t e = hb::launch_int_peak(op_class, blocks, threads, iters,
+                                      reinterpret_cast<unsigned long long*>(cycles_out_dev),
+                                      sink_dev, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? HB_OK : (e == cudaErrorInvalidValue ? HB_ERR_ARG : HB_ERR_CUDA);
+}
+
+int hash_int_peak_ops_per_iter(void) { return 32; }
+
+int hash_selftest_wait_timeout(uint64_t timeout_ns, void* stream) {
+  Ctx* c = nullptr;
+  int rc = get_ctx(&c);
+  if (rc) return rc;
+  cudaError_t e = hb::launch_selftest_wait(timeout_ns, c->status, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? HB_OK : HB_ERR_CUDA;
+}
+
+uint64_t hash_set_wait_limit_ns(uint64_t limit_ns) {
+  std::lock_guard<std::mutex> lock(g_mu);
+  const uint64_t old = g_wait_limit_ns;
+  if (limit_ns) g_wait_limit_ns = limit_ns;
+  return old;
+}
+
+}  // extern "C"

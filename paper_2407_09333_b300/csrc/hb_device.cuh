@@ -1,0 +1,164 @@
+// hb_device.cuh -- sm_103a device primitives used by every hashing kernel:
+// integer ops pinned to single instructions (LOP3, SHF, PRMT), the per-warp
+// bulk-copy (TMA, no multicast) staging pipeline built on mbarriers, and the
+// bounded waits that report a timeout instead of hanging.
+#pragma once
+
+#include <cstdint>
+
+#include "hashbatch.h"
+
+namespace hb {
+
+// ---------------------------------------------------------------------------
+// Integer building blocks.
+
+// Three-input Boolean function as one LOP3; LUT is the function's truth table
+// evaluated on the canonical operands a = 0xF0, b = 0xCC, c = 0xAA.
+template <uint32_t LUT>
+__device__ __forceinline__ uint32_t lop3(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t d;
+  asm("lop3.b32 %0, %1, %2, %3, %4;" : "=r"(d) : "r"(a), "r"(b), "r"(c), "n"(LUT));
+  return d;
+}
+
+// Truth tables, computed from the Boolean definitions on the canonical inputs.
+constexpr uint32_t kA = 0xF0, kB = 0xCC, kC = 0xAA;
+constexpr uint32_t LUT_XOR3 = (kA ^ kB ^ kC) & 0xFF;                         // x^y^z
+constexpr uint32_t LUT_CHOOSE = ((kA & kB) | (~kA & kC)) & 0xFF;             // x?y:z
+constexpr uint32_t LUT_MAJ = ((kA & kB) | (kA & kC) | (kB & kC)) & 0xFF;     // majority
+constexpr uint32_t LUT_MD5_G = ((kA & kC) | (kB & ~kC)) & 0xFF;              // (x&z)|(y&~z)
+constexpr uint32_t LUT_MD5_I = (kB ^ (kA | ~kC)) & 0xFF;                     // y^(x|~z)
+
+// Left rotation as a funnel shift (SHF.L.W).
+template <int S>
+__device__ __forceinline__ uint32_t rotl(uint32_t x) {
+  return __funnelshift_l(x, x, S);
+}
+
+// Byte permute (PRMT): bytes of the 64-bit value {hi:lo} picked by `sel`.
+__device__ __forceinline__ uint32_t prmt(uint32_t lo, uint32_t hi, uint32_t sel) {
+  return __byte_perm(lo, hi, sel);
+}
+
+// Byte-reverse of one word.
+__device__ __forceinline__ uint32_t bswap32(uint32_t x) { return __byte_perm(x, 0, 0x0123); }
+
+// ---------------------------------------------------------------------------
+// Shared-memory, mbarrier and bulk-copy wrappers (PTX ISA, sm_90+).
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_inval(uint32_t bar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// Make mbarrier initialisation (and earlier generic shared-memory writes)
+// visible to the async proxy that performs bulk-copy completion.
+__device__ __forceinline__ void fence_barrier_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// One arrival that also raises the expected transaction byte count.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile(
+      "{\n\t.reg .b64 st;\n\t"
+      "mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(bar),
+      "r"(bytes)
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_timer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Wait for phase `parity` of an mbarrier to complete, giving up after
+// `limit_ns` nanoseconds.  On timeout, records HB_DEV_TIMEOUT in *status and
+// returns false; the caller stops issuing work.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, uint64_t limit_ns,
+                                                  int* status) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_timer_ns();
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (global_timer_ns() - t0 > limit_ns) {
+      if (status) atomicOr(status, HB_DEV_TIMEOUT);
+      return false;
+    }
+  }
+}
+
+// 1-D bulk copy global -> shared (TMA engine, no multicast).  dst, src and
+// bytes must be multiples of 16; completion is signalled on `bar` as
+// transaction bytes.
+__device__ __forceinline__ void bulk_copy_g2s(uint32_t dst, const void* src, uint32_t bytes,
+                                              uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
+// Shared-memory accesses by 32-bit shared-window address.  They are
+// `volatile` so they keep their order relative to the mbarrier waits and to
+// each other at the source level, but carry no memory clobber, so the
+// compiler still schedules the surrounding arithmetic freely.
+__device__ __forceinline__ uint32_t lds32(uint32_t addr) {
+  uint32_t v;
+  asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
+  return v;
+}
+
+__device__ __forceinline__ uint4 lds128(uint32_t addr) {
+  uint4 v;
+  asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "r"(addr));
+  return v;
+}
+
+__device__ __forceinline__ void sts32(uint32_t addr, uint32_t v) {
+  asm volatile("st.shared.u32 [%0], %1;" ::"r"(addr), "r"(v));
+}
+
+__device__ __forceinline__ void sts128(uint32_t addr, uint4 v) {
+  asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v.x), "r"(v.y),
+               "r"(v.z), "r"(v.w));
+}
+
+// Read-only global loads of the per-message metadata.
+__device__ __forceinline__ uint64_t ldg_nc_u64(const uint64_t* p) { return __ldg(p); }
+__device__ __forceinline__ uint32_t ldg_nc_u32(const uint32_t* p) { return __ldg(p); }
+
+// Streaming 16-byte global store (digest slots are written once).
+__device__ __forceinline__ void stg128_cs(void* p, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+  asm volatile("st.global.cs.v4.u32 [%0], {%1, %2, %3, %4};" ::"l"(p), "r"(a), "r"(b), "r"(c),
+               "r"(d)
+               : "memory");
+}
+
+}  // namespace hb

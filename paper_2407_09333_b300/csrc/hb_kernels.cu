@@ -1,0 +1,338 @@
+// hb_kernels.cu -- every kernel of the library and its host-side launcher.
+//
+//   hb_plain_kernel    one algorithm, one message per thread, static
+//                      grid-stride over 32-message tasks (hash_batch)
+//   hb_hist_kernel     ragged path, step 1: histogram of (cost bucket, alg)
+//   hb_scan_kernel     ragged path, step 2: group starts, padding, counters
+//   hb_scatter_kernel  ragged path, step 3: message ids into their group
+//   hb_mixed_kernel    ragged path, step 4: persistent, chunks popped from a
+//                      counter longest-first (hash_batch_mixed)
+//   hb_bounds_kernel   offsets/lengths against the packed buffer size
+//   hb_int_peak_kernel integer-issue microbenchmark (measurement only)
+//   hb_selftest_wait_kernel  bounded-wait failure test
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "hb_launch.h"
+#include "hb_pipeline.cuh"
+
+namespace hb {
+
+// ---------------------------------------------------------------------------
+// Fixed-algorithm kernel.
+
+template <int ALG, int WARPS, int STAGES>
+__global__ void __launch_bounds__(WARPS * 32) hb_plain_kernel(KernelArgs a) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t warp = threadIdx.x >> 5;
+  if (a.abort_flag && *a.abort_flag) return;
+  uint8_t* wsm = smem + warp * WarpSmem<STAGES>::kBytes;
+  const uint64_t gwarp = (uint64_t)blockIdx.x * WARPS + warp;
+  const uint64_t nwarps = (uint64_t)gridDim.x * WARPS;
+  StaticSource<ALG> src(a, gwarp, nwarps, lane);
+  warp_pipeline<STAGES, ALG, false>(src, wsm, a, lane);
+}
+
+// ---------------------------------------------------------------------------
+// Ragged path: bucketing by estimated cost, then the persistent kernel.
+
+// Relative cost of one block: MD5 : SHA-1 : SM3 ~ 4 : 7 : 17 (their counted
+// 32-bit operations per block, about 330 : 610 : 1410).
+__device__ __forceinline__ uint32_t cost_group(uint32_t len, uint32_t alg) {
+  const uint32_t w = alg == HB_MD5 ? 4u : alg == HB_SHA1 ? 7u : 17u;
+  const uint32_t c = padded_blocks(len) * w;  // < 2^27 * 17 < 2^32
+  const int e = 31 - __clz(c);                // floor(log2 c), c >= 4
+  const uint32_t frac = (c >> (e - 2)) & 3u;  // two bits below the leading one
+  const uint32_t bucket = (uint32_t)e * 4u + frac;  // < kCostBuckets
+  return (kCostBuckets - 1u - bucket) * 3u + alg;   // most expensive first
+}
+
+__global__ void hb_hist_kernel(MixedArgs m) {
+  __shared__ uint32_t counts[kGroups];
+  for (uint32_t g = threadIdx.x; g < kGroups; g += blockDim.x) counts[g] = 0;
+  __syncthreads();
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m.n; i += stride) {
+    const uint32_t alg = m.algs[i];
+    if (alg <= HB_SM3) {
+      atomicAdd(&counts[cost_group(m.lengths[i], alg)], 1u);
+    } else {
+      // Unknown code: the slot stays all zero and the message is not hashed.
+      uint8_t* dst = m.digests + i * HB_SLOT_BYTES;
+      stg128_cs(dst, 0, 0, 0, 0);
+      stg128_cs(dst + 16, 0, 0, 0, 0);
+    }
+  }
+  __syncthreads();
+  for (uint32_t g = threadIdx.x; g < kGroups; g += blockDim.x)
+    if (counts[g]) atomicAdd(&m.ws->counts[g], counts[g]);
+}
+
+// One block of kGroups threads.  Groups are laid out in group order, each
+// padded to a multiple of 32 so that every chunk holds a single algorithm
+// and starts with a real message.
+__global__ void hb_scan_kernel(MixedArgs m) {
+  __shared__ uint32_t padded[kGroups];
+  const uint32_t g = threadIdx.x;
+  const uint32_t cnt = m.ws->counts[g];
+  padded[g] = (cnt + 31u) & ~31u;
+  __syncthreads();
+  if (g == 0) {
+    uint32_t run = 0;
+    for (uint32_t k = 0; k < kGroups; ++k) {
+      const uint32_t p = padded[k];
+      padded[k] = run;
+      run += p;
+    }
+    m.ws->nchunks = run / 32u;
+    m.ws->chunk_counter = 0u;
+  }
+  __syncthreads();
+  const uint32_t start = padded[g];
+  m.ws->cursor[g] = start;
+  const uint32_t end = start + ((cnt + 31u) & ~31u);
+  for (uint32_t k = start + cnt; k < end; ++k) m.perm[k] = 0xFFFFFFFFu;
+}
+
+__global__ void hb_scatter_kernel(MixedArgs m) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t n_up = (m.n + 31u) & ~31ull;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_up; i += stride) {
+    uint32_t key = 0xFFFFFFFFu;
+    if (i < m.n) {
+      const uint32_t alg = m.algs[i];
+      if (alg <= HB_SM3) key = cost_group(m.lengths[i], alg);
+    }
+    // Warp-aggregated reservation: one atomic per distinct group in the warp.
+    const uint32_t peers = __match_any_sync(kFull, key);
+    const uint32_t leader = __ffs(peers) - 1u;
+    const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
+    uint32_t base = 0;
+    if (key != 0xFFFFFFFFu && lane == leader) base = atomicAdd(&m.ws->cursor[key], __popc(peers));
+    base = __shfl_sync(kFull, base, leader);
+    if (key != 0xFFFFFFFFu) m.perm[base + rank] = (uint32_t)i;
+  }
+}
+
+template <int WARPS, int STAGES>
+__global__ void __launch_bounds__(WARPS * 32) hb_mixed_kernel(KernelArgs a) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t warp = threadIdx.x >> 5;
+  if (a.abort_flag && *a.abort_flag) return;
+  uint8_t* wsm = smem + warp * WarpSmem<STAGES>::kBytes;
+  DynamicSource src(a, lane);
+  warp_pipeline<STAGES, HB_MD5, true>(src, wsm, a, lane);
+}
+
+// ---------------------------------------------------------------------------
+// Bounds check (never traps; reports through status words).
+
+__global__ void hb_bounds_kernel(const uint64_t* offsets, const uint32_t* lengths, uint64_t n,
+                                 uint64_t packed_len, int* status_dev, int* ctx_status) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  bool bad = false;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const uint64_t o = offsets[i];
+    const uint64_t l = lengths[i];
+    bad |= (o > packed_len) || (l > packed_len - o);
+  }
+  if (bad) {
+    if (status_dev) atomicOr(status_dev, HB_DEV_BOUNDS);
+    if (ctx_status) atomicOr(ctx_status, HB_DEV_BOUNDS);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Integer issue microbenchmark: eight independent chains per thread, four
+// unrolled steps per iteration, one 32-bit operation per chain per step.
+
+template <int OP>
+__device__ __forceinline__ uint32_t peak_op(uint32_t x, uint32_t y, uint32_t z) {
+  if constexpr (OP == 0) return lop3<0x96>(x, y, z);
+  else if constexpr (OP == 1) return x + y + z;
+  else if constexpr (OP == 2) return __funnelshift_l(x, y, 7);
+  else if constexpr (OP == 3) return __byte_perm(x, y, 0x6351);
+  else if constexpr (OP == 5) return x * y + z;
+  else return x;
+}
+
+template <int OP>
+__global__ void hb_int_peak_kernel(int iters, unsigned long long* cycles, uint32_t* sink) {
+  uint32_t x[8];
+  const uint32_t seed = threadIdx.x * 2654435761u + blockIdx.x;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) x[k] = seed ^ (0x9e3779b9u * (k + 1));
+  const uint32_t z = seed | 1u;
+  __syncthreads();
+  const unsigned long long t0 = clock64();
+#pragma unroll 1
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        if constexpr (OP == 4) {
+          // LOP3, IADD3 and SHF in rotation.
+          const int m = (u * 8 + k) % 3;
+          if (m == 0) x[k] = lop3<0x96>(x[k], x[(k + 1) & 7], z);
+          else if (m == 1) x[k] = x[k] + x[(k + 1) & 7] + z;
+          else x[k] = __funnelshift_l(x[k], x[(k + 1) & 7], 7);
+        } else if constexpr (OP == 6) {
+          // LOP3 and IMAD alternating (ALU and multiply-add pipes).
+          if ((u * 8 + k) & 1) x[k] = x[k] * x[(k + 1) & 7] + z;
+          else x[k] = lop3<0x96>(x[k], x[(k + 1) & 7], z);
+        } else {
+          x[k] = peak_op<OP>(x[k], x[(k + 1) & 7], z);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  const unsigned long long t1 = clock64();
+  uint32_t acc = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) acc ^= x[k];
+  if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
+  if (acc == 0x12345678u) sink[0] = acc;  // keeps the chains alive
+}
+
+// ---------------------------------------------------------------------------
+// Failure-detection self test: a wait on a barrier phase nobody completes.
+
+__global__ void hb_selftest_wait_kernel(uint64_t limit_ns, int* status) {
+  __shared__ __align__(8) uint64_t bar;
+  const uint32_t addr = smem_addr(&bar);
+  if (threadIdx.x == 0) {
+    mbar_init(addr, 1);
+    fence_barrier_init();
+  }
+  __syncwarp();
+  mbar_wait_bounded(addr, 0, limit_ns, status);
+}
+
+// ---------------------------------------------------------------------------
+// Launch shapes and host launchers.
+
+struct ShapeDesc {
+  int warps, stages;
+};
+static const ShapeDesc kShapes[] = {{4, 4}, {4, 2}, {8, 3}, {1, 4}, {2, 3}, {16, 2}};
+static constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
+
+using KernelFn = void (*)(KernelArgs);
+
+template <int ALG>
+static KernelFn plain_fn(int shape) {
+  switch (shape) {
+    case 0: return hb_plain_kernel<ALG, 4, 4>;
+    case 1: return hb_plain_kernel<ALG, 4, 2>;
+    case 2: return hb_plain_kernel<ALG, 8, 3>;
+    case 3: return hb_plain_kernel<ALG, 1, 4>;
+    case 4: return hb_plain_kernel<ALG, 2, 3>;
+    case 5: return hb_plain_kernel<ALG, 16, 2>;
+    default: return nullptr;
+  }
+}
+
+static KernelFn mixed_fn(int shape) {
+  switch (shape) {
+    case 0: return hb_mixed_kernel<4, 4>;
+    case 1: return hb_mixed_kernel<4, 2>;
+    case 2: return hb_mixed_kernel<8, 3>;
+    case 3: return hb_mixed_kernel<1, 4>;
+    case 4: return hb_mixed_kernel<2, 3>;
+    case 5: return hb_mixed_kernel<16, 2>;
+    default: return nullptr;
+  }
+}
+
+static int shape_smem(int shape) {
+  const ShapeDesc d = kShapes[shape];
+  switch (d.stages) {
+    case 2: return d.warps * WarpSmem<2>::kBytes;
+    case 3: return d.warps * WarpSmem<3>::kBytes;
+    default: return d.warps * WarpSmem<4>::kBytes;
+  }
+}
+
+int num_shapes() { return kNumShapes; }
+
+bool shape_desc(int shape, int* warps, int* stages) {
+  if (shape < 0 || shape >= kNumShapes) return false;
+  *warps = kShapes[shape].warps;
+  *stages = kShapes[shape].stages;
+  return true;
+}
+
+int shape_smem_bytes(int shape) { return shape_smem(shape); }
+
+static KernelFn pick(bool mixed, int alg, int shape) {
+  if (mixed) return mixed_fn(shape);
+  switch (alg) {
+    case HB_MD5: return plain_fn<HB_MD5>(shape);
+    case HB_SHA1: return plain_fn<HB_SHA1>(shape);
+    case HB_SM3: return plain_fn<HB_SM3>(shape);
+    default: return nullptr;
+  }
+}
+
+cudaError_t prepare_kernel(bool mixed, int alg, int shape, int* blocks_per_sm) {
+  KernelFn fn = pick(mixed, alg, shape);
+  if (!fn) return cudaErrorInvalidValue;
+  const int smem = shape_smem(shape);
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, kShapes[shape].warps * 32,
+                                                       smem);
+}
+
+cudaError_t launch_hash(bool mixed, int alg, int shape, int grid, const KernelArgs& a,
+                        cudaStream_t stream) {
+  KernelFn fn = pick(mixed, alg, shape);
+  if (!fn || grid <= 0) return cudaErrorInvalidValue;
+  fn<<<grid, kShapes[shape].warps * 32, shape_smem(shape), stream>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bucketing(const MixedArgs& m, int grid, cudaStream_t stream) {
+  cudaError_t e = cudaMemsetAsync(m.ws->counts, 0, sizeof(m.ws->counts), stream);
+  if (e != cudaSuccess) return e;
+  hb_hist_kernel<<<grid, 256, 0, stream>>>(m);
+  hb_scan_kernel<<<1, kGroups, 0, stream>>>(m);
+  hb_scatter_kernel<<<grid, 256, 0, stream>>>(m);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bounds(const uint64_t* offsets, const uint32_t* lengths, uint64_t n,
+                          uint64_t packed_len, int* status_dev, int* ctx_status, int grid,
+                          cudaStream_t stream) {
+  hb_bounds_kernel<<<grid, 256, 0, stream>>>(offsets, lengths, n, packed_len, status_dev,
+                                             ctx_status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_int_peak(int op, int blocks, int threads, int iters, unsigned long long* cycles,
+                            uint32_t* sink, cudaStream_t stream) {
+  switch (op) {
+    case 0: hb_int_peak_kernel<0><<<blocks, threads, 0, stream>>>(iters, cycles, sink); break;
+    case 1: hb_int_peak_kernel<1><<<blocks, threads, 0, stream>>>(iters, cycles, sink); break;
+    case 2: hb_int_peak_kernel<2><<<blocks, threads, 0, stream>>>(iters, cycles, sink); break;
+    case 3: hb_int_peak_kernel<3><<<blocks, threads, 0, stream>>>(iters, cycles, sink); break;
+    case 4: hb_int_peak_kernel<4><<<blocks, threads, 0, stream>>>(iters, cycles, sink); break;
+    case 5: hb_int_peak_kernel<5><<<blocks, threads, 0, stream>>>(iters, cycles, sink); break;
+    case 6: hb_int_peak_kernel<6><<<blocks, threads, 0, stream>>>(iters, cycles, sink); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_selftest_wait(uint64_t limit_ns, int* status, cudaStream_t stream) {
+  hb_selftest_wait_kernel<<<1, 32, 0, stream>>>(limit_ns, status);
+  return cudaGetLastError();
+}
+
+}  // namespace hb

@@ -1,0 +1,73 @@
+// hb_launch.h -- internal interface between the kernels (hb_kernels.cu) and
+// the C-ABI layer (hb_capi.cu).  Not installed; not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "hashbatch.h"
+
+namespace hb {
+
+// Kernel arguments for the hashing kernels (plain and mixed).
+struct KernelArgs {
+  const uint8_t* packed;
+  const uint64_t* offsets;
+  const uint32_t* lengths;
+  const uint8_t* algs;        // mixed path only
+  const uint32_t* perm;       // mixed path only: chunk slot -> message index
+  uint32_t* chunk_counter;    // mixed path only
+  const uint32_t* nchunks;    // mixed path only
+  uint64_t n;
+  uint8_t* digests;
+  int* status;                // per-device status word (HB_DEV_* bits)
+  const int* abort_flag;      // optional: skip all work when *abort_flag != 0
+  uint64_t wait_limit_ns;
+};
+
+// Ragged-path bucketing: groups are (cost bucket, algorithm) pairs ordered
+// from the most to the least expensive estimated work per message.
+constexpr uint32_t kCostBuckets = 128;
+constexpr uint32_t kGroups = kCostBuckets * 3;
+
+// Device scratch of the ragged path; followed in memory by the permutation
+// array of (n + 31 * kGroups) uint32 entries.
+struct MixedWorkspace {
+  uint32_t counts[kGroups];
+  uint32_t cursor[kGroups];
+  uint32_t chunk_counter;
+  uint32_t nchunks;
+  uint32_t pad[30];
+};
+
+inline size_t mixed_workspace_bytes(uint64_t n) {
+  return sizeof(MixedWorkspace) + (size_t)(n + 31ull * kGroups) * sizeof(uint32_t);
+}
+
+struct MixedArgs {
+  const uint8_t* algs;
+  const uint32_t* lengths;
+  uint64_t n;
+  uint8_t* digests;
+  MixedWorkspace* ws;
+  uint32_t* perm;
+};
+
+int num_shapes();
+bool shape_desc(int shape, int* warps, int* stages);
+int shape_smem_bytes(int shape);
+
+// Sets the kernel's shared-memory attribute and returns its occupancy.
+cudaError_t prepare_kernel(bool mixed, int alg, int shape, int* blocks_per_sm);
+cudaError_t launch_hash(bool mixed, int alg, int shape, int grid, const KernelArgs& a,
+                        cudaStream_t stream);
+cudaError_t launch_bucketing(const MixedArgs& m, int grid, cudaStream_t stream);
+cudaError_t launch_bounds(const uint64_t* offsets, const uint32_t* lengths, uint64_t n,
+                          uint64_t packed_len, int* status_dev, int* ctx_status, int grid,
+                          cudaStream_t stream);
+cudaError_t launch_int_peak(int op, int blocks, int threads, int iters, unsigned long long* cycles,
+                            uint32_t* sink, cudaStream_t stream);
+cudaError_t launch_selftest_wait(uint64_t limit_ns, int* status, cudaStream_t stream);
+
+}  // namespace hb

@@ -46,9 +46,11 @@ class Batch:
 
 
 def _random_bytes(rng: np.random.Generator, size: int) -> np.ndarray:
+    """`size` uniform random bytes: the raw 64-bit PCG64 outputs, little-endian."""
     if size == 0:
         return np.zeros(0, dtype=np.uint8)
-    return np.frombuffer(rng.bytes(size), dtype=np.uint8).copy()
+    words = rng.bit_generator.random_raw((size + 7) // 8)
+    return words.view(np.uint8)[:size]
 
 
 def fixed(n: int, length: int, seed: int) -> Batch:

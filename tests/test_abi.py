@@ -1,0 +1,92 @@
+"""The C-ABI library loads and exports every symbol include/hashbatch.h
+declares; argument checks that return before any CUDA call behave as
+documented.  No GPU needed."""
+import ctypes
+
+import pytest
+
+from paper_2407_09333_b300 import api
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2407_09333_b300 import build
+    build.build()
+    return api.lib()
+
+
+def test_every_declared_function_is_exported(lib):
+    names = api.header_functions()
+    assert len(names) >= 15
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+    # and the binding declares a signature for each of them
+    assert set(names) <= set(api._SIGNATURES), set(names) - set(api._SIGNATURES)
+
+
+def test_digest_sizes_and_strerror(lib):
+    assert [api.digest_size(a) for a in (0, 1, 2, 3, -1)] == [16, 20, 32, 0, 0]
+    for code in range(0, -11, -1):
+        assert lib.hash_strerror(code)
+    assert api.strerror(-1) == "invalid algorithm code"
+    assert api.strerror(-99) == "unknown error code"
+
+
+def test_argument_checks_before_cuda(lib):
+    buf = ctypes.create_string_buffer(64)
+    p = ctypes.c_void_p(ctypes.addressof(buf))
+    # invalid algorithm
+    assert lib.hash_batch(3, p, p, p, 1, p, None) == -1
+    assert lib.hash_batch(-1, p, p, p, 1, p, None) == -1
+    # empty batch is a no-op even with null pointers
+    assert lib.hash_batch(0, None, None, None, 0, None, None) == 0
+    assert lib.hash_batch_mixed(None, None, None, None, 0, None, None) == 0
+    # null pointers
+    assert lib.hash_batch(0, None, p, p, 1, p, None) == -2
+    assert lib.hash_batch(1, p, None, p, 1, p, None) == -2
+    assert lib.hash_batch(2, p, p, None, 1, p, None) == -2
+    assert lib.hash_batch(2, p, p, p, 1, None, None) == -2
+    assert lib.hash_batch_mixed(None, p, p, p, 1, p, None) == -2
+    # digest slots must be 16-byte aligned
+    odd = ctypes.c_void_p(((ctypes.addressof(buf) + 15) & ~15) + 4)
+    assert lib.hash_batch(0, p, p, p, 1, odd, None) == -7
+    # size limits
+    assert lib.hash_batch(0, p, p, p, 1 << 40, p, None) == -3
+    assert lib.hash_batch_mixed(p, p, p, p, 1 << 31, p, None) == -3
+    # host path argument checks
+    assert lib.hash_batch_host(5, None, p, 1, p, p, 1, p, None) == -1
+    assert lib.hash_batch_host(0, None, p, 1, None, p, 1, p, None) == -2
+    assert lib.hash_batch_host(0, None, None, 0, None, None, 0, None, None) == 0
+
+
+def test_tuning_shape_table(lib):
+    n = lib.hash_tune_shapes()
+    assert n >= 4
+    w, s = ctypes.c_int(), ctypes.c_int()
+    for i in range(n):
+        assert lib.hash_tune_shape(i, ctypes.byref(w), ctypes.byref(s)) == 0
+        assert w.value in (1, 2, 4, 8, 16) and 2 <= s.value <= 4
+    assert lib.hash_tune_shape(n, ctypes.byref(w), ctypes.byref(s)) == -10
+    assert lib.hash_tune_set(0, n) == -10
+    assert lib.hash_tune_set(7, 0) == -1
+
+
+def test_int_peak_argument_checks(lib):
+    assert lib.hash_int_peak(0, 1, 32, 1, None, None, None) == -2
+    buf = ctypes.create_string_buffer(64)
+    p = ctypes.c_void_p(ctypes.addressof(buf))
+    assert lib.hash_int_peak(0, 0, 32, 1, p, p, None) == -10
+    assert lib.hash_int_peak(0, 1, 2048, 1, p, p, None) == -10
+    assert lib.hash_int_peak_ops_per_iter() == 32
+
+
+def test_product_path_does_not_import_oracle():
+    import paper_2407_09333_b300
+    import os
+    pkg = os.path.dirname(paper_2407_09333_b300.__file__)
+    for root, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                text = open(os.path.join(root, f)).read()
+                assert "import oracle" not in text and "from oracle" not in text, f
+                assert "hash_oracle" not in text and "liboracle" not in text, f

@@ -1,0 +1,236 @@
+"""Parity of the CUDA path with the CPU oracle, slot by slot, bit-exact.
+
+Digests are integer results with one correct value each, so the tolerance is
+zero: every byte of every 32-byte slot (digest, then zero fill) must match.
+Small cases are compared in full; the full-size batches (2^22 x 55 B,
+65536 x 16 KiB, 2^20 ragged) are compared on seeded samples that the oracle
+digests one message at a time, in the launch configuration the benchmark uses.
+"""
+import numpy as np
+import pytest
+
+from paper_2407_09333_b300 import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+ALGS = (0, 1, 2)
+
+
+@pytest.fixture(scope="module")
+def hb():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2407_09333_b300 import api, build
+    build.build()
+    api.lib()
+    return api
+
+
+def _oracle_slots(oracle_mod, batch, alg, idx=None):
+    if idx is None:
+        return oracle_mod.hash_batch(alg, batch.packed, batch.offsets, batch.lengths,
+                                     algs=batch.algs, threads=oracle_mod.host_threads())
+    algs = batch.algs[idx] if batch.algs is not None else None
+    return oracle_mod.hash_batch(alg, batch.packed, batch.offsets[idx], batch.lengths[idx],
+                                 algs=algs, threads=oracle_mod.host_threads())
+
+
+def _gpu_slots(hb, batch, alg, shape=-1, mixed=False):
+    packed, offsets, lengths, algs = hb.to_device(batch)
+    if mixed:
+        out = hb.hash_batch_mixed(algs, packed, offsets, lengths, shape=shape)
+    else:
+        out = hb.hash_batch(alg, packed, offsets, lengths, shape=shape)
+    torch.cuda.synchronize()
+    assert hb.device_status() == 0
+    return out.cpu().numpy()
+
+
+def _assert_slots_equal(got, want, where):
+    if not np.array_equal(got, want):
+        bad = np.nonzero((got != want).any(axis=1))[0]
+        raise AssertionError("%s: %d of %d slots differ, first at %s" % (where, bad.size, len(want), bad[:8]))
+
+
+@pytest.mark.parametrize("alg", ALGS)
+def test_4096_by_64_bytes_seed0(hb, oracle_mod, alg):
+    b = workloads.fixed(4096, 64, seed=0)
+    _assert_slots_equal(_gpu_slots(hb, b, alg), _oracle_slots(oracle_mod, b, alg), "4096x64")
+
+
+@pytest.mark.parametrize("alg", ALGS)
+def test_every_length_0_to_300_packed_unaligned(hb, oracle_mod, alg):
+    lens = list(range(0, 301)) + [511, 512, 513, 1000, 1023, 1024, 1025, 4095, 4096, 4097]
+    b = workloads.scattered(lens, seed=11 + alg, overlap=False)
+    _assert_slots_equal(_gpu_slots(hb, b, alg), _oracle_slots(oracle_mod, b, alg), "lengths")
+
+
+@pytest.mark.parametrize("alg", ALGS)
+def test_overlapping_unaligned_messages_all_shapes(hb, oracle_mod, alg):
+    rng = np.random.default_rng(100 + alg)
+    lens = rng.integers(0, 3000, size=1000)
+    lens[:7] = workloads.BOUNDARY_LENGTHS
+    b = workloads.scattered(lens, seed=21 + alg, overlap=True)
+    want = _oracle_slots(oracle_mod, b, alg)
+    for shape in range(len(hb.shapes())):
+        _assert_slots_equal(_gpu_slots(hb, b, alg, shape=shape), want, "shape %d" % shape)
+
+
+@pytest.mark.parametrize("n", [1, 2, 31, 32, 33, 63, 65, 1000, 4097])
+def test_ragged_warp_tails(hb, oracle_mod, n):
+    b = workloads.fixed(n, 57, seed=n)
+    for alg in ALGS:
+        _assert_slots_equal(_gpu_slots(hb, b, alg), _oracle_slots(oracle_mod, b, alg), "n=%d" % n)
+
+
+def test_long_messages(hb, oracle_mod):
+    lens = [16384, 65536, 65537, 1 << 20, 100003, 0, 55, 120]
+    b = workloads.scattered(lens, seed=5, overlap=False)
+    for alg in ALGS:
+        _assert_slots_equal(_gpu_slots(hb, b, alg), _oracle_slots(oracle_mod, b, alg), "long")
+
+
+def test_nine_digit_messages(hb, oracle_mod):
+    b = workloads.digits9(5000, first=999_995_000)   # wraps past 999999999
+    for alg in ALGS:
+        _assert_slots_equal(_gpu_slots(hb, b, alg), _oracle_slots(oracle_mod, b, alg), "digits9")
+
+
+def test_empty_batch_is_noop(hb):
+    packed = torch.zeros(16, dtype=torch.uint8, device="cuda")
+    off = torch.zeros(0, dtype=torch.int64, device="cuda")
+    ln = torch.zeros(0, dtype=torch.int32, device="cuda")
+    out = hb.hash_batch(0, packed, off, ln)
+    assert out.shape == (0, 32)
+    out = hb.hash_batch_mixed(torch.zeros(0, dtype=torch.uint8, device="cuda"), packed, off, ln)
+    assert out.shape == (0, 32)
+
+
+def test_deterministic_and_same_alone_as_in_batch(hb, oracle_mod):
+    b = workloads.scattered(np.arange(0, 700, 7), seed=3, overlap=True)
+    g1 = _gpu_slots(hb, b, 2)
+    g2 = _gpu_slots(hb, b, 2)
+    assert np.array_equal(g1, g2)
+    for i in (0, 17, 50, 99):
+        one = workloads.Batch(b.packed, b.offsets[i:i + 1].copy(), b.lengths[i:i + 1].copy())
+        assert np.array_equal(_gpu_slots(hb, one, 2)[0], g1[i])
+
+
+# ---------------------------------------------------------------------------
+# mixed / ragged path
+
+def test_mixed_small_full_compare(hb, oracle_mod):
+    b = workloads.ragged(20000, seed=7, max_len=8192)
+    want = _oracle_slots(oracle_mod, b, None)
+    _assert_slots_equal(_gpu_slots(hb, b, None, mixed=True), want, "mixed")
+
+
+def test_mixed_all_shapes_and_invalid_codes(hb, oracle_mod):
+    lens = np.random.default_rng(9).integers(0, 2000, size=3000)
+    b = workloads.scattered(lens, seed=9, overlap=True, mixed=True)
+    b.algs[::97] = 7          # unknown algorithm code: slot must stay zero
+    ok = b.algs <= 2
+    want = np.zeros((b.n, 32), dtype=np.uint8)
+    idx = np.nonzero(ok)[0]
+    want[idx] = _oracle_slots(oracle_mod, b, None, idx)
+    for shape in range(len(hb.shapes())):
+        _assert_slots_equal(_gpu_slots(hb, b, None, shape=shape, mixed=True), want, "shape %d" % shape)
+
+
+def test_mixed_matches_single_algorithm_path(hb):
+    b = workloads.ragged(5000, seed=8, max_len=4096)
+    mixed = _gpu_slots(hb, b, None, mixed=True)
+    for alg in ALGS:
+        sel = np.nonzero(b.algs == alg)[0]
+        sub = workloads.Batch(b.packed, b.offsets[sel], b.lengths[sel])
+        _assert_slots_equal(mixed[sel], _gpu_slots(hb, sub, alg), "alg %d" % alg)
+
+
+# ---------------------------------------------------------------------------
+# host-buffer path, bounds, failure detection
+
+def test_host_path_plain_and_mixed(hb, oracle_mod):
+    b = workloads.scattered(np.arange(0, 400), seed=4, overlap=True, mixed=True)
+    out = np.zeros((b.n, 32), dtype=np.uint8)
+    hb.hash_batch_host(None, b.packed, b.offsets, b.lengths, out, algs=b.algs)
+    _assert_slots_equal(out, _oracle_slots(oracle_mod, b, None), "host mixed")
+    plain = workloads.fixed(1000, 55, seed=1)
+    out = np.zeros((plain.n, 32), dtype=np.uint8)
+    hb.hash_batch_host(1, plain.packed, plain.offsets, plain.lengths, out)
+    _assert_slots_equal(out, _oracle_slots(oracle_mod, plain, 1), "host plain")
+
+
+def test_host_path_rejects_out_of_bounds(hb):
+    b = workloads.fixed(100, 40, seed=2)
+    offs = b.offsets.copy()
+    offs[50] = b.packed.size - 10          # runs 30 bytes past the end
+    out = np.zeros((b.n, 32), dtype=np.uint8)
+    with pytest.raises(hb.HashBatchError) as e:
+        hb.hash_batch_host(0, b.packed, offs, b.lengths, out)
+    assert e.value.code == -8
+    # the library stays usable
+    hb.hash_batch_host(0, b.packed, b.offsets, b.lengths, out)
+
+
+def test_check_bounds(hb):
+    b = workloads.fixed(1000, 33, seed=6)
+    _, off, ln, _ = hb.to_device(b)
+    st = hb.check_bounds(off, ln, b.packed.size)
+    assert int(st.item()) == 0
+    st = hb.check_bounds(off, ln, b.packed.size - 1)
+    assert int(st.item()) == hb.DEV_BOUNDS
+    assert hb.device_status() & hb.DEV_BOUNDS
+    assert hb.device_status() == 0        # cleared by the previous read
+
+
+def test_bounded_wait_reports_timeout_and_context_survives(hb, oracle_mod):
+    hb.device_status()
+    hb.selftest_wait_timeout(20_000_000)   # 20 ms on a phase nothing completes
+    assert hb.device_status() == hb.DEV_TIMEOUT
+    b = workloads.fixed(64, 100, seed=12)
+    _assert_slots_equal(_gpu_slots(hb, b, 0), _oracle_slots(oracle_mod, b, 0), "after timeout")
+
+
+# ---------------------------------------------------------------------------
+# full-size batches, sampled
+
+def _sample(n, k, seed):
+    rng = np.random.default_rng(seed)
+    idx = np.unique(np.concatenate([np.arange(min(n, 256)), np.arange(max(0, n - 256), n),
+                                    rng.integers(0, n, size=k)]))
+    return idx
+
+
+def test_full_size_2pow22_by_55_sampled(hb, oracle_mod):
+    b = workloads.fixed(1 << 22, 55, seed=1)
+    packed, off, ln, _ = hb.to_device(b)
+    idx = _sample(b.n, 20000, 1)
+    for alg in ALGS:
+        out = hb.hash_batch(alg, packed, off, ln)
+        got = out[torch.from_numpy(idx).cuda()].cpu().numpy()
+        _assert_slots_equal(got, _oracle_slots(oracle_mod, b, alg, idx), "C2 alg %d" % alg)
+    assert hb.device_status() == 0
+
+
+def test_full_size_65536_by_16KiB_sampled(hb, oracle_mod):
+    b = workloads.fixed(65536, 16384, seed=3)
+    packed, off, ln, _ = hb.to_device(b)
+    idx = _sample(b.n, 1500, 3)
+    for alg in ALGS:
+        out = hb.hash_batch(alg, packed, off, ln)
+        got = out[torch.from_numpy(idx).cuda()].cpu().numpy()
+        _assert_slots_equal(got, _oracle_slots(oracle_mod, b, alg, idx), "C4 alg %d" % alg)
+
+
+def test_full_size_ragged_2pow20_sampled(hb, oracle_mod):
+    b = workloads.ragged(1 << 20, seed=2)
+    packed, off, ln, algs = hb.to_device(b)
+    out = hb.hash_batch_mixed(algs, packed, off, ln)
+    idx = _sample(b.n, 6000, 2)
+    # all forced boundary-length messages too
+    bl = np.nonzero(np.isin(b.lengths, workloads.BOUNDARY_LENGTHS))[0]
+    idx = np.unique(np.concatenate([idx, bl]))
+    got = out[torch.from_numpy(idx).cuda()].cpu().numpy()
+    _assert_slots_equal(got, _oracle_slots(oracle_mod, b, None, idx), "C3")
+    assert hb.device_status() == 0
