@@ -73,53 +73,105 @@ def alu_peak_tops(sms: int, sm_mhz: float, lanes_per_sm: int = 128) -> float:
 # clocks during the timed region (NVML reads only; no setting is changed)
 
 class ClockSampler:
+    """Samples the SM clock and the clock-event reasons while the timed region
+    runs: NVML reads from a thread, else `nvidia-smi -lms` in the background.
+    Nothing is set; settings are only read."""
     REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
                0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown",
-               0x2: "applications_clocks_setting", 0x1: "gpu_idle"}
+               0x2: "applications_clocks_setting"}
 
     def __init__(self, device_index: int, period_s: float = 0.005):
         self.period = period_s
+        self.device_index = device_index
         self.samples = []
         self.reasons = 0
         self.max_mhz = None
+        self.error = None
+        self.source = "nvml"
         self._stop = threading.Event()
         self._thread = None
+        self._proc = None
+        self._nvml = None
         try:
             import pynvml
             pynvml.nvmlInit()
+            self._h = self._handle(pynvml, device_index)
+            self.max_mhz = float(pynvml.nvmlDeviceGetMaxClockInfo(self._h, pynvml.NVML_CLOCK_SM))
             self._nvml = pynvml
-            self._h = pynvml.nvmlDeviceGetHandleByIndex(device_index)
-            self.max_mhz = pynvml.nvmlDeviceGetMaxClockInfo(self._h, pynvml.NVML_CLOCK_SM)
+        except Exception as e:  # fall back to nvidia-smi
+            self.error = "nvml: %s" % (e,)
+            self.source = "nvidia-smi"
+
+    @staticmethod
+    def _handle(nv, device_index):
+        """NVML handle of the CUDA device (matched by UUID: NVML numbers all
+        GPUs of the machine, CUDA only the visible ones)."""
+        try:
+            import torch
+            uuid = str(torch.cuda.get_device_properties(device_index).uuid)
+            return nv.nvmlDeviceGetHandleByUUID(uuid if uuid.startswith("GPU-") else "GPU-" + uuid)
         except Exception:
-            self._nvml = None
+            return nv.nvmlDeviceGetHandleByIndex(device_index)
+
+    def _reasons_now(self):
+        nv = self._nvml
+        fn = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            getattr(nv, "nvmlDeviceGetCurrentClocksThrottleReasons")
+        return fn(self._h)
 
     def _run(self):
         nv = self._nvml
         while not self._stop.is_set():
             try:
-                self.samples.append(nv.nvmlDeviceGetClockInfo(self._h, nv.NVML_CLOCK_SM))
-                self.reasons |= nv.nvmlDeviceGetCurrentClocksEventReasons(self._h)
-            except Exception:
-                pass
+                self.samples.append(float(nv.nvmlDeviceGetClockInfo(self._h, nv.NVML_CLOCK_SM)))
+                self.reasons |= int(self._reasons_now())
+            except Exception as e:
+                self.error = "nvml sample: %s" % (e,)
             time.sleep(self.period)
 
     def __enter__(self):
         if self._nvml is not None:
             self._thread = threading.Thread(target=self._run, daemon=True)
             self._thread.start()
+        else:
+            import subprocess
+            import tempfile
+            self._tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            try:
+                self._proc = subprocess.Popen(
+                    ["nvidia-smi", "-i", str(self.device_index),
+                     "--query-gpu=clocks.sm,clocks.max.sm,clocks_event_reasons.active",
+                     "--format=csv,noheader,nounits", "-lms", "100"],
+                    stdout=self._tmp, stderr=subprocess.DEVNULL)
+            except OSError as e:
+                self.error = "%s; nvidia-smi: %s" % (self.error, e)
         return self
 
     def __exit__(self, *exc):
         self._stop.set()
         if self._thread:
             self._thread.join()
+        if self._proc is not None:
+            self._proc.terminate()
+            self._proc.wait()
+            self._tmp.seek(0)
+            for row in self._tmp.read().splitlines():
+                parts = [x.strip() for x in row.split(",")]
+                try:
+                    self.samples.append(float(parts[0]))
+                    self.max_mhz = float(parts[1])
+                    self.reasons |= int(parts[2], 16)
+                except (ValueError, IndexError):
+                    pass
 
     def summary(self):
-        if not self.samples:
-            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": [], "samples": 0}
-        reasons = [name for bit, name in self.REASONS.items() if self.reasons & bit and bit != 0x1]
-        return {"sm_mhz": float(statistics.median(self.samples)), "sm_max_mhz": self.max_mhz,
-                "reasons": reasons, "samples": len(self.samples)}
+        reasons = [name for bit, name in self.REASONS.items() if self.reasons & bit]
+        out = {"sm_mhz": float(statistics.median(self.samples)) if self.samples else None,
+               "sm_max_mhz": self.max_mhz, "reasons": reasons, "samples": len(self.samples),
+               "source": self.source}
+        if self.error and not self.samples:
+            out["error"] = self.error
+        return out
 
 
 # ---------------------------------------------------------------------------
@@ -303,6 +355,14 @@ def run_ours(args, dist):
     props = torch.cuda.get_device_properties(torch.cuda.current_device())
     sms = props.multi_processor_count
 
+    from paper_2407_09333_b300 import autotune
+    tuned = {}
+    mean_len = batch.total_bytes / max(n, 1)
+    for a in ([None] if mixed else [0, 1, 2]):
+        r = autotune.tune(a, packed, off, ln, out, algs=algs, mean_len=mean_len)
+        tuned["mixed" if a is None else ALG_NAMES[a]] = {"warps": r["warps"], "stages": r["stages"],
+                                                          "cached": r["cached"]}
+
     if mixed:
         launches = [(None, lambda: api.hash_batch_mixed(algs, packed, off, ln, out=out))]
         bytes_per_step = batch.total_bytes
@@ -392,6 +452,7 @@ def run_ours(args, dist):
                    "parallelism": "dp%d: disjoint message shards, no collective on the data path" % dist.world},
         "mhash_per_s": dist.world * msgs_per_step * args.steps / (ms * 1e-3) / 1e6,
         "per_alg": per_alg,
+        "tuned_shapes": tuned,
         "roofline": roofline,
         "gpu_launches": args.steps * nl * (4 if mixed else 1),
         "clocks": clk,
@@ -435,22 +496,55 @@ def e2e_measure(args, batch, mixed, api, torch):
             "api": "hash_batch_host (pinned host buffers)"}
 
 
+def run_int_peak(args, dist):
+    """K5: sustained 32-bit operations per clock per SM for each op class."""
+    import torch
+    from paper_2407_09333_b300 import api, build
+
+    build.build()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    names = ["LOP3", "IADD3", "SHF", "PRMT", "LOP3/IADD3/SHF", "IMAD", "LOP3/IMAD", "IADD3/IMAD",
+             "SHF/IMAD", "LOP3/FFMA", "IMAD-add", "LOP3/IMAD-add", "LOP3/SHF/IADD3/IMAD-add"]
+    threads, iters = 512, 4000
+    blocks = sms * 4
+    res = {}
+    for op, name in enumerate(names):
+        api.int_peak(op, blocks, threads, 200)
+        torch.cuda.synchronize()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        cyc = api.int_peak(op, blocks, threads, iters)
+        e.record()
+        e.synchronize()
+        ms = s.elapsed_time(e)
+        ops = blocks * threads * iters * api.int_peak_ops_per_iter()
+        cmax = int(cyc.max().item())
+        res[name] = {"ops_per_clk_per_sm": ops / cmax / sms, "tops": ops / ms / 1e9,
+                     "clock_mhz": cmax / ms / 1e3}
+    print(json.dumps({"int_peak": res, "sms": sms, "blocks": blocks, "threads": threads,
+                      "iters": iters, "ops_per_iter": api.int_peak_ops_per_iter()}), flush=True)
+
+
 def main(argv=None):
     p = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--steps", type=int, default=2000)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4"])
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--e2e-steps", type=int, default=10)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--int-peak", action="store_true",
+                   help="run the integer-issue microbenchmark instead of the hashing step")
     args = p.parse_args(argv)
     if args.warmup < 3:
         raise SystemExit("--warmup must be at least 3")
     dist = Dist(args.gpus)
     try:
-        if args.impl == "reference":
+        if args.int_peak:
+            run_int_peak(args, dist)
+        elif args.impl == "reference":
             run_reference(args, dist)
         else:
             run_ours(args, dist)

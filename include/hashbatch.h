@@ -182,12 +182,14 @@ int hash_batch_mixed_shape(const uint8_t *algs, const uint8_t *packed_bytes,
 
 /*
  * Integer-issue microbenchmark (measurement only; not part of the hashing
- * path): runs `iters` iterations of independent chains of one opcode class
- * (0 LOP3, 1 IADD3, 2 SHF funnel rotate, 3 PRMT, 4 mixed LOP3+IADD3+SHF)
- * on every resident warp and writes the elapsed SM cycles per SM to
- * cycles_out[blocks] and a sink value to sink_dev.  blocks/threads give the
- * launch shape.  The number of 32-bit operations executed is
- * blocks * threads * iters * hash_int_peak_ops_per_iter().
+ * path): runs `iters` iterations of eight independent chains per thread of
+ * one operation class on every thread of the launch -- 0 LOP3, 1 IADD3,
+ * 2 SHF funnel rotate, 3 PRMT, 4 LOP3/IADD3/SHF in rotation, 5 IMAD x*y+z,
+ * 6 LOP3/IMAD, 7 IADD3/IMAD, 8 SHF/IMAD, 9 LOP3/FFMA, 10 IMAD x*1+y (an add
+ * on the multiply-add pipe), 11 LOP3/(x*1+y), 12 LOP3/SHF/IADD3/(x*1+y) --
+ * and writes the SM cycles each block took to cycles_out_dev[blocks]
+ * (device) and a sink word to sink_dev.  The number of 32-bit operations
+ * executed is blocks * threads * iters * hash_int_peak_ops_per_iter().
  */
 int hash_int_peak(int op_class, int blocks, int threads, int iters, uint64_t *cycles_out_dev,
                   uint32_t *sink_dev, void *stream);

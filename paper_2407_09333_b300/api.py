@@ -23,7 +23,8 @@ DEV_TIMEOUT = 0x1
 DEV_BOUNDS = 0x2
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "libhashbatch.so")
+# HB_LIBRARY may name another build of the same library (e.g. an A/B variant).
+LIB_PATH = os.environ.get("HB_LIBRARY") or os.path.join(_PKG, "libhashbatch.so")
 HEADER_PATH = os.path.join(os.path.dirname(_PKG), "include", "hashbatch.h")
 
 _c_int, _c_u64, _c_u32, _vp = ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p

@@ -1,0 +1,107 @@
+"""Autotuner for the launch shape of the hashing kernels.
+
+A shape is (warps per block, cp.async stages per warp), i.e. the threads per
+block and the bytes staged per warp (stages x 32 lanes x 80-byte windows).
+For a given algorithm and a representative batch, every shape is timed with
+CUDA events on the caller's stream and the fastest is installed in the
+library (hash_tune_set).  Results are cached in JSON keyed by device name,
+SM count, algorithm (or "mixed") and a length class (floor(log2(mean
+message length + 1))), so a later process with the same device and workload
+shape reuses them without timing.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+
+from . import api
+
+DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "hashbatch", "tune.json")
+
+
+def cache_path() -> str:
+    return os.environ.get("HB_TUNE_CACHE", DEFAULT_CACHE)
+
+
+def length_class(mean_len: float) -> int:
+    return int(math.floor(math.log2(max(mean_len, 0.0) + 1.0)))
+
+
+def cache_key(device_name: str, sms: int, alg, mean_len: float) -> str:
+    name = "mixed" if alg is None else api.ALG_NAMES[alg]
+    return "%s|%d|%s|L%d" % (device_name, sms, name, length_class(mean_len))
+
+
+def load_cache(path: str | None = None) -> dict:
+    path = path or cache_path()
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def save_cache(cache: dict, path: str | None = None):
+    path = path or cache_path()
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    tmp = path + ".tmp.%d" % os.getpid()
+    with open(tmp, "w") as f:
+        json.dump(cache, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def _time_ms(torch, fn, reps: int) -> float:
+    fn()
+    torch.cuda.synchronize()
+    best = float("inf")
+    for _ in range(reps):
+        s = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        s.record()
+        fn()
+        e.record()
+        e.synchronize()
+        best = min(best, s.elapsed_time(e))
+    return best
+
+
+def tune(alg, packed, offsets, lengths, out, algs=None, mean_len: float | None = None,
+         reps: int = 3, use_cache: bool = True, path: str | None = None) -> dict:
+    """Pick and install the fastest shape for `alg` (None = the mixed path).
+
+    Returns {"shape": index, "warps": w, "stages": s, "ms": {index: ms},
+    "cached": bool}.
+    """
+    import torch
+
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    if mean_len is None:
+        mean_len = float(lengths.double().mean().item()) if lengths.numel() else 0.0
+    key = cache_key(props.name, props.multi_processor_count, alg, mean_len)
+    tune_alg = api.TUNE_MIXED if alg is None else alg
+    shapes = api.shapes()
+    cache = load_cache(path) if use_cache else {}
+    if key in cache and 0 <= cache[key]["shape"] < len(shapes):
+        api.tune_set(tune_alg, cache[key]["shape"])
+        return dict(cache[key], cached=True)
+
+    timings = {}
+    for idx in range(len(shapes)):
+        if alg is None:
+            fn = lambda idx=idx: api.hash_batch_mixed(algs, packed, offsets, lengths, out=out, shape=idx)
+        else:
+            fn = lambda idx=idx: api.hash_batch(alg, packed, offsets, lengths, out=out, shape=idx)
+        timings[idx] = _time_ms(torch, fn, reps)
+    best = min(timings, key=timings.get)
+    api.tune_set(tune_alg, best)
+    result = {"shape": best, "warps": shapes[best][0], "stages": shapes[best][1],
+              "ms": {str(k): v for k, v in timings.items()}, "key": key}
+    if use_cache:
+        cache = load_cache(path)
+        cache[key] = result
+        try:
+            save_cache(cache, path)
+        except OSError:
+            pass
+    return dict(result, cached=False)

@@ -29,12 +29,13 @@ def _deps():
     return out
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    if not force and os.path.exists(LIB):
-        t = os.path.getmtime(LIB)
+def build(force: bool = False, verbose: bool = False, extra=(), out: str | None = None) -> str:
+    lib = out or LIB
+    if not force and os.path.exists(lib):
+        t = os.path.getmtime(lib)
         if all(os.path.getmtime(d) <= t for d in _deps()):
-            return LIB
-    tmp = LIB + ".tmp.%d" % os.getpid()
+            return lib
+    tmp = lib + ".tmp.%d" % os.getpid()
     cmd = [NVCC, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared",
            "-Xcompiler", "-fPIC", "-cudart", "shared",
            "-I", INCLUDE, "-I", CSRC, "-o", tmp]
@@ -43,8 +44,8 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     cmd += list(extra)
     cmd += [os.path.join(CSRC, s) for s in SOURCES]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

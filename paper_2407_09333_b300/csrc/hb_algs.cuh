@@ -1,7 +1,10 @@
 // hb_algs.cuh -- the three compression functions on one 64-byte block held in
 // registers, fully unrolled: MD5 (RFC 1321 Sec. 3.4), SHA-1 (FIPS 180-4
 // Sec. 6.1.2) and SM3 (GB/T 32905-2016 Sec. 5.3).  Boolean functions are one
-// LOP3 each, rotations one funnel shift, sums fold into IADD3.
+// LOP3 each, rotations one funnel shift, sums fold into IADD3.  Work is split
+// between the ALU pipe (LOP3, IADD3, SHF) and the multiply-add pipe (adds as
+// x*1+y, rotations as the two halves of x*2^s; hb_device.cuh) so that both
+// pipes carry about the same number of instructions per round.
 //
 // Word order on entry: MD5 takes the block's words little-endian; SHA-1 and
 // SM3 take them big-endian (the staging code byte-swaps with PRMT).
@@ -50,89 +53,97 @@ __device__ __forceinline__ void md5_init(uint32_t (&st)[8]) {
   st[3] = 0x10325476u;
 }
 
-// One operation a = b + ((a + g(b,c,d) + X[k] + T[i]) <<< s).
-#define HB_MD5_OP(LUT, a, b, c, d, xk, t, s)      \
-  do {                                           \
-    a += lop3<LUT>(b, c, d) + (xk) + (t);        \
-    a = rotl<s>(a) + b;                          \
+// One operation a = b + ((a + g(b,c,d) + X[k] + T[i]) <<< s).  The sum
+// a + X[k] + T[i] does not depend on b, c, d and is one IADD3; the rest
+// alternates between two splits: V = 1 puts the rotate-and-add on the FMA
+// pipe (ALU 2, FMA 3), V = 0 rotates on the ALU (ALU 3, FMA 2).
+#define HB_MD5_OP(LUT, a, b, c, d, xk, t, s, V)     \
+  do {                                             \
+    a += (xk) + (t);                               \
+    a = add_f(lop3<LUT>(b, c, d), a, mc);          \
+    if (V)                                         \
+      a = rotl_add_f<s>(a, b, mc);                 \
+    else                                           \
+      a = add_f(rotl<s>(a), b, mc);                \
   } while (0)
 
 // Round 2's G(x,y,z) = (x & z) | (y & ~z): LUT built with x->a, y->b, z->c.
-__device__ __forceinline__ void md5_compress(uint32_t (&st)[8], const uint32_t (&X)[16]) {
+__device__ __forceinline__ void md5_compress(uint32_t (&st)[8], const uint32_t (&X)[16],
+                                             const MulConsts& mc) {
   constexpr uint32_t T[64] = {HB_MD5_T_TABLE};
   uint32_t a = st[0], b = st[1], c = st[2], d = st[3];
   // Round 1: F, words in order, shifts 7 12 17 22.
-  HB_MD5_OP(LUT_CHOOSE, a, b, c, d, X[0], T[0], 7);
-  HB_MD5_OP(LUT_CHOOSE, d, a, b, c, X[1], T[1], 12);
-  HB_MD5_OP(LUT_CHOOSE, c, d, a, b, X[2], T[2], 17);
-  HB_MD5_OP(LUT_CHOOSE, b, c, d, a, X[3], T[3], 22);
-  HB_MD5_OP(LUT_CHOOSE, a, b, c, d, X[4], T[4], 7);
-  HB_MD5_OP(LUT_CHOOSE, d, a, b, c, X[5], T[5], 12);
-  HB_MD5_OP(LUT_CHOOSE, c, d, a, b, X[6], T[6], 17);
-  HB_MD5_OP(LUT_CHOOSE, b, c, d, a, X[7], T[7], 22);
-  HB_MD5_OP(LUT_CHOOSE, a, b, c, d, X[8], T[8], 7);
-  HB_MD5_OP(LUT_CHOOSE, d, a, b, c, X[9], T[9], 12);
-  HB_MD5_OP(LUT_CHOOSE, c, d, a, b, X[10], T[10], 17);
-  HB_MD5_OP(LUT_CHOOSE, b, c, d, a, X[11], T[11], 22);
-  HB_MD5_OP(LUT_CHOOSE, a, b, c, d, X[12], T[12], 7);
-  HB_MD5_OP(LUT_CHOOSE, d, a, b, c, X[13], T[13], 12);
-  HB_MD5_OP(LUT_CHOOSE, c, d, a, b, X[14], T[14], 17);
-  HB_MD5_OP(LUT_CHOOSE, b, c, d, a, X[15], T[15], 22);
+  HB_MD5_OP(LUT_CHOOSE, a, b, c, d, X[0], T[0], 7, 1);
+  HB_MD5_OP(LUT_CHOOSE, d, a, b, c, X[1], T[1], 12, 0);
+  HB_MD5_OP(LUT_CHOOSE, c, d, a, b, X[2], T[2], 17, 1);
+  HB_MD5_OP(LUT_CHOOSE, b, c, d, a, X[3], T[3], 22, 0);
+  HB_MD5_OP(LUT_CHOOSE, a, b, c, d, X[4], T[4], 7, 1);
+  HB_MD5_OP(LUT_CHOOSE, d, a, b, c, X[5], T[5], 12, 0);
+  HB_MD5_OP(LUT_CHOOSE, c, d, a, b, X[6], T[6], 17, 1);
+  HB_MD5_OP(LUT_CHOOSE, b, c, d, a, X[7], T[7], 22, 0);
+  HB_MD5_OP(LUT_CHOOSE, a, b, c, d, X[8], T[8], 7, 1);
+  HB_MD5_OP(LUT_CHOOSE, d, a, b, c, X[9], T[9], 12, 0);
+  HB_MD5_OP(LUT_CHOOSE, c, d, a, b, X[10], T[10], 17, 1);
+  HB_MD5_OP(LUT_CHOOSE, b, c, d, a, X[11], T[11], 22, 0);
+  HB_MD5_OP(LUT_CHOOSE, a, b, c, d, X[12], T[12], 7, 1);
+  HB_MD5_OP(LUT_CHOOSE, d, a, b, c, X[13], T[13], 12, 0);
+  HB_MD5_OP(LUT_CHOOSE, c, d, a, b, X[14], T[14], 17, 1);
+  HB_MD5_OP(LUT_CHOOSE, b, c, d, a, X[15], T[15], 22, 0);
   // Round 2: G, words 1 + 5j mod 16, shifts 5 9 14 20.
-  HB_MD5_OP(LUT_MD5_G, a, b, c, d, X[1], T[16], 5);
-  HB_MD5_OP(LUT_MD5_G, d, a, b, c, X[6], T[17], 9);
-  HB_MD5_OP(LUT_MD5_G, c, d, a, b, X[11], T[18], 14);
-  HB_MD5_OP(LUT_MD5_G, b, c, d, a, X[0], T[19], 20);
-  HB_MD5_OP(LUT_MD5_G, a, b, c, d, X[5], T[20], 5);
-  HB_MD5_OP(LUT_MD5_G, d, a, b, c, X[10], T[21], 9);
-  HB_MD5_OP(LUT_MD5_G, c, d, a, b, X[15], T[22], 14);
-  HB_MD5_OP(LUT_MD5_G, b, c, d, a, X[4], T[23], 20);
-  HB_MD5_OP(LUT_MD5_G, a, b, c, d, X[9], T[24], 5);
-  HB_MD5_OP(LUT_MD5_G, d, a, b, c, X[14], T[25], 9);
-  HB_MD5_OP(LUT_MD5_G, c, d, a, b, X[3], T[26], 14);
-  HB_MD5_OP(LUT_MD5_G, b, c, d, a, X[8], T[27], 20);
-  HB_MD5_OP(LUT_MD5_G, a, b, c, d, X[13], T[28], 5);
-  HB_MD5_OP(LUT_MD5_G, d, a, b, c, X[2], T[29], 9);
-  HB_MD5_OP(LUT_MD5_G, c, d, a, b, X[7], T[30], 14);
-  HB_MD5_OP(LUT_MD5_G, b, c, d, a, X[12], T[31], 20);
+  HB_MD5_OP(LUT_MD5_G, a, b, c, d, X[1], T[16], 5, 1);
+  HB_MD5_OP(LUT_MD5_G, d, a, b, c, X[6], T[17], 9, 0);
+  HB_MD5_OP(LUT_MD5_G, c, d, a, b, X[11], T[18], 14, 1);
+  HB_MD5_OP(LUT_MD5_G, b, c, d, a, X[0], T[19], 20, 0);
+  HB_MD5_OP(LUT_MD5_G, a, b, c, d, X[5], T[20], 5, 1);
+  HB_MD5_OP(LUT_MD5_G, d, a, b, c, X[10], T[21], 9, 0);
+  HB_MD5_OP(LUT_MD5_G, c, d, a, b, X[15], T[22], 14, 1);
+  HB_MD5_OP(LUT_MD5_G, b, c, d, a, X[4], T[23], 20, 0);
+  HB_MD5_OP(LUT_MD5_G, a, b, c, d, X[9], T[24], 5, 1);
+  HB_MD5_OP(LUT_MD5_G, d, a, b, c, X[14], T[25], 9, 0);
+  HB_MD5_OP(LUT_MD5_G, c, d, a, b, X[3], T[26], 14, 1);
+  HB_MD5_OP(LUT_MD5_G, b, c, d, a, X[8], T[27], 20, 0);
+  HB_MD5_OP(LUT_MD5_G, a, b, c, d, X[13], T[28], 5, 1);
+  HB_MD5_OP(LUT_MD5_G, d, a, b, c, X[2], T[29], 9, 0);
+  HB_MD5_OP(LUT_MD5_G, c, d, a, b, X[7], T[30], 14, 1);
+  HB_MD5_OP(LUT_MD5_G, b, c, d, a, X[12], T[31], 20, 0);
   // Round 3: H, words 5 + 3j mod 16, shifts 4 11 16 23.
-  HB_MD5_OP(LUT_XOR3, a, b, c, d, X[5], T[32], 4);
-  HB_MD5_OP(LUT_XOR3, d, a, b, c, X[8], T[33], 11);
-  HB_MD5_OP(LUT_XOR3, c, d, a, b, X[11], T[34], 16);
-  HB_MD5_OP(LUT_XOR3, b, c, d, a, X[14], T[35], 23);
-  HB_MD5_OP(LUT_XOR3, a, b, c, d, X[1], T[36], 4);
-  HB_MD5_OP(LUT_XOR3, d, a, b, c, X[4], T[37], 11);
-  HB_MD5_OP(LUT_XOR3, c, d, a, b, X[7], T[38], 16);
-  HB_MD5_OP(LUT_XOR3, b, c, d, a, X[10], T[39], 23);
-  HB_MD5_OP(LUT_XOR3, a, b, c, d, X[13], T[40], 4);
-  HB_MD5_OP(LUT_XOR3, d, a, b, c, X[0], T[41], 11);
-  HB_MD5_OP(LUT_XOR3, c, d, a, b, X[3], T[42], 16);
-  HB_MD5_OP(LUT_XOR3, b, c, d, a, X[6], T[43], 23);
-  HB_MD5_OP(LUT_XOR3, a, b, c, d, X[9], T[44], 4);
-  HB_MD5_OP(LUT_XOR3, d, a, b, c, X[12], T[45], 11);
-  HB_MD5_OP(LUT_XOR3, c, d, a, b, X[15], T[46], 16);
-  HB_MD5_OP(LUT_XOR3, b, c, d, a, X[2], T[47], 23);
+  HB_MD5_OP(LUT_XOR3, a, b, c, d, X[5], T[32], 4, 1);
+  HB_MD5_OP(LUT_XOR3, d, a, b, c, X[8], T[33], 11, 0);
+  HB_MD5_OP(LUT_XOR3, c, d, a, b, X[11], T[34], 16, 1);
+  HB_MD5_OP(LUT_XOR3, b, c, d, a, X[14], T[35], 23, 0);
+  HB_MD5_OP(LUT_XOR3, a, b, c, d, X[1], T[36], 4, 1);
+  HB_MD5_OP(LUT_XOR3, d, a, b, c, X[4], T[37], 11, 0);
+  HB_MD5_OP(LUT_XOR3, c, d, a, b, X[7], T[38], 16, 1);
+  HB_MD5_OP(LUT_XOR3, b, c, d, a, X[10], T[39], 23, 0);
+  HB_MD5_OP(LUT_XOR3, a, b, c, d, X[13], T[40], 4, 1);
+  HB_MD5_OP(LUT_XOR3, d, a, b, c, X[0], T[41], 11, 0);
+  HB_MD5_OP(LUT_XOR3, c, d, a, b, X[3], T[42], 16, 1);
+  HB_MD5_OP(LUT_XOR3, b, c, d, a, X[6], T[43], 23, 0);
+  HB_MD5_OP(LUT_XOR3, a, b, c, d, X[9], T[44], 4, 1);
+  HB_MD5_OP(LUT_XOR3, d, a, b, c, X[12], T[45], 11, 0);
+  HB_MD5_OP(LUT_XOR3, c, d, a, b, X[15], T[46], 16, 1);
+  HB_MD5_OP(LUT_XOR3, b, c, d, a, X[2], T[47], 23, 0);
   // Round 4: I, words 7j mod 16, shifts 6 10 15 21.
-  HB_MD5_OP(LUT_MD5_I, a, b, c, d, X[0], T[48], 6);
-  HB_MD5_OP(LUT_MD5_I, d, a, b, c, X[7], T[49], 10);
-  HB_MD5_OP(LUT_MD5_I, c, d, a, b, X[14], T[50], 15);
-  HB_MD5_OP(LUT_MD5_I, b, c, d, a, X[5], T[51], 21);
-  HB_MD5_OP(LUT_MD5_I, a, b, c, d, X[12], T[52], 6);
-  HB_MD5_OP(LUT_MD5_I, d, a, b, c, X[3], T[53], 10);
-  HB_MD5_OP(LUT_MD5_I, c, d, a, b, X[10], T[54], 15);
-  HB_MD5_OP(LUT_MD5_I, b, c, d, a, X[1], T[55], 21);
-  HB_MD5_OP(LUT_MD5_I, a, b, c, d, X[8], T[56], 6);
-  HB_MD5_OP(LUT_MD5_I, d, a, b, c, X[15], T[57], 10);
-  HB_MD5_OP(LUT_MD5_I, c, d, a, b, X[6], T[58], 15);
-  HB_MD5_OP(LUT_MD5_I, b, c, d, a, X[13], T[59], 21);
-  HB_MD5_OP(LUT_MD5_I, a, b, c, d, X[4], T[60], 6);
-  HB_MD5_OP(LUT_MD5_I, d, a, b, c, X[11], T[61], 10);
-  HB_MD5_OP(LUT_MD5_I, c, d, a, b, X[2], T[62], 15);
-  HB_MD5_OP(LUT_MD5_I, b, c, d, a, X[9], T[63], 21);
-  st[0] += a;
-  st[1] += b;
-  st[2] += c;
-  st[3] += d;
+  HB_MD5_OP(LUT_MD5_I, a, b, c, d, X[0], T[48], 6, 1);
+  HB_MD5_OP(LUT_MD5_I, d, a, b, c, X[7], T[49], 10, 0);
+  HB_MD5_OP(LUT_MD5_I, c, d, a, b, X[14], T[50], 15, 1);
+  HB_MD5_OP(LUT_MD5_I, b, c, d, a, X[5], T[51], 21, 0);
+  HB_MD5_OP(LUT_MD5_I, a, b, c, d, X[12], T[52], 6, 1);
+  HB_MD5_OP(LUT_MD5_I, d, a, b, c, X[3], T[53], 10, 0);
+  HB_MD5_OP(LUT_MD5_I, c, d, a, b, X[10], T[54], 15, 1);
+  HB_MD5_OP(LUT_MD5_I, b, c, d, a, X[1], T[55], 21, 0);
+  HB_MD5_OP(LUT_MD5_I, a, b, c, d, X[8], T[56], 6, 1);
+  HB_MD5_OP(LUT_MD5_I, d, a, b, c, X[15], T[57], 10, 0);
+  HB_MD5_OP(LUT_MD5_I, c, d, a, b, X[6], T[58], 15, 1);
+  HB_MD5_OP(LUT_MD5_I, b, c, d, a, X[13], T[59], 21, 0);
+  HB_MD5_OP(LUT_MD5_I, a, b, c, d, X[4], T[60], 6, 1);
+  HB_MD5_OP(LUT_MD5_I, d, a, b, c, X[11], T[61], 10, 0);
+  HB_MD5_OP(LUT_MD5_I, c, d, a, b, X[2], T[62], 15, 1);
+  HB_MD5_OP(LUT_MD5_I, b, c, d, a, X[9], T[63], 21, 0);
+  st[0] = add_f(st[0], a, mc);
+  st[1] = add_f(st[1], b, mc);
+  st[2] = add_f(st[2], c, mc);
+  st[3] = add_f(st[3], d, mc);
 }
 #undef HB_MD5_OP
 
@@ -164,35 +175,44 @@ __device__ __forceinline__ constexpr uint32_t sha1_k() {
 }
 
 // Rounds T .. 79 by compile-time recursion; W is the 16-word schedule ring.
+// Split per round: the schedule word (two LOP3 and a rotate), f and
+// e + W + K (IADD3) on the ALU; (f + that) and the rotate-and-add of a on the
+// FMA pipe; ROTL30(b) on the FMA pipe while the schedule runs (ALU 5, FMA 5),
+// on the ALU before it (ALU 3, FMA 3).
 template <int T>
 __device__ __forceinline__ void sha1_rounds(uint32_t& a, uint32_t& b, uint32_t& c, uint32_t& d,
-                                            uint32_t& e, uint32_t (&W)[16]) {
+                                            uint32_t& e, uint32_t (&W)[16], const MulConsts& mc) {
   if constexpr (T < 80) {
     if constexpr (T >= 16) {
       W[T & 15] = rotl<1>(lop3<LUT_XOR3>(W[(T - 3) & 15], W[(T - 8) & 15], W[(T - 14) & 15]) ^
                           W[T & 15]);
     }
-    const uint32_t t = rotl<5>(a) + sha1_f<T>(b, c, d) + e + sha1_k<T>() + W[T & 15];
+    const uint32_t ewk = e + W[T & 15] + sha1_k<T>();
+    const uint32_t t = rotl_add_f<5>(a, add_f(sha1_f<T>(b, c, d), ewk, mc), mc);
     e = d;
     d = c;
-    c = rotl<30>(b);
+    if constexpr (T >= 16)
+      c = rotl_f<30>(b, mc);
+    else
+      c = rotl<30>(b);
     b = a;
     a = t;
-    sha1_rounds<T + 1>(a, b, c, d, e, W);
+    sha1_rounds<T + 1>(a, b, c, d, e, W, mc);
   }
 }
 
-__device__ __forceinline__ void sha1_compress(uint32_t (&st)[8], const uint32_t (&X)[16]) {
+__device__ __forceinline__ void sha1_compress(uint32_t (&st)[8], const uint32_t (&X)[16],
+                                              const MulConsts& mc) {
   uint32_t W[16];
 #pragma unroll
   for (int i = 0; i < 16; ++i) W[i] = X[i];
   uint32_t a = st[0], b = st[1], c = st[2], d = st[3], e = st[4];
-  sha1_rounds<0>(a, b, c, d, e, W);
-  st[0] += a;
-  st[1] += b;
-  st[2] += c;
-  st[3] += d;
-  st[4] += e;
+  sha1_rounds<0>(a, b, c, d, e, W, mc);
+  st[0] = add_f(st[0], a, mc);
+  st[1] = add_f(st[1], b, mc);
+  st[2] = add_f(st[2], c, mc);
+  st[3] = add_f(st[3], d, mc);
+  st[4] = add_f(st[4], e, mc);
 }
 
 // ---------------------------------------------------------------------------
@@ -227,14 +247,18 @@ __device__ __forceinline__ uint32_t sm3_p1(uint32_t x) {
 
 // Rounds J .. 63.  W is a 16-word ring holding W_{J} .. W_{J+3} (and older
 // words still needed); round J first extends it with W_{J+4} (Sec. 5.3.2),
-// so that W'_J = W_J ^ W_{J+4} is available.
+// so that W'_J = W_J ^ W_{J+4} is available.  Split per round: rotations
+// feeding XORs, the Boolean functions, P0 and SS1's sum on the ALU; the six
+// adds of TT1 and TT2 and the standalone rotations B<<<9 and F<<<19 on the
+// FMA pipe (ALU 10, FMA 10); the expansion adds three LOP3 and P1's two
+// rotations on the ALU and its two word rotations on the FMA pipe.
 template <int J>
-__device__ __forceinline__ void sm3_rounds(uint32_t (&v)[8], uint32_t (&W)[16]) {
+__device__ __forceinline__ void sm3_rounds(uint32_t (&v)[8], uint32_t (&W)[16], const MulConsts& mc) {
   if constexpr (J < 64) {
     constexpr int M = J + 4;  // index of the word produced this round
     if constexpr (M >= 16 && M < 68) {
-      const uint32_t x = lop3<LUT_XOR3>(W[(M - 16) & 15], W[(M - 9) & 15], rotl<15>(W[(M - 3) & 15]));
-      W[M & 15] = lop3<LUT_XOR3>(sm3_p1(x), rotl<7>(W[(M - 13) & 15]), W[(M - 6) & 15]);
+      const uint32_t x = lop3<LUT_XOR3>(W[(M - 16) & 15], W[(M - 9) & 15], rotl_f<15>(W[(M - 3) & 15], mc));
+      W[M & 15] = lop3<LUT_XOR3>(sm3_p1(x), rotl_f<7>(W[(M - 13) & 15], mc), W[(M - 6) & 15]);
     }
     uint32_t& A = v[0];
     uint32_t& B = v[1];
@@ -257,28 +281,29 @@ __device__ __forceinline__ void sm3_rounds(uint32_t (&v)[8], uint32_t (&W)[16]) 
       ff = lop3<LUT_MAJ>(A, B, C);
       gg = lop3<LUT_CHOOSE>(E, F, G);
     }
-    const uint32_t tt1 = ff + D + ss2 + wpj;
-    const uint32_t tt2 = gg + H + ss1 + wj;
+    const uint32_t tt1 = add_f(ss2, add_f(ff, add_f(D, wpj, mc), mc), mc);
+    const uint32_t tt2 = add_f(ss1, add_f(gg, add_f(H, wj, mc), mc), mc);
     D = C;
-    C = rotl<9>(B);
+    C = rotl_f<9>(B, mc);
     B = A;
     A = tt1;
     H = G;
-    G = rotl<19>(F);
+    G = rotl_f<19>(F, mc);
     F = E;
     E = sm3_p0(tt2);
-    sm3_rounds<J + 1>(v, W);
+    sm3_rounds<J + 1>(v, W, mc);
   }
 }
 
-__device__ __forceinline__ void sm3_compress(uint32_t (&st)[8], const uint32_t (&X)[16]) {
+__device__ __forceinline__ void sm3_compress(uint32_t (&st)[8], const uint32_t (&X)[16],
+                                             const MulConsts& mc) {
   uint32_t W[16];
 #pragma unroll
   for (int i = 0; i < 16; ++i) W[i] = X[i];
   uint32_t v[8];
 #pragma unroll
   for (int i = 0; i < 8; ++i) v[i] = st[i];
-  sm3_rounds<0>(v, W);
+  sm3_rounds<0>(v, W, mc);
 #pragma unroll
   for (int i = 0; i < 8; ++i) st[i] ^= v[i];
 }
@@ -294,10 +319,11 @@ __device__ __forceinline__ void alg_init(uint32_t (&st)[8]) {
 }
 
 template <int ALG>
-__device__ __forceinline__ void alg_compress(uint32_t (&st)[8], const uint32_t (&X)[16]) {
-  if constexpr (ALG == HB_MD5) md5_compress(st, X);
-  else if constexpr (ALG == HB_SHA1) sha1_compress(st, X);
-  else sm3_compress(st, X);
+__device__ __forceinline__ void alg_compress(uint32_t (&st)[8], const uint32_t (&X)[16],
+                                             const MulConsts& mc) {
+  if constexpr (ALG == HB_MD5) md5_compress(st, X, mc);
+  else if constexpr (ALG == HB_SHA1) sha1_compress(st, X, mc);
+  else sm3_compress(st, X, mc);
 }
 
 // Digest words in memory order for the 32-byte slot (zero fill after the

@@ -164,6 +164,7 @@ int launch_mixed(Ctx* c, int shape, int grid, const uint8_t* algs, const uint8_t
   a.status = c->status;
   a.abort_flag = abort_flag;
   a.wait_limit_ns = g_wait_limit_ns;
+  a.mc = hb::make_mul_consts();
   if (grid <= 0) grid = c->sms * occ;
   e = hb::launch_hash(true, 0, shape, grid, a, s);
   return e == cudaSuccess ? HB_OK : cuda_fail(e);
@@ -227,6 +228,7 @@ int hash_batch_shape(int alg, const uint8_t* packed_bytes, const uint64_t* offse
   a.digests = digests_out;
   a.status = c->status;
   a.wait_limit_ns = g_wait_limit_ns;
+  a.mc = hb::make_mul_consts();
   return launch_plain(c, alg, shape_index, grid_blocks, a, static_cast<cudaStream_t>(stream));
 }
 
@@ -337,6 +339,7 @@ int hash_batch_host(int alg, const uint8_t* algs_host, const uint8_t* packed_hos
     a.status = c->status;
     a.abort_flag = d_flag;
     a.wait_limit_ns = g_wait_limit_ns;
+  a.mc = hb::make_mul_consts();
     if ((rc = launch_plain(c, alg, c->tune_plain[alg], 0, a, s))) return rc;
   }
   if (cudaMemcpyAsync(digests_host, d_dig, n * (size_t)HB_SLOT_BYTES, cudaMemcpyDeviceToHost, s) ||

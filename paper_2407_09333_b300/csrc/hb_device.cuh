@@ -7,6 +7,7 @@
 #include <cstdint>
 
 #include "hashbatch.h"
+#include "hb_launch.h"
 
 namespace hb {
 
@@ -34,6 +35,58 @@ constexpr uint32_t LUT_MD5_I = (kB ^ (kA | ~kC)) & 0xFF;                     // 
 template <int S>
 __device__ __forceinline__ uint32_t rotl(uint32_t x) {
   return __funnelshift_l(x, x, S);
+}
+
+// ---------------------------------------------------------------------------
+// Work for the multiply-add pipe.  The SM's 32-bit integer ALU pipe (LOP3,
+// IADD3, SHF, PRMT) retires 64 results per clock per SM; the multiply-add
+// (FMA) pipe retires another 64 IMAD results per clock concurrently.  An add
+// becomes x * 1 + y and a rotation becomes the two halves of x * 2^s, with
+// the factors read from kernel arguments so that the compiler cannot turn the
+// multiplications back into ALU adds and shifts:
+//   rotl(x, s) + y = mad.hi(x, 2^s, mad.lo(x, 2^s, y))   (s = 1..31)
+// because x * 2^s = (x >> (32 - s)) * 2^32 + (x << s) and the two parts do not
+// overlap.  HB_FMA_OFFLOAD=0 builds the plain ALU forms for comparison.
+#ifndef HB_FMA_OFFLOAD
+#define HB_FMA_OFFLOAD 0
+#endif
+
+__device__ __forceinline__ uint32_t mad_lo(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t d;
+  asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
+}
+
+__device__ __forceinline__ uint32_t mad_hi(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t d;
+  asm("mad.hi.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
+}
+
+// x + y on the FMA pipe.
+__device__ __forceinline__ uint32_t add_f(uint32_t x, uint32_t y, const MulConsts& m) {
+#if HB_FMA_OFFLOAD
+  return mad_lo(x, m.one, y);
+#else
+  return x + y;
+#endif
+}
+
+// rotl(x, S) + y on the FMA pipe (two IMADs).
+template <int S>
+__device__ __forceinline__ uint32_t rotl_add_f(uint32_t x, uint32_t y, const MulConsts& m) {
+#if HB_FMA_OFFLOAD
+  const uint32_t p = m.pow2[S];
+  return mad_hi(x, p, mad_lo(x, p, y));
+#else
+  return __funnelshift_l(x, x, S) + y;
+#endif
+}
+
+// rotl(x, S) on the FMA pipe (two IMADs).
+template <int S>
+__device__ __forceinline__ uint32_t rotl_f(uint32_t x, const MulConsts& m) {
+  return rotl_add_f<S>(x, 0u, m);
 }
 
 // Byte permute (PRMT): bytes of the 64-bit value {hi:lo} picked by `sel`.
@@ -148,6 +201,28 @@ __device__ __forceinline__ void sts32(uint32_t addr, uint32_t v) {
 __device__ __forceinline__ void sts128(uint32_t addr, uint4 v) {
   asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v.x), "r"(v.y),
                "r"(v.z), "r"(v.w));
+}
+
+__device__ __forceinline__ void sts8(uint32_t addr, uint32_t v) {
+  asm volatile("st.shared.u8 [%0], %1;" ::"r"(addr), "r"(v));
+}
+
+// Asynchronous 16-byte global -> shared copy (LDGSTS, L2 only) of the first
+// `src_bytes` (0..16) bytes at `src`; the rest of the 16 destination bytes are
+// zero-filled.  Both addresses must be 16-byte aligned.
+__device__ __forceinline__ void cp_async16_zfill(uint32_t dst, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// Wait until at most N of this thread's committed copy groups are pending.
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
 // Read-only global loads of the per-message metadata.

@@ -149,19 +149,39 @@ __global__ void hb_bounds_kernel(const uint64_t* offsets, const uint32_t* length
 // ---------------------------------------------------------------------------
 // Integer issue microbenchmark: eight independent chains per thread, four
 // unrolled steps per iteration, one 32-bit operation per chain per step.
+// `one` is a kernel argument equal to 1, so x * one + y stays a multiply-add
+// (IMAD) that the compiler cannot turn back into a plain add.
+//   0 LOP3   1 IADD3   2 SHF   3 PRMT   4 LOP3/IADD3/SHF   5 IMAD x*y+z
+//   6 LOP3/IMAD   7 IADD3/IMAD   8 SHF/IMAD   9 LOP3/FFMA   10 IMAD x*1+y
+//   11 LOP3/(x*1+y)   12 LOP3/SHF/IADD3/(x*1+y)
 
 template <int OP>
-__device__ __forceinline__ uint32_t peak_op(uint32_t x, uint32_t y, uint32_t z) {
+__device__ __forceinline__ uint32_t peak_step(int u, uint32_t x, uint32_t y, uint32_t z, uint32_t one) {
   if constexpr (OP == 0) return lop3<0x96>(x, y, z);
   else if constexpr (OP == 1) return x + y + z;
   else if constexpr (OP == 2) return __funnelshift_l(x, y, 7);
   else if constexpr (OP == 3) return __byte_perm(x, y, 0x6351);
-  else if constexpr (OP == 5) return x * y + z;
-  else return x;
+  else if constexpr (OP == 4) {
+    const int m = u % 3;
+    return m == 0 ? lop3<0x96>(x, y, z) : m == 1 ? x + y + z : __funnelshift_l(x, y, 7);
+  } else if constexpr (OP == 5) return x * y + z;
+  else if constexpr (OP == 6) return (u & 1) ? x * y + z : lop3<0x96>(x, y, z);
+  else if constexpr (OP == 7) return (u & 1) ? x * y + z : x + y + z;
+  else if constexpr (OP == 8) return (u & 1) ? x * y + z : __funnelshift_l(x, y, 7);
+  else if constexpr (OP == 9) {
+    if (u & 1) return __float_as_uint(fmaf(__uint_as_float(x), 1.0001f, __uint_as_float(z)));
+    return lop3<0x96>(x, y, z);
+  } else if constexpr (OP == 10) return x * one + y;
+  else if constexpr (OP == 11) return (u & 1) ? x * one + y : lop3<0x96>(x, y, z);
+  else {
+    const int m = u & 3;
+    return m == 0 ? lop3<0x96>(x, y, z) : m == 1 ? __funnelshift_l(x, y, 7)
+         : m == 2 ? x + y + z : x * one + y;
+  }
 }
 
 template <int OP>
-__global__ void hb_int_peak_kernel(int iters, unsigned long long* cycles, uint32_t* sink) {
+__global__ void hb_int_peak_kernel(int iters, uint32_t one, unsigned long long* cycles, uint32_t* sink) {
   uint32_t x[8];
   const uint32_t seed = threadIdx.x * 2654435761u + blockIdx.x;
 #pragma unroll
@@ -174,21 +194,7 @@ __global__ void hb_int_peak_kernel(int iters, unsigned long long* cycles, uint32
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
 #pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        if constexpr (OP == 4) {
-          // LOP3, IADD3 and SHF in rotation.
-          const int m = (u * 8 + k) % 3;
-          if (m == 0) x[k] = lop3<0x96>(x[k], x[(k + 1) & 7], z);
-          else if (m == 1) x[k] = x[k] + x[(k + 1) & 7] + z;
-          else x[k] = __funnelshift_l(x[k], x[(k + 1) & 7], 7);
-        } else if constexpr (OP == 6) {
-          // LOP3 and IMAD alternating (ALU and multiply-add pipes).
-          if ((u * 8 + k) & 1) x[k] = x[k] * x[(k + 1) & 7] + z;
-          else x[k] = lop3<0x96>(x[k], x[(k + 1) & 7], z);
-        } else {
-          x[k] = peak_op<OP>(x[k], x[(k + 1) & 7], z);
-        }
-      }
+      for (int k = 0; k < 8; ++k) x[k] = peak_step<OP>(u * 8 + k, x[k], x[(k + 1) & 7], z, one);
     }
   }
   __syncthreads();
@@ -315,18 +321,22 @@ cudaError_t launch_bounds(const uint64_t* offsets, const uint32_t* lengths, uint
   return cudaGetLastError();
 }
 
+template <int OP>
+static void int_peak_launch(int blocks, int threads, int iters, unsigned long long* cycles,
+                            uint32_t* sink, cudaStream_t stream) {
+  hb_int_peak_kernel<OP><<<blocks, threads, 0, stream>>>(iters, 1u, cycles, sink);
+}
+
 cudaError_t launch_int_peak(int op, int blocks, int threads, int iters, unsigned long long* cycles,
                             uint32_t* sink, cudaStream_t stream) {
-  switch (op) {
-    case 0: hb_int_peak_kernel<0><<<blocks, threads, 0, stream>>>(iters, cycles, sink); break;
-    case 1: hb_int_peak_kernel<1><<<blocks, threads, 0, stream>>>(iters, cycles, sink); break;
-    case 2: hb_int_peak_kernel<2><<<blocks, threads, 0, stream>>>(iters, cycles, sink); break;
-    case 3: hb_int_peak_kernel<3><<<blocks, threads, 0, stream>>>(iters, cycles, sink); break;
-    case 4: hb_int_peak_kernel<4><<<blocks, threads, 0, stream>>>(iters, cycles, sink); break;
-    case 5: hb_int_peak_kernel<5><<<blocks, threads, 0, stream>>>(iters, cycles, sink); break;
-    case 6: hb_int_peak_kernel<6><<<blocks, threads, 0, stream>>>(iters, cycles, sink); break;
-    default: return cudaErrorInvalidValue;
-  }
+  using Fn = void (*)(int, int, int, unsigned long long*, uint32_t*, cudaStream_t);
+  static const Fn table[] = {int_peak_launch<0>, int_peak_launch<1>, int_peak_launch<2>,
+                             int_peak_launch<3>, int_peak_launch<4>, int_peak_launch<5>,
+                             int_peak_launch<6>, int_peak_launch<7>, int_peak_launch<8>,
+                             int_peak_launch<9>, int_peak_launch<10>, int_peak_launch<11>,
+                             int_peak_launch<12>};
+  if (op < 0 || op >= (int)(sizeof(table) / sizeof(table[0]))) return cudaErrorInvalidValue;
+  table[op](blocks, threads, iters, cycles, sink, stream);
   return cudaGetLastError();
 }
 

@@ -10,6 +10,21 @@
 
 namespace hb {
 
+// Factors for moving adds and rotations onto the multiply-add pipe (see
+// hb_device.cuh): one = 1, pow2[s] = 2^s.  Passed as kernel arguments so the
+// compiler cannot fold them.
+struct MulConsts {
+  uint32_t one;
+  uint32_t pow2[32];
+};
+
+inline MulConsts make_mul_consts() {
+  MulConsts m;
+  m.one = 1u;
+  for (int s = 0; s < 32; ++s) m.pow2[s] = 1u << s;
+  return m;
+}
+
 // Kernel arguments for the hashing kernels (plain and mixed).
 struct KernelArgs {
   const uint8_t* packed;
@@ -24,6 +39,7 @@ struct KernelArgs {
   int* status;                // per-device status word (HB_DEV_* bits)
   const int* abort_flag;      // optional: skip all work when *abort_flag != 0
   uint64_t wait_limit_ns;
+  MulConsts mc;
 };
 
 // Ragged-path bucketing: groups are (cost bucket, algorithm) pairs ordered

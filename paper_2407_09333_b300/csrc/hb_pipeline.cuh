@@ -7,25 +7,25 @@
 // message at that block.
 //
 // Staging.  Every lane stages its own window into a private 80-byte slot of
-// shared memory with one 1-D bulk copy (cp.async.bulk, TMA engine, never
-// multicast): the copy covers the 16-byte aligned granules that hold message
-// bytes of the window, so the window's first byte lands at slot + (addr & 15).
-// Completion is counted in transaction bytes on one mbarrier per stage; lane 0
-// arms it with the warp's total byte count.  STAGES items are in flight: the
-// warp issues item j + STAGES - 1 before it waits for item j, so the copies
-// run under the compression of earlier blocks.  An item record (message
-// index, length, block number, alignment, algorithm) travels with each stage
-// in shared memory, so the consuming side needs no global metadata loads.
+// shared memory with four or five asynchronous 16-byte copies (cp.async,
+// LDGSTS): the copies cover the 16-byte aligned granules that hold the
+// window, so the window's first byte lands at slot + (addr & 15).  Granules
+// are zero-filled past the message end by the copy itself (src-size), so a
+// window that runs past the end of its message already holds zeros there.
+// STAGES items are in flight: the warp issues item j + STAGES - 1 before it
+// waits for item j (cp.async.wait_group), so the copies run under the
+// compression of earlier blocks.  Every lane reads only what it copied
+// itself, so no cross-lane synchronisation is needed.  An item record
+// (message index, length, block number, alignment, algorithm) travels with
+// each stage in shared memory, so the consuming side needs no global
+// metadata loads.
 //
-// Padding (RFC 1321 Sec. 3.1-3.2, FIPS 180-4 Sec. 5.1.1, GB/T 32905 Sec. 5.2)
-// is done in the lane's own slot: the byte after the message becomes 0x80,
-// the rest of the window is zeroed; a block past the message end is all zero;
-// the final block's last two words are replaced by the 64-bit bit length in
-// registers.  Words are read with 32-bit shared loads and realigned with one
-// PRMT each, which also applies the big-endian byte swap for SHA-1 and SM3.
-//
-// Waits are bounded (hb_device.cuh): a wait that times out sets
-// HB_DEV_TIMEOUT in the status word and the warp drains and returns.
+// Padding (RFC 1321 Sec. 3.1-3.2, FIPS 180-4 Sec. 5.1.1, GB/T 32905 Sec. 5.2):
+// the zero-filled window gives the zero bytes; the lane stores the 0x80
+// marker after the last message byte into its own slot; the final block's
+// last two words are replaced by the 64-bit bit length in registers.  Words
+// are read with 32-bit shared loads and realigned with one PRMT each, which
+// also applies the big-endian byte swap for SHA-1 and SM3.
 #pragma once
 
 #include <cstdint>
@@ -45,8 +45,7 @@ template <int STAGES>
 struct WarpSmem {
   static constexpr int kSlots = STAGES * 32 * kSlotBytes;
   static constexpr int kItems = STAGES * 32 * kItemBytes;
-  static constexpr int kBars = ((STAGES * 8 + 127) / 128) * 128;
-  static constexpr int kBytes = kSlots + kItems + kBars;  // multiple of 128
+  static constexpr int kBytes = kSlots + kItems;  // multiple of 128
 };
 
 // Padded block count: message + 0x80 + 8 length bytes, rounded up to 64.
@@ -212,35 +211,15 @@ __device__ __forceinline__ void read_block_words(uint32_t slot, uint32_t s, uint
   for (int i = 0; i < 16; ++i) w[i] = prmt(x[i], x[i + 1], sel);
 }
 
-// Write the 0x80 marker at window byte `rem` (0 <= rem < 64) and zero the
-// rest of the window, in the lane's own slot.
-__device__ __forceinline__ void pad_tail_in_slot(uint32_t slot, uint32_t s, uint32_t rem) {
-  const uint32_t pos = slot + s + rem;
-  const uint32_t wa = pos & ~3u;
-  const uint32_t bi = pos & 3u;
-  const uint32_t keep = bi ? (0xFFFFFFFFu >> (32u - 8u * bi)) : 0u;
-  sts32(wa, (lds32(wa) & keep) | (0x80u << (8u * bi)));
-  const uint32_t end = slot + s + 64u;  // words starting below this are read
-#pragma unroll 1
-  for (uint32_t a = wa + 4; a < end; a += 4) sts32(a, 0u);
-  fence_proxy_async_smem();  // order these writes before the slot's next bulk copy
-}
-
 template <int ALG>
-__device__ __forceinline__ void process_block(uint32_t (&st)[8], uint32_t slot, uint32_t s, uint32_t len, uint32_t b, uint64_t msg,
-                                              uint8_t* digests) {
+__device__ __forceinline__ void process_block(uint32_t (&st)[8], uint32_t slot, uint32_t s,
+                                              uint32_t len, uint32_t b, uint64_t msg,
+                                              uint8_t* digests, const MulConsts& mc) {
   constexpr bool BE = AlgTraits<ALG>::kBigEndian;
-  const int64_t rem = (int64_t)len - 64 * (int64_t)b;
+  const int64_t rem = (int64_t)len - 64 * (int64_t)b;  // message bytes from this block on
+  if (rem >= 0 && rem < 64) sts8(slot + s + (uint32_t)rem, 0x80u);
   uint32_t w[16];
-  if (rem >= 64) {
-    read_block_words<BE>(slot, s, w);
-  } else if (rem >= 0) {
-    pad_tail_in_slot(slot, s, (uint32_t)rem);
-    read_block_words<BE>(slot, s, w);
-  } else {
-#pragma unroll
-    for (int i = 0; i < 16; ++i) w[i] = 0u;
-  }
+  read_block_words<BE>(slot, s, w);
   const bool final_block = rem <= 55;
   if (final_block) {
     const uint32_t lo = len << 3, hi = len >> 29;  // bit length mod 2^64
@@ -248,7 +227,7 @@ __device__ __forceinline__ void process_block(uint32_t (&st)[8], uint32_t slot, 
     w[15] = BE ? lo : hi;
   }
   if (b == 0) alg_init<ALG>(st);
-  alg_compress<ALG>(st, w);
+  alg_compress<ALG>(st, w, mc);
   if (final_block) {
     uint32_t o[8];
     alg_digest_words<ALG>(st, o);
@@ -268,15 +247,7 @@ __device__ __forceinline__ void warp_pipeline(Source& src, uint8_t* wsm, const K
   using L = WarpSmem<STAGES>;
   const uint32_t slots = smem_addr(wsm);
   const uint32_t items = slots + L::kSlots;
-  const uint32_t bars = items + L::kItems;
-
-  if (lane == 0) {
-#pragma unroll
-    for (int i = 0; i < STAGES; ++i) mbar_init(bars + 8 * i, 1);
-    fence_barrier_init();
-  }
-  fence_proxy_async_smem();
-  __syncwarp();
+  const uint64_t safe_src = reinterpret_cast<uint64_t>(a.packed) & ~15ull;
 
   // Issuing side state (warp-uniform except the LaneTask fields).
   LaneTask t;
@@ -287,34 +258,33 @@ __device__ __forceinline__ void warp_pipeline(Source& src, uint8_t* wsm, const K
 
   // Consuming side state.
   int cs = 0;
-  uint32_t cpar = 0;
   uint32_t st[8];
   int inflight = 0;
-  bool failed = false;
 
   auto issue = [&]() {
-    uint32_t bytes = 0;
-    uint64_t lo = 0;
     const bool act = ib < t.nb;
-    if (act) {
-      const uint64_t A = t.addr + 64ull * ib;
-      const uint64_t end = t.addr + t.len;
-      if (A < end) {
-        lo = A & ~15ull;
-        const uint64_t e = (A + 64 < end) ? A + 64 : end;
-        bytes = (uint32_t)(((e + 15) & ~15ull) - lo);
-      }
-    }
     uint4 rec;
     rec.x = (uint32_t)t.msg;
     rec.y = (uint32_t)(t.msg >> 32) | ((uint32_t)(t.addr & 15u) << 24) | (t.alg << 28);
     rec.z = t.len;
     rec.w = act ? ib : kNoBlock;
     sts128(items + (is * 32 + lane) * kItemBytes, rec);
-    const uint32_t total = __reduce_add_sync(kFull, bytes);
-    if (lane == 0) mbar_arrive_expect_tx(bars + 8 * is, total);
-    if (bytes) bulk_copy_g2s(slots + (is * 32 + lane) * kSlotBytes,
-                             reinterpret_cast<const void*>(lo), bytes, bars + 8 * is);
+    if (act) {
+      const uint64_t A = t.addr + 64ull * ib;            // window start
+      const uint64_t g0 = A & ~15ull;                    // first granule
+      const uint64_t end = t.addr + t.len;               // one past the last message byte
+      const uint64_t left = end > g0 ? end - g0 : 0ull;  // message bytes from g0 on
+      const int32_t avail = left > 80ull ? 80 : (int32_t)left;
+      const uint32_t dst = slots + (is * 32 + lane) * kSlotBytes;
+      const bool five = (A & 15u) != 0u;                 // unaligned window spans 5 granules
+#pragma unroll
+      for (int g = 0; g < 5; ++g) {
+        const int32_t v = avail - 16 * g;
+        const uint32_t nbytes = v <= 0 ? 0u : (v >= 16 ? 16u : (uint32_t)v);
+        const uint64_t from = nbytes ? g0 + 16ull * g : safe_src;
+        if (g < 4 || five) cp_async16_zfill(dst + 16 * g, reinterpret_cast<const void*>(from), nbytes);
+      }
+    }
     ++inflight;
     is = (is + 1 == STAGES) ? 0 : is + 1;
     if (++ib >= maxnb) {
@@ -325,40 +295,35 @@ __device__ __forceinline__ void warp_pipeline(Source& src, uint8_t* wsm, const K
   };
 
 #pragma unroll 1
-  for (int k = 0; k < STAGES - 1 && have; ++k) issue();
+  for (int k = 0; k < STAGES - 1; ++k) {
+    if (have) issue();
+    cp_async_commit();
+  }
 
 #pragma unroll 1
   while (inflight > 0) {
-    if (have && !failed) issue();
-    const bool ok = !failed && mbar_wait_bounded(bars + 8 * cs, cpar, a.wait_limit_ns, a.status);
-    if (!ok) {
-      // Drain: give every copy still in flight a bounded chance to land
-      // before the warp leaves (a copy must not outlive its shared memory).
-      failed = true;
-      mbar_wait_bounded(bars + 8 * cs, cpar, a.wait_limit_ns, nullptr);
-    } else {
-      const uint4 rec = lds128(items + (cs * 32 + lane) * kItemBytes);
-      if (rec.w != kNoBlock) {
-        const uint64_t msg = (uint64_t)rec.x | ((uint64_t)(rec.y & 0x00FFFFFFu) << 32);
-        const uint32_t s = (rec.y >> 24) & 15u;
-        const uint32_t slot = slots + (cs * 32 + lane) * kSlotBytes;
-        if constexpr (MIXED) {
-          const uint32_t alg = rec.y >> 28;
-          if (alg == HB_MD5)
-            process_block<HB_MD5>(st, slot, s, rec.z, rec.w, msg, a.digests);
-          else if (alg == HB_SHA1)
-            process_block<HB_SHA1>(st, slot, s, rec.z, rec.w, msg, a.digests);
-          else
-            process_block<HB_SM3>(st, slot, s, rec.z, rec.w, msg, a.digests);
-        } else {
-          process_block<ALG>(st, slot, s, rec.z, rec.w, msg, a.digests);
-        }
+    if (have) issue();
+    cp_async_commit();
+    cp_async_wait<STAGES - 1>();  // this lane's copies of item `cs` have landed
+    const uint4 rec = lds128(items + (cs * 32 + lane) * kItemBytes);
+    if (rec.w != kNoBlock) {
+      const uint64_t msg = (uint64_t)rec.x | ((uint64_t)(rec.y & 0x00FFFFFFu) << 32);
+      const uint32_t s = (rec.y >> 24) & 15u;
+      const uint32_t slot = slots + (cs * 32 + lane) * kSlotBytes;
+      if constexpr (MIXED) {
+        const uint32_t alg = rec.y >> 28;
+        if (alg == HB_MD5)
+          process_block<HB_MD5>(st, slot, s, rec.z, rec.w, msg, a.digests, a.mc);
+        else if (alg == HB_SHA1)
+          process_block<HB_SHA1>(st, slot, s, rec.z, rec.w, msg, a.digests, a.mc);
+        else
+          process_block<HB_SM3>(st, slot, s, rec.z, rec.w, msg, a.digests, a.mc);
+      } else {
+        process_block<ALG>(st, slot, s, rec.z, rec.w, msg, a.digests, a.mc);
       }
     }
-    __syncwarp();  // every lane is done with stage cs before it is re-armed
     --inflight;
     cs = (cs + 1 == STAGES) ? 0 : cs + 1;
-    cpar ^= (cs == 0) ? 1u : 0u;
   }
 }
 

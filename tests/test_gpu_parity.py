@@ -234,3 +234,27 @@ def test_full_size_ragged_2pow20_sampled(hb, oracle_mod):
     got = out[torch.from_numpy(idx).cuda()].cpu().numpy()
     _assert_slots_equal(got, _oracle_slots(oracle_mod, b, None, idx), "C3")
     assert hb.device_status() == 0
+
+
+def test_autotuner_installs_a_valid_shape(hb, oracle_mod, tmp_path):
+    from paper_2407_09333_b300 import autotune
+    b = workloads.fixed(20000, 55, seed=13)
+    packed, off, ln, _ = hb.to_device(b)
+    out = torch.empty((b.n, 32), dtype=torch.uint8, device="cuda")
+    path = str(tmp_path / "tune.json")
+    r = autotune.tune(2, packed, off, ln, out, path=path)
+    assert not r["cached"] and 0 <= r["shape"] < len(hb.shapes())
+    assert hb.tune_get(2) == r["shape"]
+    r2 = autotune.tune(2, packed, off, ln, out, path=path)
+    assert r2["cached"] and r2["shape"] == r["shape"]
+    got = hb.hash_batch(2, packed, off, ln).cpu().numpy()
+    _assert_slots_equal(got, _oracle_slots(oracle_mod, b, 2), "tuned")
+    hb.tune_set(2, 0)
+
+
+def test_int_peak_microbenchmark_runs(hb):
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    for op in range(13):
+        cyc = hb.int_peak(op, sms, 128, 10)
+        torch.cuda.synchronize()
+        assert int(cyc.min().item()) > 0
