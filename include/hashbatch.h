@@ -111,6 +111,33 @@ int hash_batch_mixed(const uint8_t *algs, const uint8_t *packed_bytes,
                      uint8_t *digests_out, void *stream);
 
 /*
+ * hash_batch_mixed_noalloc -- hash_batch_mixed for callers that cannot
+ * allocate device memory.  The paper has no counterpart: it exists because
+ * hash_batch_mixed may call cudaMalloc (its scratch area and the per-device
+ * context grow on demand), which some callers must avoid -- a process whose
+ * device memory belongs to another owner under a fixed budget, or a
+ * latency-critical loop that must not meet the device-wide synchronisation
+ * an allocation can cause.  This variant allocates nothing: its bucketing
+ * scratch is a fixed array of about 4.3 MB compiled into the library, held
+ * by every GPU that loads the library until the process exits.
+ *   - n must be at most HB_NOALLOC_MAX_MESSAGES; larger batches return
+ *     HB_ERR_TOO_LARGE without touching the GPU.  n == 0 is a no-op.
+ *   - The first call on a device looks up the array's device address and
+ *     the kernel's launch limits (no allocation); make that first call on
+ *     each device before any stream capture.
+ *   - All calls on a device share the array.  Each call clears what must
+ *     start at zero, but calls whose work overlaps on the GPU race on it:
+ *     order them (one stream, or events).
+ * Arguments, layout and results are those of hash_batch_mixed; the digests
+ * are identical.  Returns HB_OK, HB_ERR_TOO_LARGE, HB_ERR_NULL, HB_ERR_ALIGN
+ * or HB_ERR_CUDA.
+ */
+#define HB_NOALLOC_MAX_MESSAGES (1u << 20)
+int hash_batch_mixed_noalloc(const uint8_t *algs, const uint8_t *packed_bytes,
+                             const uint64_t *offsets, const uint32_t *lengths, uint64_t n,
+                             uint8_t *digests_out, void *stream);
+
+/*
  * hash_batch_check_bounds -- checks on the device that every message lies in
  * [0, packed_len): offsets[i] + lengths[i] <= packed_len, computed without
  * overflow.  Writes 0 to *status_dev when all messages are in bounds, else

@@ -33,6 +33,7 @@ _SIGNATURES = {
     "hash_strerror": (ctypes.c_char_p, [_c_int]),
     "hash_batch": (_c_int, [_c_int, _vp, _vp, _vp, _c_u64, _vp, _vp]),
     "hash_batch_mixed": (_c_int, [_vp, _vp, _vp, _vp, _c_u64, _vp, _vp]),
+    "hash_batch_mixed_noalloc": (_c_int, [_vp, _vp, _vp, _vp, _c_u64, _vp, _vp]),
     "hash_batch_check_bounds": (_c_int, [_vp, _vp, _c_u64, _c_u64, _vp, _vp]),
     "hash_batch_host": (_c_int, [_c_int, _vp, _vp, _c_u64, _vp, _vp, _c_u64, _vp, _vp]),
     "hash_device_status": (_c_int, [_vp, ctypes.POINTER(_c_int)]),
@@ -157,6 +158,31 @@ def hash_batch_mixed(algs, packed, offsets, lengths, out=None, stream=None,
         _dev_ptr(offsets, 8, "offsets"), _dev_ptr(lengths, 4, "lengths"), n,
         _dev_ptr(out, 1, "out"), int(shape), int(grid), _stream_handle(stream))
     _check(rc, "hash_batch_mixed")
+    return out
+
+
+NOALLOC_MAX_MESSAGES = 1 << 20
+
+
+def hash_batch_mixed_noalloc(algs, packed, offsets, lengths, out, stream=None):
+    """hash_batch_mixed without any device allocation by the library.
+
+    For callers that must not trigger cudaMalloc (device memory owned by
+    someone else under a fixed budget, or a latency-critical loop): the
+    bucketing scratch is a fixed array inside the library, so `out` must be
+    supplied and n is limited to NOALLOC_MAX_MESSAGES.  Calls that overlap on
+    the GPU share that array and must be ordered.
+    """
+    n = int(offsets.numel())
+    if lengths.numel() != n or algs.numel() != n:
+        raise ValueError("algs, offsets and lengths must have one entry per message")
+    if out.dtype.itemsize != 1 or out.numel() < n * SLOT_BYTES or not out.is_contiguous():
+        raise ValueError("out must be a contiguous uint8 tensor of n*32 bytes")
+    rc = lib().hash_batch_mixed_noalloc(
+        _dev_ptr(algs, 1, "algs"), _dev_ptr(packed, 1, "packed"),
+        _dev_ptr(offsets, 8, "offsets"), _dev_ptr(lengths, 4, "lengths"), n,
+        _dev_ptr(out, 1, "out"), _stream_handle(stream))
+    _check(rc, "hash_batch_mixed_noalloc")
     return out
 
 
