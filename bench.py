@@ -222,7 +222,11 @@ def shard_seed(base: int, rank: int) -> int:
 # ---------------------------------------------------------------------------
 # workloads
 
-def make_workload(name: str, rank: int):
+def make_workload(name: str, rank: int, messages: int = 0):
+    if name == "c3" and messages:
+        return ("ragged mixed-algorithm batch: %d messages, log-uniform lengths in [0, 64 KiB], "
+                "1%% at padding boundaries, algorithm per message" % messages,
+                workloads.ragged(messages, shard_seed(2, rank)), True)
     if name == "c1":
         return ("plain fixed-length batch: 4096 messages x 64 B, MD5+SHA-1+SM3 per step",
                 workloads.fixed(4096, 64, shard_seed(0, rank)), False)
@@ -283,7 +287,7 @@ def cpu_baseline(batch, mixed: bool, target_s: float = 10.0, cap_s: float = 30.0
 def run_reference(args, dist):
     if dist.rank != 0:
         return
-    desc, batch, mixed = make_workload(args.workload, 0)
+    desc, batch, mixed = make_workload(args.workload, 0, args.messages)
     import oracle
     threads = oracle.host_threads()
     sub = oracle_sample(batch, mixed, 1 << 18 if args.workload != "c4" else 1 << 10)
@@ -346,7 +350,7 @@ def run_ours(args, dist):
         torch.cuda.set_device(dist.local_rank)
     build.build()
     api.lib()
-    desc, batch, mixed = make_workload(args.workload, dist.rank)
+    desc, batch, mixed = make_workload(args.workload, dist.rank, args.messages)
     packed, off, ln, algs = api.to_device(batch)
     n = batch.n
     out = torch.empty((n, 32), dtype=torch.uint8, device="cuda")
@@ -359,9 +363,26 @@ def run_ours(args, dist):
     tuned = {}
     mean_len = batch.total_bytes / max(n, 1)
     for a in ([None] if mixed else [0, 1, 2]):
+        if args.shape is not None:
+            # fixed launch configuration (reproducible profiler captures)
+            api.tune_set(api.TUNE_MIXED if a is None else a, args.shape)
+            if a is None and args.buckets:
+                api.tune_buckets(*[int(x) for x in args.buckets.split(",")])
+            w, st, kb, co = api.shapes()[args.shape]
+            tuned["mixed" if a is None else ALG_NAMES[a]] = {"warps": w, "stages": st,
+                                                              "blocks_per_stage": kb,
+                                                              "cooperative": bool(co), "fixed": True}
+            continue
         r = autotune.tune(a, packed, off, ln, out, algs=algs, mean_len=mean_len)
         tuned["mixed" if a is None else ALG_NAMES[a]] = {"warps": r["warps"], "stages": r["stages"],
+                                                          "blocks_per_stage": r.get("blocks_per_stage", 1),
+                                                          "cooperative": r.get("cooperative", False),
                                                           "cached": r["cached"]}
+        if "buckets" in r:
+            tuned["mixed"]["buckets_per_octave"] = 1 << r["buckets"][0]
+            tuned["mixed"]["algorithm_major"] = bool(r["buckets"][1])
+        if "warps_per_sm" in r:
+            tuned["mixed"]["warps_per_sm"] = r["warps_per_sm"] or "occupancy"
 
     if mixed:
         launches = [(None, lambda: api.hash_batch_mixed(algs, packed, off, ln, out=out))]
@@ -533,6 +554,12 @@ def main(argv=None):
     p.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4"])
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--e2e-steps", type=int, default=10)
+    p.add_argument("--shape", type=int, default=None,
+                   help="fixed launch shape index instead of the autotuner's choice")
+    p.add_argument("--buckets", default="",
+                   help="fixed ragged bucketing 'sub_log2,alg_major' (with --shape)")
+    p.add_argument("--messages", type=int, default=0,
+                   help="message count of the ragged workload (default 2^20); smaller for profiling")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--int-peak", action="store_true",

@@ -118,7 +118,7 @@ int hash_batch_mixed(const uint8_t *algs, const uint8_t *packed_bytes,
  * device memory belongs to another owner under a fixed budget, or a
  * latency-critical loop that must not meet the device-wide synchronisation
  * an allocation can cause.  This variant allocates nothing: its bucketing
- * scratch is a fixed array of about 4.3 MB compiled into the library, held
+ * scratch is a fixed array of about 4.34 MB compiled into the library, held
  * by every GPU that loads the library until the process exits.
  *   - n must be at most HB_NOALLOC_MAX_MESSAGES; larger batches return
  *     HB_ERR_TOO_LARGE without touching the GPU.  n == 0 is a no-op.
@@ -178,7 +178,11 @@ int hash_release_device(void);
 
 /*
  * Tuning.  The hashing kernels are instantiated for a few launch shapes
- * (warps per block x bulk-copy stages in flight per warp).  hash_tune_set
+ * (warps per block x copy stages in flight per warp x 64-byte blocks staged
+ * per lane and stage x copy mapping: each lane copying its own message, or
+ * the warp copying message after message with consecutive lanes on
+ * consecutive 16-byte pieces, which keeps one copy instruction within two or
+ * three messages).  hash_tune_set
  * selects the shape that hash_batch uses for `alg`, or that the ragged path
  * uses when alg == HB_TUNE_MIXED; hash_tune_get reads the selection;
  * hash_tune_shape describes shape `index` and hash_tune_occupancy returns
@@ -188,10 +192,31 @@ int hash_release_device(void);
  */
 #define HB_TUNE_MIXED 3
 int hash_tune_shapes(void);
-int hash_tune_shape(int index, int *warps_per_block, int *stages);
+int hash_tune_shape(int index, int *warps_per_block, int *stages, int *blocks_per_stage,
+                    int *cooperative);
 int hash_tune_set(int alg, int shape_index);
 int hash_tune_get(int alg);
 int hash_tune_occupancy(int alg, int shape_index);
+
+/*
+ * hash_tune_buckets -- bucketing of the ragged path on the current device:
+ * each octave of estimated per-message cost (padded blocks x relative cost of
+ * the algorithm's block) is split into 2^sub_log2 buckets (0 <= sub_log2 <=
+ * 3; finer buckets give chunks of more equal length), and with alg_major = 1
+ * the chunk order runs through all SM3 messages, then SHA-1, then MD5, each
+ * longest first, instead of interleaving the algorithms.  Digests do not
+ * depend on either choice.  Defaults: sub_log2 = 2, alg_major = 0.
+ */
+int hash_tune_buckets(int sub_log2, int alg_major);
+
+/*
+ * hash_tune_mixed_warps -- resident warps per SM of the persistent ragged
+ * kernel on the current device (0 = as many as fit).  A long message is a
+ * serial chain of blocks, so the warp that holds it should not share its SM
+ * sub-partition with many other busy warps; default 8 (two per
+ * sub-partition).  Returns HB_ERR_ARG outside [0, 64].
+ */
+int hash_tune_mixed_warps(int warps_per_sm);
 
 /*
  * hash_batch_shape / hash_batch_mixed_shape -- hash_batch / hash_batch_mixed

@@ -39,10 +39,13 @@ _SIGNATURES = {
     "hash_device_status": (_c_int, [_vp, ctypes.POINTER(_c_int)]),
     "hash_release_device": (_c_int, []),
     "hash_tune_shapes": (_c_int, []),
-    "hash_tune_shape": (_c_int, [_c_int, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int)]),
+    "hash_tune_shape": (_c_int, [_c_int, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int),
+                                 ctypes.POINTER(_c_int), ctypes.POINTER(_c_int)]),
     "hash_tune_set": (_c_int, [_c_int, _c_int]),
     "hash_tune_get": (_c_int, [_c_int]),
     "hash_tune_occupancy": (_c_int, [_c_int, _c_int]),
+    "hash_tune_buckets": (_c_int, [_c_int, _c_int]),
+    "hash_tune_mixed_warps": (_c_int, [_c_int]),
     "hash_batch_shape": (_c_int, [_c_int, _vp, _vp, _vp, _c_u64, _vp, _c_int, _c_int, _vp]),
     "hash_batch_mixed_shape": (_c_int, [_vp, _vp, _vp, _vp, _c_u64, _vp, _c_int, _c_int, _vp]),
     "hash_int_peak": (_c_int, [_c_int, _c_int, _c_int, _c_int, _vp, _vp, _vp]),
@@ -244,13 +247,16 @@ def selftest_wait_timeout(timeout_ns: int, stream=None):
 # ---------------------------------------------------------------------------
 # tuning
 
-def shapes() -> list[tuple[int, int]]:
+def shapes() -> list[tuple[int, int, int, int]]:
+    """Launch shapes: (warps per block, stages per warp, blocks per stage,
+    cooperative copies 0/1)."""
     L = lib()
     out = []
     for i in range(L.hash_tune_shapes()):
-        w, s = ctypes.c_int(0), ctypes.c_int(0)
-        _check(L.hash_tune_shape(i, ctypes.byref(w), ctypes.byref(s)), "hash_tune_shape")
-        out.append((int(w.value), int(s.value)))
+        w, s, k, c = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+        _check(L.hash_tune_shape(i, ctypes.byref(w), ctypes.byref(s), ctypes.byref(k),
+                                 ctypes.byref(c)), "hash_tune_shape")
+        out.append((int(w.value), int(s.value), int(k.value), int(c.value)))
     return out
 
 
@@ -263,6 +269,14 @@ def tune_get(alg: int) -> int:
     if rc < 0:
         raise HashBatchError(rc, "hash_tune_get")
     return rc
+
+
+def tune_buckets(sub_log2: int, alg_major: bool):
+    _check(lib().hash_tune_buckets(int(sub_log2), int(bool(alg_major))), "hash_tune_buckets")
+
+
+def tune_mixed_warps(warps_per_sm: int):
+    _check(lib().hash_tune_mixed_warps(int(warps_per_sm)), "hash_tune_mixed_warps")
 
 
 def tune_occupancy(alg: int, shape: int) -> int:

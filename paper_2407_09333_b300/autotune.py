@@ -84,19 +84,53 @@ def tune(alg, packed, offsets, lengths, out, algs=None, mean_len: float | None =
     cache = load_cache(path) if use_cache else {}
     if key in cache and 0 <= cache[key]["shape"] < len(shapes):
         api.tune_set(tune_alg, cache[key]["shape"])
+        if alg is None and "buckets" in cache[key]:
+            api.tune_buckets(*cache[key]["buckets"])
+        if alg is None and "warps_per_sm" in cache[key]:
+            api.tune_mixed_warps(cache[key]["warps_per_sm"])
         return dict(cache[key], cached=True)
 
-    timings = {}
-    for idx in range(len(shapes)):
+    def run(idx):
         if alg is None:
-            fn = lambda idx=idx: api.hash_batch_mixed(algs, packed, offsets, lengths, out=out, shape=idx)
-        else:
-            fn = lambda idx=idx: api.hash_batch(alg, packed, offsets, lengths, out=out, shape=idx)
-        timings[idx] = _time_ms(torch, fn, reps)
-    best = min(timings, key=timings.get)
+            return lambda: api.hash_batch_mixed(algs, packed, offsets, lengths, out=out, shape=idx)
+        return lambda: api.hash_batch(alg, packed, offsets, lengths, out=out, shape=idx)
+
+    result = {"key": key}
+    if alg is None:
+        # Ragged path: bucket resolution and ordering first (default shape),
+        # then the launch shape with the chosen bucketing.
+        api.tune_mixed_warps(8)
+        btimes = {}
+        for sub in (1, 2, 3):
+            for major in (0, 1):
+                api.tune_buckets(sub, major)
+                btimes[(sub, major)] = _time_ms(torch, run(api.tune_get(api.TUNE_MIXED)), reps)
+        bbest = min(btimes, key=btimes.get)
+        api.tune_buckets(*bbest)
+        result["buckets"] = list(bbest)
+        result["bucket_ms"] = {"%d,%d" % k: v for k, v in btimes.items()}
+    timings = {}
+    if alg is None:
+        # launch shape x resident warps per SM (the persistent kernel's grid)
+        for idx in range(len(shapes)):
+            for wps in (8, 12, 16, 0):
+                if wps and wps % shapes[idx][0]:
+                    continue
+                api.tune_mixed_warps(wps)
+                timings[(idx, wps)] = _time_ms(torch, run(idx), reps)
+        (best, best_wps) = min(timings, key=timings.get)
+        api.tune_mixed_warps(best_wps)
+        result["warps_per_sm"] = best_wps
+        ms = {"%d,%d" % k: v for k, v in timings.items()}
+    else:
+        for idx in range(len(shapes)):
+            timings[idx] = _time_ms(torch, run(idx), reps)
+        best = min(timings, key=timings.get)
+        ms = {str(k): v for k, v in timings.items()}
     api.tune_set(tune_alg, best)
-    result = {"shape": best, "warps": shapes[best][0], "stages": shapes[best][1],
-              "ms": {str(k): v for k, v in timings.items()}, "key": key}
+    result.update({"shape": best, "warps": shapes[best][0], "stages": shapes[best][1],
+                   "blocks_per_stage": shapes[best][2], "cooperative": bool(shapes[best][3]),
+                   "ms": ms})
     if use_cache:
         cache = load_cache(path)
         cache[key] = result

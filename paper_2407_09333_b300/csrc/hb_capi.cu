@@ -57,7 +57,9 @@ struct Ctx {
   int occ_plain[3][kMaxShapes] = {};     // resident blocks per SM, 0 = not prepared
   int occ_mixed[kMaxShapes] = {};
   int tune_plain[3] = {0, 0, 0};
-  int tune_mixed = 0;
+  int tune_mixed = hb::kDefaultMixedShape;
+  int mixed_warps_per_sm = hb::kDefaultMixedWarpsPerSm;  // 0 = full occupancy
+  hb::BucketCfg buckets = hb::kDefaultBuckets;
   DeviceBuf ws;                          // ragged-path scratch
   cudaEvent_t ws_event = nullptr;        // last use of `ws`
   bool ws_used = false;
@@ -140,6 +142,7 @@ int launch_mixed(Ctx* c, int shape, int grid, const uint8_t* algs, const uint8_t
                  void* ws, const int* abort_flag, cudaStream_t s) {
   if (shape < 0 || shape >= hb::num_shapes()) return HB_ERR_ARG;
   MixedArgs m;
+  m.cfg = c->buckets;
   m.algs = algs;
   m.lengths = lengths;
   m.n = n;
@@ -165,7 +168,15 @@ int launch_mixed(Ctx* c, int shape, int grid, const uint8_t* algs, const uint8_t
   a.abort_flag = abort_flag;
   a.wait_limit_ns = g_wait_limit_ns;
   a.mc = hb::make_mul_consts();
-  if (grid <= 0) grid = c->sms * occ;
+  if (grid <= 0) {
+    int per_sm = occ;
+    if (c->mixed_warps_per_sm > 0) {
+      int warps = 0, stages = 0;
+      hb::shape_desc(shape, &warps, &stages);
+      per_sm = std::min(occ, std::max(1, c->mixed_warps_per_sm / warps));
+    }
+    grid = c->sms * per_sm;
+  }
   e = hb::launch_hash(true, 0, shape, grid, a, s);
   return e == cudaSuccess ? HB_OK : cuda_fail(e);
 }
@@ -387,9 +398,11 @@ int hash_release_device(void) {
 
 int hash_tune_shapes(void) { return hb::num_shapes(); }
 
-int hash_tune_shape(int index, int* warps_per_block, int* stages) {
-  if (!warps_per_block || !stages) return HB_ERR_NULL;
-  return hb::shape_desc(index, warps_per_block, stages) ? HB_OK : HB_ERR_ARG;
+int hash_tune_shape(int index, int* warps_per_block, int* stages, int* blocks_per_stage,
+                    int* cooperative) {
+  if (!warps_per_block || !stages || !blocks_per_stage || !cooperative) return HB_ERR_NULL;
+  return hb::shape_desc(index, warps_per_block, stages, blocks_per_stage, cooperative) ? HB_OK
+                                                                                        : HB_ERR_ARG;
 }
 
 int hash_tune_set(int alg, int shape_index) {
@@ -411,6 +424,25 @@ int hash_tune_get(int alg) {
   if (alg == HB_TUNE_MIXED) return c->tune_mixed;
   if (hash_digest_size(alg) == 0) return HB_ERR_INVALID_ALG;
   return c->tune_plain[alg];
+}
+
+int hash_tune_mixed_warps(int warps_per_sm) {
+  if (warps_per_sm < 0 || warps_per_sm > 64) return HB_ERR_ARG;
+  Ctx* c = nullptr;
+  int rc = get_ctx(&c);
+  if (rc) return rc;
+  c->mixed_warps_per_sm = warps_per_sm;
+  return HB_OK;
+}
+
+int hash_tune_buckets(int sub_log2, int alg_major) {
+  if (sub_log2 < 0 || sub_log2 > 3 || (alg_major != 0 && alg_major != 1)) return HB_ERR_ARG;
+  Ctx* c = nullptr;
+  int rc = get_ctx(&c);
+  if (rc) return rc;
+  c->buckets.sub_log2 = (uint32_t)sub_log2;
+  c->buckets.alg_major = (uint32_t)alg_major;
+  return HB_OK;
 }
 
 int hash_tune_occupancy(int alg, int shape_index) {

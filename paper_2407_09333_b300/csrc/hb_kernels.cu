@@ -22,17 +22,17 @@ namespace hb {
 // ---------------------------------------------------------------------------
 // Fixed-algorithm kernel.
 
-template <int ALG, int WARPS, int STAGES>
+template <int ALG, int WARPS, int STAGES, int KB, bool COOP>
 __global__ void __launch_bounds__(WARPS * 32) hb_plain_kernel(KernelArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t warp = threadIdx.x >> 5;
   if (a.abort_flag && *a.abort_flag) return;
-  uint8_t* wsm = smem + warp * WarpSmem<STAGES>::kBytes;
+  uint8_t* wsm = smem + warp * WarpSmem<STAGES, KB>::kBytes;
   const uint64_t gwarp = (uint64_t)blockIdx.x * WARPS + warp;
   const uint64_t nwarps = (uint64_t)gridDim.x * WARPS;
   StaticSource<ALG> src(a, gwarp, nwarps, lane);
-  warp_pipeline<STAGES, ALG, false>(src, wsm, a, lane);
+  warp_pipeline<STAGES, KB, COOP, ALG, false>(src, wsm, a, lane);
 }
 
 // ---------------------------------------------------------------------------
@@ -40,13 +40,21 @@ __global__ void __launch_bounds__(WARPS * 32) hb_plain_kernel(KernelArgs a) {
 
 // Relative cost of one block: MD5 : SHA-1 : SM3 ~ 4 : 7 : 17 (their counted
 // 32-bit operations per block, about 330 : 610 : 1410).
-__device__ __forceinline__ uint32_t cost_group(uint32_t len, uint32_t alg) {
+__device__ __forceinline__ uint32_t cost_group(uint32_t len, uint32_t alg, BucketCfg cfg) {
   const uint32_t w = alg == HB_MD5 ? 4u : alg == HB_SHA1 ? 7u : 17u;
   const uint32_t c = padded_blocks(len) * w;  // < 2^27 * 17 < 2^32
   const int e = 31 - __clz(c);                // floor(log2 c), c >= 4
-  const uint32_t frac = (c >> (e - 2)) & 3u;  // two bits below the leading one
-  const uint32_t bucket = (uint32_t)e * 4u + frac;  // < kCostBuckets
-  return (kCostBuckets - 1u - bucket) * 3u + alg;   // most expensive first
+  const int sub = (int)cfg.sub_log2;
+  const uint32_t mask = (1u << sub) - 1u;
+  // the `sub` bits below the leading one
+  const uint32_t frac = e >= sub ? (c >> (e - sub)) & mask : (c << (sub - e)) & mask;
+  const uint32_t bucket = ((uint32_t)e << sub) + frac;  // < kCostBuckets
+  const uint32_t desc = kCostBuckets - 1u - bucket;     // most expensive first
+  if (cfg.alg_major) {
+    const uint32_t rank = alg == HB_SM3 ? 0u : alg == HB_SHA1 ? 1u : 2u;
+    return rank * kCostBuckets + desc;
+  }
+  return desc * 3u + alg;
 }
 
 __global__ void hb_hist_kernel(MixedArgs m) {
@@ -57,7 +65,7 @@ __global__ void hb_hist_kernel(MixedArgs m) {
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m.n; i += stride) {
     const uint32_t alg = m.algs[i];
     if (alg <= HB_SM3) {
-      atomicAdd(&counts[cost_group(m.lengths[i], alg)], 1u);
+      atomicAdd(&counts[cost_group(m.lengths[i], alg, m.cfg)], 1u);
     } else {
       // Unknown code: the slot stays all zero and the message is not hashed.
       uint8_t* dst = m.digests + i * HB_SLOT_BYTES;
@@ -104,7 +112,7 @@ __global__ void hb_scatter_kernel(MixedArgs m) {
     uint32_t key = 0xFFFFFFFFu;
     if (i < m.n) {
       const uint32_t alg = m.algs[i];
-      if (alg <= HB_SM3) key = cost_group(m.lengths[i], alg);
+      if (alg <= HB_SM3) key = cost_group(m.lengths[i], alg, m.cfg);
     }
     // Warp-aggregated reservation: one atomic per distinct group in the warp.
     const uint32_t peers = __match_any_sync(kFull, key);
@@ -117,15 +125,15 @@ __global__ void hb_scatter_kernel(MixedArgs m) {
   }
 }
 
-template <int WARPS, int STAGES>
+template <int WARPS, int STAGES, int KB, bool COOP>
 __global__ void __launch_bounds__(WARPS * 32) hb_mixed_kernel(KernelArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t warp = threadIdx.x >> 5;
   if (a.abort_flag && *a.abort_flag) return;
-  uint8_t* wsm = smem + warp * WarpSmem<STAGES>::kBytes;
+  uint8_t* wsm = smem + warp * WarpSmem<STAGES, KB>::kBytes;
   DynamicSource src(a, lane);
-  warp_pipeline<STAGES, HB_MD5, true>(src, wsm, a, lane);
+  warp_pipeline<STAGES, KB, COOP, HB_MD5, true>(src, wsm, a, lane);
 }
 
 // ---------------------------------------------------------------------------
@@ -223,54 +231,75 @@ __global__ void hb_selftest_wait_kernel(uint64_t limit_ns, int* status) {
 // ---------------------------------------------------------------------------
 // Launch shapes and host launchers.
 
+// Launch shapes: (warps per block, stages in flight per warp, blocks per
+// stage, cooperative copies).  The table is the single list every kernel is
+// instantiated for.
+#define HB_SHAPES(X)     \
+  X(0, 4, 4, 1, false)   \
+  X(1, 4, 2, 1, false)   \
+  X(2, 8, 3, 1, false)   \
+  X(3, 1, 4, 1, false)   \
+  X(4, 2, 3, 1, false)   \
+  X(5, 16, 2, 1, false)  \
+  X(6, 8, 2, 4, false)   \
+  X(7, 4, 3, 4, false)   \
+  X(8, 8, 2, 2, false)   \
+  X(9, 4, 2, 4, false)   \
+  X(10, 4, 3, 4, true)   \
+  X(11, 8, 2, 4, true)   \
+  X(12, 16, 2, 1, true)  \
+  X(13, 4, 4, 1, true)   \
+  X(14, 8, 2, 2, true)
+
 struct ShapeDesc {
-  int warps, stages;
+  int warps, stages, kb;
+  bool coop;
 };
-static const ShapeDesc kShapes[] = {{4, 4}, {4, 2}, {8, 3}, {1, 4}, {2, 3}, {16, 2}};
+#define HB_SHAPE_DESC(i, w, st, kb, co) {w, st, kb, co},
+static const ShapeDesc kShapes[] = {HB_SHAPES(HB_SHAPE_DESC)};
 static constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 
 using KernelFn = void (*)(KernelArgs);
 
 template <int ALG>
 static KernelFn plain_fn(int shape) {
+#define HB_PLAIN_CASE(i, w, st, kb, co) \
+  case i: return hb_plain_kernel<ALG, w, st, kb, co>;
   switch (shape) {
-    case 0: return hb_plain_kernel<ALG, 4, 4>;
-    case 1: return hb_plain_kernel<ALG, 4, 2>;
-    case 2: return hb_plain_kernel<ALG, 8, 3>;
-    case 3: return hb_plain_kernel<ALG, 1, 4>;
-    case 4: return hb_plain_kernel<ALG, 2, 3>;
-    case 5: return hb_plain_kernel<ALG, 16, 2>;
+    HB_SHAPES(HB_PLAIN_CASE)
     default: return nullptr;
   }
+#undef HB_PLAIN_CASE
 }
 
 static KernelFn mixed_fn(int shape) {
+#define HB_MIXED_CASE(i, w, st, kb, co) \
+  case i: return hb_mixed_kernel<w, st, kb, co>;
   switch (shape) {
-    case 0: return hb_mixed_kernel<4, 4>;
-    case 1: return hb_mixed_kernel<4, 2>;
-    case 2: return hb_mixed_kernel<8, 3>;
-    case 3: return hb_mixed_kernel<1, 4>;
-    case 4: return hb_mixed_kernel<2, 3>;
-    case 5: return hb_mixed_kernel<16, 2>;
+    HB_SHAPES(HB_MIXED_CASE)
     default: return nullptr;
   }
+#undef HB_MIXED_CASE
 }
 
 static int shape_smem(int shape) {
-  const ShapeDesc d = kShapes[shape];
-  switch (d.stages) {
-    case 2: return d.warps * WarpSmem<2>::kBytes;
-    case 3: return d.warps * WarpSmem<3>::kBytes;
-    default: return d.warps * WarpSmem<4>::kBytes;
+#define HB_SMEM_CASE(i, w, st, kb, co) \
+  case i: return w * WarpSmem<st, kb>::kBytes;
+  switch (shape) {
+    HB_SHAPES(HB_SMEM_CASE)
+    default: return 0;
   }
+#undef HB_SMEM_CASE
 }
 
 int num_shapes() { return kNumShapes; }
 
-bool shape_desc(int shape, int* warps, int* stages) {
+bool shape_desc(int shape, int* warps, int* stages, int* kb, int* coop) {
   if (shape < 0 || shape >= kNumShapes) return false;
   *warps = kShapes[shape].warps;
   *stages = kShapes[shape].stages;
+  if (kb) *kb = kShapes[shape].kb;
+  if (coop) *coop = kShapes[shape].coop ? 1 : 0;
   return true;
 }
 

@@ -43,9 +43,31 @@ struct KernelArgs {
 };
 
 // Ragged-path bucketing: groups are (cost bucket, algorithm) pairs ordered
-// from the most to the least expensive estimated work per message.
-constexpr uint32_t kCostBuckets = 128;
+// from the most to the least expensive estimated work per message.  Cost
+// buckets split each octave of estimated cost into 2^sub_log2 parts
+// (sub_log2 <= 3, so at most 32 * 8 buckets).  With alg_major the order is
+// all SM3 groups, then SHA-1, then MD5 (each longest first), so that warps
+// running at the same time mostly run the same algorithm; otherwise the
+// algorithms interleave bucket by bucket (strict longest-first).
+constexpr uint32_t kCostBuckets = 256;
 constexpr uint32_t kGroups = kCostBuckets * 3;
+
+struct BucketCfg {
+  uint32_t sub_log2;   // 0..3
+  uint32_t alg_major;  // 0 or 1
+};
+
+constexpr BucketCfg kDefaultBuckets = {2u, 0u};
+
+// Default launch of the persistent ragged kernel: shape 10 (4 warps, 3 stages
+// of 4 blocks, cooperative copies) with 8 resident warps per SM, i.e. two per
+// SM sub-partition.  A
+// long message is a serial chain of blocks; with more co-resident warps its
+// warp gets a smaller share of the sub-partition's issue slots and the
+// longest chains finish last (MD5 saturates a sub-partition at about four
+// warps, SHA-1 and SM3 at two).
+constexpr int kDefaultMixedShape = 10;
+constexpr int kDefaultMixedWarpsPerSm = 8;
 
 // Device scratch of the ragged path; followed in memory by the permutation
 // array of (n + 31 * kGroups) uint32 entries.
@@ -62,6 +84,7 @@ inline size_t mixed_workspace_bytes(uint64_t n) {
 }
 
 struct MixedArgs {
+  BucketCfg cfg;
   const uint8_t* algs;
   const uint32_t* lengths;
   uint64_t n;
@@ -71,7 +94,7 @@ struct MixedArgs {
 };
 
 int num_shapes();
-bool shape_desc(int shape, int* warps, int* stages);
+bool shape_desc(int shape, int* warps, int* stages, int* kb = nullptr, int* coop = nullptr);
 int shape_smem_bytes(int shape);
 
 // Sets the kernel's shared-memory attribute and returns its occupancy.

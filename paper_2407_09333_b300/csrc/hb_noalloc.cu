@@ -30,7 +30,7 @@
 namespace {
 
 constexpr uint64_t kMaxMessages = HB_NOALLOC_MAX_MESSAGES;
-constexpr int kShape = 0;             // launch shape (warps x stages), same digests for all
+constexpr int kShape = hb::kDefaultMixedShape;  // launch shape; digests do not depend on it
 constexpr size_t kStatusBytes = 256;  // status word, kept in its own 256-byte line
 constexpr size_t kScratchBytes =
     kStatusBytes + sizeof(hb::MixedWorkspace) + (kMaxMessages + 31ull * hb::kGroups) * sizeof(uint32_t);
@@ -69,7 +69,9 @@ int setup_current_device(DeviceSetup** out) {
     if (hb::prepare_kernel(true, 0, kShape, &occ) != cudaSuccess) return HB_ERR_CUDA;
     s.scratch = static_cast<uint8_t*>(p);
     s.sms = sms;
-    s.blocks_per_sm = occ > 0 ? occ : 1;
+    int warps = 0, stages = 0;
+    hb::shape_desc(kShape, &warps, &stages);
+    s.blocks_per_sm = std::max(1, std::min(occ, hb::kDefaultMixedWarpsPerSm / warps));
     s.ready = true;
   }
   *out = &s;
@@ -95,6 +97,7 @@ extern "C" int hash_batch_mixed_noalloc(const uint8_t* algs, const uint8_t* pack
   uint32_t* perm = reinterpret_cast<uint32_t*>(s->scratch + kStatusBytes + sizeof(hb::MixedWorkspace));
 
   hb::MixedArgs m;
+  m.cfg = hb::kDefaultBuckets;
   m.algs = algs;
   m.lengths = lengths;
   m.n = n;

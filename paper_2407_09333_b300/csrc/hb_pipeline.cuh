@@ -2,14 +2,16 @@
 // algorithm and the ragged (mixed-algorithm) kernels.
 //
 // Unit of work.  A warp owns a "task" of 32 messages, one per lane, and walks
-// them block by block (64-byte blocks of the padded message).  An "item" is
-// one block step of one task: for each lane, the 64-byte window of its
-// message at that block.
+// them block by block (64-byte blocks of the padded message).  An "item"
+// (stage) is KB block steps of one task: for each lane, the window of its
+// message covering those KB blocks.
 //
-// Staging.  Every lane stages its own window into a private 80-byte slot of
-// shared memory with four or five asynchronous 16-byte copies (cp.async,
-// LDGSTS): the copies cover the 16-byte aligned granules that hold the
-// window, so the window's first byte lands at slot + (addr & 15).  Granules
+// Staging.  Every lane stages its own window of KB blocks (64*KB bytes) into a
+// private slot of 64*KB + 16 bytes of shared memory with 4*KB or 4*KB + 1
+// asynchronous 16-byte copies (cp.async, LDGSTS): the copies cover the
+// 16-byte aligned granules that hold the window, so the window's first byte
+// lands at slot + (addr & 15).  Larger KB means fewer, larger requests per
+// lane, which matters when the 32 lanes of a warp read 32 distant places.  Granules
 // are zero-filled past the message end by the copy itself (src-size), so a
 // window that runs past the end of its message already holds zeros there.
 // STAGES items are in flight: the warp issues item j + STAGES - 1 before it
@@ -36,16 +38,22 @@
 
 namespace hb {
 
-constexpr int kSlotBytes = 80;   // 64-byte window + up to 15 lead bytes, rounded to 16
+// A stage holds KB consecutive blocks of each lane's message: a window of
+// 64*KB bytes plus up to 15 lead bytes, rounded to 16.
+template <int KB>
+struct Slot {
+  static constexpr int kBytes = 64 * KB + 16;
+};
 constexpr int kItemBytes = 16;   // item record per lane per stage
 constexpr uint32_t kFull = 0xFFFFFFFFu;
 constexpr uint32_t kNoBlock = 0xFFFFFFFFu;
 
-template <int STAGES>
+template <int STAGES, int KB>
 struct WarpSmem {
-  static constexpr int kSlots = STAGES * 32 * kSlotBytes;
+  static constexpr int kSlots = STAGES * 32 * Slot<KB>::kBytes;
   static constexpr int kItems = STAGES * 32 * kItemBytes;
-  static constexpr int kBytes = kSlots + kItems;  // multiple of 128
+  static constexpr int kTable = 32 * 16;  // per-lane copy descriptors (cooperative copies)
+  static constexpr int kBytes = kSlots + kItems + kTable;  // multiple of 128
 };
 
 // Padded block count: message + 0x80 + 8 length bytes, rounded up to 64.
@@ -103,6 +111,8 @@ struct StaticSource {
     next += stride;
   }
 
+  __device__ __forceinline__ void hint(uint32_t) {}
+
   // Move to the next task; false when the source is exhausted.
   __device__ __forceinline__ bool take(LaneTask& t) {
     if (!pf_ok) return false;
@@ -118,8 +128,11 @@ struct StaticSource {
 };
 
 // Mixed algorithms: chunks of 32 bucketed messages popped from a shared
-// counter in order (longest estimated cost first).  Three-deep prefetch:
-// popped chunk id -> permutation entry -> message metadata.
+// counter in order (longest estimated cost first).  A warp reserves its next
+// chunk only while it issues the last items of the current one, so no chunk
+// is tied to a warp long before the warp can start it: the pop, the
+// permutation load and the metadata loads are spread over the last three
+// items (hint), and `take` finishes whatever is still outstanding.
 struct DynamicSource {
   const uint8_t* packed;
   const uint64_t* offsets;
@@ -128,36 +141,11 @@ struct DynamicSource {
   const uint32_t* perm;
   uint32_t* counter;
   uint32_t lane, nchunks;
-  uint32_t pf_chunk;        // popped id, perm entry not yet loaded
-  uint32_t pf_perm_chunk;   // chunk whose perm entry is in pf_msg
-  uint32_t pf_msg;          // perm entry of pf_perm_chunk
-  uint32_t pf_meta_chunk;   // chunk whose metadata is in pf_*
-  uint32_t pf_msg2;
-  uint64_t pf_off;
-  uint32_t pf_len, pf_alg;
-
-  __device__ __forceinline__ uint32_t pop() {
-    uint32_t c = 0;
-    if (lane == 0) c = atomicAdd(counter, 1u);
-    return __shfl_sync(kFull, c, 0);
-  }
-
-  __device__ __forceinline__ uint32_t load_perm(uint32_t chunk) {
-    return chunk < nchunks ? ldg_nc_u32(perm + (uint64_t)chunk * 32 + lane) : 0xFFFFFFFFu;
-  }
-
-  __device__ __forceinline__ void load_meta(uint32_t chunk, uint32_t msg) {
-    pf_meta_chunk = chunk;
-    pf_msg2 = msg;
-    pf_off = 0;
-    pf_len = 0;
-    pf_alg = 0;
-    if (chunk < nchunks && msg != 0xFFFFFFFFu) {
-      pf_off = ldg_nc_u64(offsets + msg);
-      pf_len = ldg_nc_u32(lengths + msg);
-      pf_alg = __ldg(algs + msg);
-    }
-  }
+  int stage;         // 0 nothing reserved, 1 popped, 2 perm loaded, 3 metadata loaded
+  uint32_t chunk;    // reserved chunk id (stage >= 1)
+  uint32_t msg;      // this lane's message in it (stage >= 2)
+  uint64_t off;      // stage 3
+  uint32_t len, alg;
 
   __device__ DynamicSource(const KernelArgs& args, uint32_t lane_)
       : packed(args.packed),
@@ -166,29 +154,54 @@ struct DynamicSource {
         algs(args.algs),
         perm(args.perm),
         counter(args.chunk_counter),
-        lane(lane_) {
+        lane(lane_),
+        stage(0) {
     nchunks = *args.nchunks;
-    const uint32_t c0 = pop();
-    load_meta(c0, load_perm(c0));
-    pf_perm_chunk = pop();
-    pf_msg = load_perm(pf_perm_chunk);
-    pf_chunk = pop();
+  }
+
+  // One more step towards having the next chunk ready (warp-uniform).
+  __device__ __forceinline__ void advance() {
+    if (stage == 0) {
+      uint32_t c = 0;
+      if (lane == 0) c = atomicAdd(counter, 1u);
+      chunk = __shfl_sync(kFull, c, 0);
+      stage = 1;
+    } else if (stage == 1) {
+      msg = chunk < nchunks ? ldg_nc_u32(perm + (uint64_t)chunk * 32 + lane) : 0xFFFFFFFFu;
+      stage = 2;
+    } else if (stage == 2) {
+      off = 0;
+      len = 0;
+      alg = 0;
+      if (chunk < nchunks && msg != 0xFFFFFFFFu) {
+        off = ldg_nc_u64(offsets + msg);
+        len = ldg_nc_u32(lengths + msg);
+        alg = __ldg(algs + msg);
+      }
+      stage = 3;
+    }
+  }
+
+  // Called after each issued item with the items left in the current task.
+  __device__ __forceinline__ void hint(uint32_t items_left) {
+    if (items_left <= 3) advance();
   }
 
   __device__ __forceinline__ bool take(LaneTask& t) {
-    if (pf_meta_chunk >= nchunks) return false;
-    const bool valid = pf_msg2 != 0xFFFFFFFFu;
-    t.msg = pf_msg2;
-    t.addr = reinterpret_cast<uint64_t>(packed) + pf_off;
-    t.len = pf_len;
-    t.nb = valid ? padded_blocks(pf_len) : 0u;
+    while (stage < 3) advance();
+    stage = 0;
+    if (chunk >= nchunks) {
+      stage = 3;  // exhausted: stays exhausted
+      return false;
+    }
+    const bool valid = msg != 0xFFFFFFFFu;
+    t.msg = msg;
+    t.addr = reinterpret_cast<uint64_t>(packed) + off;
+    t.len = len;
+    t.nb = valid ? padded_blocks(len) : 0u;
     // Codes outside {0,1,2} were excluded by the bucketing step; the chunk's
     // algorithm is that of lane 0 (every chunk starts with a real message).
-    t.alg = __shfl_sync(kFull, pf_alg, 0);
-    load_meta(pf_perm_chunk, pf_msg);
-    pf_perm_chunk = pf_chunk;
-    pf_msg = load_perm(pf_chunk);
-    pf_chunk = pf_chunk < nchunks ? pop() : pf_chunk;
+    t.alg = __shfl_sync(kFull, alg, 0);
     return true;
   }
 };
@@ -241,19 +254,43 @@ __device__ __forceinline__ void process_block(uint32_t (&st)[8], uint32_t slot, 
 // The warp loop.  MIXED selects the algorithm per item (warp-uniform);
 // otherwise ALG is fixed.
 
-template <int STAGES, int ALG, bool MIXED, class Source>
+// Consumes the KB blocks of one stage for one lane (blocks past the
+// message's padded length are skipped).
+template <int ALG, int KB>
+__device__ __forceinline__ void process_stage(uint32_t (&st)[8], uint32_t slot, uint32_t s,
+                                              uint32_t len, uint32_t b0, uint64_t msg,
+                                              uint8_t* digests, const MulConsts& mc) {
+  const uint32_t nb = padded_blocks(len);
+#pragma unroll 1
+  for (int j = 0; j < KB; ++j) {
+    if (b0 + j >= nb) break;
+    process_block<ALG>(st, slot + 64 * j, s, len, b0 + j, msg, digests, mc);
+  }
+}
+
+// COOP selects the copy mapping.  false: every lane copies the granules of
+// its own window (one instruction touches 32 messages).  true: the warp copies
+// window after window, consecutive lanes taking consecutive granules of the
+// same message, so one instruction touches two or three messages -- far fewer
+// distinct pages per instruction when the messages lie far apart.  Lanes then
+// read windows that other lanes copied, so the warp synchronises after the
+// copy wait and before a stage is reused.
+template <int STAGES, int KB, bool COOP, int ALG, bool MIXED, class Source>
 __device__ __forceinline__ void warp_pipeline(Source& src, uint8_t* wsm, const KernelArgs& a,
                                               uint32_t lane) {
-  using L = WarpSmem<STAGES>;
+  using L = WarpSmem<STAGES, KB>;
+  constexpr int kSlotBytes = Slot<KB>::kBytes;
+  constexpr int kGranules = 4 * KB + 1;
   const uint32_t slots = smem_addr(wsm);
   const uint32_t items = slots + L::kSlots;
+  const uint32_t table = items + L::kItems;
   const uint64_t safe_src = reinterpret_cast<uint64_t>(a.packed) & ~15ull;
 
   // Issuing side state (warp-uniform except the LaneTask fields).
   LaneTask t;
   bool have = src.take(t);
   uint32_t maxnb = have ? __reduce_max_sync(kFull, t.nb) : 0u;
-  uint32_t ib = 0;  // next block of the current task to issue
+  uint32_t ib = 0;  // first block of the next stage to issue
   int is = 0;       // stage the next issue goes to
 
   // Consuming side state.
@@ -269,25 +306,57 @@ __device__ __forceinline__ void warp_pipeline(Source& src, uint8_t* wsm, const K
     rec.z = t.len;
     rec.w = act ? ib : kNoBlock;
     sts128(items + (is * 32 + lane) * kItemBytes, rec);
+    // This lane's window: first granule and message bytes from there on.
+    uint64_t g0 = 0;
+    int32_t avail = 0;
     if (act) {
       const uint64_t A = t.addr + 64ull * ib;            // window start
-      const uint64_t g0 = A & ~15ull;                    // first granule
+      g0 = A & ~15ull;                                   // first granule
       const uint64_t end = t.addr + t.len;               // one past the last message byte
       const uint64_t left = end > g0 ? end - g0 : 0ull;  // message bytes from g0 on
-      const int32_t avail = left > 80ull ? 80 : (int32_t)left;
-      const uint32_t dst = slots + (is * 32 + lane) * kSlotBytes;
-      const bool five = (A & 15u) != 0u;                 // unaligned window spans 5 granules
+      avail = left > (uint64_t)kSlotBytes ? kSlotBytes : (int32_t)left;
+    }
+    if constexpr (!COOP) {
+      if (act) {
+        const uint32_t dst = slots + (is * 32 + lane) * kSlotBytes;
+        const bool extra = (t.addr & 15u) != 0u;  // unaligned window needs one more granule
 #pragma unroll
-      for (int g = 0; g < 5; ++g) {
-        const int32_t v = avail - 16 * g;
+        for (int g = 0; g < kGranules; ++g) {
+          const int32_t v = avail - 16 * g;
+          const uint32_t nbytes = v <= 0 ? 0u : (v >= 16 ? 16u : (uint32_t)v);
+          const uint64_t from = nbytes ? g0 + 16ull * g : safe_src;
+          if (g < kGranules - 1 || extra)
+            cp_async16_zfill(dst + 16 * g, reinterpret_cast<const void*>(from), nbytes);
+        }
+      }
+    } else {
+      // Publish this lane's window, then copy all 32 windows granule-major:
+      // round r, lane l copies granule (32r + l) mod G of window (32r + l) / G.
+      sts128(table + lane * 16, make_uint4((uint32_t)g0, (uint32_t)(g0 >> 32), (uint32_t)avail, 0u));
+      __syncwarp();
+      uint32_t m = lane / kGranules;
+      uint32_t g = lane % kGranules;
+#pragma unroll
+      for (int r = 0; r < kGranules; ++r) {
+        const uint4 e = lds128(table + m * 16);
+        const int32_t v = (int32_t)e.z - 16 * (int32_t)g;
         const uint32_t nbytes = v <= 0 ? 0u : (v >= 16 ? 16u : (uint32_t)v);
-        const uint64_t from = nbytes ? g0 + 16ull * g : safe_src;
-        if (g < 4 || five) cp_async16_zfill(dst + 16 * g, reinterpret_cast<const void*>(from), nbytes);
+        const uint64_t from = nbytes ? (((uint64_t)e.y << 32) | e.x) + 16ull * g : safe_src;
+        cp_async16_zfill(slots + (is * 32 + m) * kSlotBytes + 16 * g,
+                         reinterpret_cast<const void*>(from), nbytes);
+        m += 32 / kGranules;
+        g += 32 % kGranules;
+        if (g >= (uint32_t)kGranules) {
+          g -= kGranules;
+          ++m;
+        }
       }
     }
     ++inflight;
     is = (is + 1 == STAGES) ? 0 : is + 1;
-    if (++ib >= maxnb) {
+    ib += KB;
+    src.hint(ib >= maxnb ? 0u : (maxnb - ib + KB - 1) / KB);
+    if (ib >= maxnb) {
       have = src.take(t);
       maxnb = have ? __reduce_max_sync(kFull, t.nb) : 0u;
       ib = 0;
@@ -305,6 +374,7 @@ __device__ __forceinline__ void warp_pipeline(Source& src, uint8_t* wsm, const K
     if (have) issue();
     cp_async_commit();
     cp_async_wait<STAGES - 1>();  // this lane's copies of item `cs` have landed
+    if constexpr (COOP) __syncwarp();  // ... and every other lane's
     const uint4 rec = lds128(items + (cs * 32 + lane) * kItemBytes);
     if (rec.w != kNoBlock) {
       const uint64_t msg = (uint64_t)rec.x | ((uint64_t)(rec.y & 0x00FFFFFFu) << 32);
@@ -313,17 +383,18 @@ __device__ __forceinline__ void warp_pipeline(Source& src, uint8_t* wsm, const K
       if constexpr (MIXED) {
         const uint32_t alg = rec.y >> 28;
         if (alg == HB_MD5)
-          process_block<HB_MD5>(st, slot, s, rec.z, rec.w, msg, a.digests, a.mc);
+          process_stage<HB_MD5, KB>(st, slot, s, rec.z, rec.w, msg, a.digests, a.mc);
         else if (alg == HB_SHA1)
-          process_block<HB_SHA1>(st, slot, s, rec.z, rec.w, msg, a.digests, a.mc);
+          process_stage<HB_SHA1, KB>(st, slot, s, rec.z, rec.w, msg, a.digests, a.mc);
         else
-          process_block<HB_SM3>(st, slot, s, rec.z, rec.w, msg, a.digests, a.mc);
+          process_stage<HB_SM3, KB>(st, slot, s, rec.z, rec.w, msg, a.digests, a.mc);
       } else {
-        process_block<ALG>(st, slot, s, rec.z, rec.w, msg, a.digests, a.mc);
+        process_stage<ALG, KB>(st, slot, s, rec.z, rec.w, msg, a.digests, a.mc);
       }
     }
     --inflight;
     cs = (cs + 1 == STAGES) ? 0 : cs + 1;
+    if constexpr (COOP) __syncwarp();  // stage cs - 1 is free for the next copies
   }
 }
 

@@ -62,11 +62,13 @@ def test_argument_checks_before_cuda(lib):
 def test_tuning_shape_table(lib):
     n = lib.hash_tune_shapes()
     assert n >= 4
-    w, s = ctypes.c_int(), ctypes.c_int()
+    w, s, k, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    refs = [ctypes.byref(x) for x in (w, s, k, c)]
     for i in range(n):
-        assert lib.hash_tune_shape(i, ctypes.byref(w), ctypes.byref(s)) == 0
-        assert w.value in (1, 2, 4, 8, 16) and 2 <= s.value <= 4
-    assert lib.hash_tune_shape(n, ctypes.byref(w), ctypes.byref(s)) == -10
+        assert lib.hash_tune_shape(i, *refs) == 0
+        assert w.value in (1, 2, 4, 8, 16) and 2 <= s.value <= 4 and k.value in (1, 2, 4)
+        assert c.value in (0, 1)
+    assert lib.hash_tune_shape(n, *refs) == -10
     assert lib.hash_tune_set(0, n) == -10
     assert lib.hash_tune_set(7, 0) == -1
 
