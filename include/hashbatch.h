@@ -84,6 +84,10 @@ size_t hash_digest_size(int alg);
 /* Static description of a return code. */
 const char *hash_strerror(int code);
 
+/* The CUDA runtime's description of the last CUDA failure that made an entry
+ * point return HB_ERR_CUDA or HB_ERR_NOMEM on the calling thread. */
+const char *hash_last_cuda_error(void);
+
 /*
  * hash_batch -- one algorithm for the whole batch (paper Sec. IV-B, parallel
  * op; Sec. V-D, separate slots).  One message per GPU thread; each warp stages
@@ -205,7 +209,7 @@ int hash_tune_occupancy(int alg, int shape_index);
  * 3; finer buckets give chunks of more equal length), and with alg_major = 1
  * the chunk order runs through all SM3 messages, then SHA-1, then MD5, each
  * longest first, instead of interleaving the algorithms.  Digests do not
- * depend on either choice.  Defaults: sub_log2 = 2, alg_major = 0.
+ * depend on either choice.  Defaults: sub_log2 = 3, alg_major = 1.
  */
 int hash_tune_buckets(int sub_log2, int alg_major);
 

@@ -31,6 +31,7 @@ _c_int, _c_u64, _c_u32, _vp = ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32, ct
 _SIGNATURES = {
     "hash_digest_size": (ctypes.c_size_t, [_c_int]),
     "hash_strerror": (ctypes.c_char_p, [_c_int]),
+    "hash_last_cuda_error": (ctypes.c_char_p, []),
     "hash_batch": (_c_int, [_c_int, _vp, _vp, _vp, _c_u64, _vp, _vp]),
     "hash_batch_mixed": (_c_int, [_vp, _vp, _vp, _vp, _c_u64, _vp, _vp]),
     "hash_batch_mixed_noalloc": (_c_int, [_vp, _vp, _vp, _vp, _c_u64, _vp, _vp]),
@@ -60,7 +61,10 @@ _lib = None
 class HashBatchError(RuntimeError):
     def __init__(self, code: int, where: str):
         self.code = code
-        super().__init__("%s failed: %s (%d)" % (where, strerror(code), code))
+        detail = ""
+        if code in (-4, -5):
+            detail = ": " + lib().hash_last_cuda_error().decode()
+        super().__init__("%s failed: %s (%d)%s" % (where, strerror(code), code, detail))
 
 
 def header_functions(path: str = HEADER_PATH) -> list[str]:

@@ -18,7 +18,7 @@ using hb::MixedWorkspace;
 namespace {
 
 constexpr int kMaxDevices = 64;
-constexpr int kMaxShapes = 16;
+constexpr int kMaxShapes = 64;  // capacity of the per-shape occupancy cache
 constexpr uint64_t kMaxPlainN = 1ull << 40;
 constexpr uint64_t kMaxMixedN = 1ull << 31;
 
@@ -72,13 +72,18 @@ std::mutex g_mu;
 Ctx* g_ctx[kMaxDevices] = {};
 uint64_t g_wait_limit_ns = 2000000000ull;
 
-int cuda_fail(cudaError_t e) { return e == cudaErrorMemoryAllocation ? HB_ERR_NOMEM : HB_ERR_CUDA; }
+thread_local cudaError_t g_last_cuda_error = cudaSuccess;
+
+int cuda_fail(cudaError_t e) {
+  g_last_cuda_error = e;
+  return e == cudaErrorMemoryAllocation ? HB_ERR_NOMEM : HB_ERR_CUDA;
+}
 
 // The current device's context, created on first use (this first call
 // allocates and must not happen inside a stream capture).
 int get_ctx(Ctx** out) {
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return HB_ERR_CUDA;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return cuda_fail(cudaGetLastError());
   std::lock_guard<std::mutex> lock(g_mu);
   if (!g_ctx[dev]) {
     Ctx* c = new Ctx();
@@ -89,7 +94,7 @@ int get_ctx(Ctx** out) {
         cudaEventCreateWithFlags(&c->ws_event, cudaEventDisableTiming) != cudaSuccess ||
         cudaHostAlloc(&c->flag_host, sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
       delete c;
-      return HB_ERR_CUDA;
+      return cuda_fail(cudaGetLastError());
     }
     g_ctx[dev] = c;
   }
@@ -98,6 +103,7 @@ int get_ctx(Ctx** out) {
 }
 
 int occupancy(Ctx* c, bool mixed, int alg, int shape, int* occ) {
+  if (shape < 0 || shape >= kMaxShapes || shape >= hb::num_shapes()) return HB_ERR_ARG;
   int& slot = mixed ? c->occ_mixed[shape] : c->occ_plain[alg][shape];
   if (slot == 0) {
     int b = 0;
@@ -184,7 +190,7 @@ int launch_mixed(Ctx* c, int shape, int grid, const uint8_t* algs, const uint8_t
 int reserve_ws(Ctx* c, uint64_t n) {
   const size_t need = hb::mixed_workspace_bytes(n);
   if (need > c->ws.cap && c->ws_used) {
-    if (cudaEventSynchronize(c->ws_event) != cudaSuccess) return HB_ERR_CUDA;
+    if (cudaEventSynchronize(c->ws_event) != cudaSuccess) return cuda_fail(cudaGetLastError());
   }
   cudaError_t e = c->ws.reserve(need);
   return e == cudaSuccess ? HB_OK : cuda_fail(e);
@@ -261,11 +267,11 @@ int hash_batch_mixed_shape(const uint8_t* algs, const uint8_t* packed_bytes,
   if (shape_index < 0) shape_index = c->tune_mixed;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if ((rc = reserve_ws(c, n))) return rc;
-  if (c->ws_used && cudaStreamWaitEvent(s, c->ws_event, 0) != cudaSuccess) return HB_ERR_CUDA;
+  if (c->ws_used && cudaStreamWaitEvent(s, c->ws_event, 0) != cudaSuccess) return cuda_fail(cudaGetLastError());
   rc = launch_mixed(c, shape_index, grid_blocks, algs, packed_bytes, offsets, lengths, n,
                     digests_out, c->ws.p, nullptr, s);
   if (rc) return rc;
-  if (cudaEventRecord(c->ws_event, s) != cudaSuccess) return HB_ERR_CUDA;
+  if (cudaEventRecord(c->ws_event, s) != cudaSuccess) return cuda_fail(cudaGetLastError());
   c->ws_used = true;
   return HB_OK;
 }
@@ -280,7 +286,7 @@ int hash_batch_check_bounds(const uint64_t* offsets, const uint32_t* lengths, ui
                             uint64_t packed_len, int* status_dev, void* stream) {
   if (!status_dev) return HB_ERR_NULL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (cudaMemsetAsync(status_dev, 0, sizeof(int), s) != cudaSuccess) return HB_ERR_CUDA;
+  if (cudaMemsetAsync(status_dev, 0, sizeof(int), s) != cudaSuccess) return cuda_fail(cudaGetLastError());
   if (n == 0) return HB_OK;
   if (!offsets || !lengths) return HB_ERR_NULL;
   Ctx* c = nullptr;
@@ -305,7 +311,7 @@ int hash_batch_host(int alg, const uint8_t* algs_host, const uint8_t* packed_hos
   if (rc) return rc;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   // Make sure no earlier call on another stream still uses the buffers.
-  if (cudaDeviceSynchronize() != cudaSuccess) return HB_ERR_CUDA;
+  if (cudaDeviceSynchronize() != cudaSuccess) return cuda_fail(cudaGetLastError());
   const size_t pbytes = ((size_t)packed_len + 15) / 16 * 16 + 16;
   cudaError_t e;
   if ((e = c->h_packed.reserve(pbytes)) != cudaSuccess ||
@@ -322,15 +328,15 @@ int hash_batch_host(int alg, const uint8_t* algs_host, const uint8_t* packed_hos
   int* d_flag = static_cast<int*>(c->h_flag.p);
   uint8_t* d_algs = static_cast<uint8_t*>(c->h_algs.p);
   if (packed_len && cudaMemcpyAsync(d_packed, packed_host, packed_len, cudaMemcpyHostToDevice, s))
-    return HB_ERR_CUDA;
+    return cuda_fail(cudaGetLastError());
   if (cudaMemcpyAsync(d_off, offsets_host, n * sizeof(uint64_t), cudaMemcpyHostToDevice, s) ||
       cudaMemcpyAsync(d_len, lengths_host, n * sizeof(uint32_t), cudaMemcpyHostToDevice, s))
-    return HB_ERR_CUDA;
+    return cuda_fail(cudaGetLastError());
   if (algs_host && cudaMemcpyAsync(d_algs, algs_host, n, cudaMemcpyHostToDevice, s))
-    return HB_ERR_CUDA;
+    return cuda_fail(cudaGetLastError());
   // Bounds are checked on the device before any message byte is read; the
   // hashing kernels skip all work when the check failed.
-  if (cudaMemsetAsync(d_flag, 0, sizeof(int), s)) return HB_ERR_CUDA;
+  if (cudaMemsetAsync(d_flag, 0, sizeof(int), s)) return cuda_fail(cudaGetLastError());
   e = hb::launch_bounds(d_off, d_len, n, packed_len, d_flag, nullptr, grid_for_elementwise(c, n), s);
   if (e != cudaSuccess) return cuda_fail(e);
   if (algs_host) {
@@ -338,7 +344,7 @@ int hash_batch_host(int alg, const uint8_t* algs_host, const uint8_t* packed_hos
     rc = launch_mixed(c, c->tune_mixed, 0, d_algs, d_packed, d_off, d_len, n, d_dig, c->ws.p,
                       d_flag, s);
     if (rc) return rc;
-    if (cudaEventRecord(c->ws_event, s) != cudaSuccess) return HB_ERR_CUDA;
+    if (cudaEventRecord(c->ws_event, s) != cudaSuccess) return cuda_fail(cudaGetLastError());
     c->ws_used = true;
   } else {
     KernelArgs a{};
@@ -355,8 +361,8 @@ int hash_batch_host(int alg, const uint8_t* algs_host, const uint8_t* packed_hos
   }
   if (cudaMemcpyAsync(digests_host, d_dig, n * (size_t)HB_SLOT_BYTES, cudaMemcpyDeviceToHost, s) ||
       cudaMemcpyAsync(c->flag_host, d_flag, sizeof(int), cudaMemcpyDeviceToHost, s))
-    return HB_ERR_CUDA;
-  if (cudaStreamSynchronize(s) != cudaSuccess) return HB_ERR_CUDA;
+    return cuda_fail(cudaGetLastError());
+  if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_fail(cudaGetLastError());
   return *c->flag_host ? HB_ERR_BOUNDS : HB_OK;
 }
 
@@ -365,18 +371,18 @@ int hash_device_status(void* stream, int* status_out) {
   Ctx* c = nullptr;
   int rc = get_ctx(&c);
   if (rc) return rc;
-  if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return HB_ERR_CUDA;
+  if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return cuda_fail(cudaGetLastError());
   int v = 0;
   if (cudaMemcpy(&v, c->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
       cudaMemset(c->status, 0, sizeof(int)) != cudaSuccess)
-    return HB_ERR_CUDA;
+    return cuda_fail(cudaGetLastError());
   *status_out = v;
   return HB_OK;
 }
 
 int hash_release_device(void) {
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return HB_ERR_CUDA;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return cuda_fail(cudaGetLastError());
   std::lock_guard<std::mutex> lock(g_mu);
   Ctx* c = g_ctx[dev];
   if (!c) return HB_OK;
@@ -394,6 +400,10 @@ int hash_release_device(void) {
   delete c;
   g_ctx[dev] = nullptr;
   return HB_OK;
+}
+
+const char* hash_last_cuda_error(void) {
+  return g_last_cuda_error == cudaSuccess ? "no CUDA error recorded" : cudaGetErrorString(g_last_cuda_error);
 }
 
 int hash_tune_shapes(void) { return hb::num_shapes(); }
@@ -420,7 +430,7 @@ int hash_tune_set(int alg, int shape_index) {
 
 int hash_tune_get(int alg) {
   Ctx* c = nullptr;
-  if (get_ctx(&c)) return HB_ERR_CUDA;
+  if (get_ctx(&c)) return cuda_fail(cudaGetLastError());
   if (alg == HB_TUNE_MIXED) return c->tune_mixed;
   if (hash_digest_size(alg) == 0) return HB_ERR_INVALID_ALG;
   return c->tune_plain[alg];

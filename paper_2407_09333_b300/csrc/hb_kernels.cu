@@ -249,7 +249,10 @@ __global__ void hb_selftest_wait_kernel(uint64_t limit_ns, int* status) {
   X(11, 8, 2, 4, true)   \
   X(12, 16, 2, 1, true)  \
   X(13, 4, 4, 1, true)   \
-  X(14, 8, 2, 2, true)
+  X(14, 8, 2, 2, true)   \
+  X(15, 8, 3, 2, true)   \
+  X(16, 4, 3, 2, true)   \
+  X(17, 4, 4, 2, true)
 
 struct ShapeDesc {
   int warps, stages, kb;

@@ -57,7 +57,7 @@ struct BucketCfg {
   uint32_t alg_major;  // 0 or 1
 };
 
-constexpr BucketCfg kDefaultBuckets = {2u, 0u};
+constexpr BucketCfg kDefaultBuckets = {3u, 1u};
 
 // Default launch of the persistent ragged kernel: shape 10 (4 warps, 3 stages
 // of 4 blocks, cooperative copies) with 8 resident warps per SM, i.e. two per

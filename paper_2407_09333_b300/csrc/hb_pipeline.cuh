@@ -330,26 +330,34 @@ __device__ __forceinline__ void warp_pipeline(Source& src, uint8_t* wsm, const K
         }
       }
     } else {
-      // Publish this lane's window, then copy all 32 windows granule-major:
-      // round r, lane l copies granule (32r + l) mod G of window (32r + l) / G.
+      // Publish this lane's window, then copy the 32 windows message-major:
+      // each round copies the 4*KB aligned granules of 32 / (4*KB) windows,
+      // lane l taking granule l % (4*KB) of window r * 32/(4*KB) + l / (4*KB);
+      // a last round copies each lane's own trailing granule (present only
+      // when its window is not 16-byte aligned).
       sts128(table + lane * 16, make_uint4((uint32_t)g0, (uint32_t)(g0 >> 32), (uint32_t)avail, 0u));
       __syncwarp();
-      uint32_t m = lane / kGranules;
-      uint32_t g = lane % kGranules;
+      constexpr int kMain = 4 * KB;            // granules every window has
+      constexpr int kPerRound = 32 / kMain;    // windows per round
+      const uint32_t gi = lane % kMain;
+      const uint32_t mlo = lane / kMain;
+      const uint32_t tab = table + mlo * 16;
+      const uint32_t dst0 = slots + (is * 32 + mlo) * kSlotBytes + 16 * gi;
 #pragma unroll
-      for (int r = 0; r < kGranules; ++r) {
-        const uint4 e = lds128(table + m * 16);
-        const int32_t v = (int32_t)e.z - 16 * (int32_t)g;
+      for (int r = 0; r < kMain; ++r) {
+        const uint4 e = lds128(tab + 16 * kPerRound * r);
+        const int32_t v = (int32_t)e.z - 16 * (int32_t)gi;
         const uint32_t nbytes = v <= 0 ? 0u : (v >= 16 ? 16u : (uint32_t)v);
-        const uint64_t from = nbytes ? (((uint64_t)e.y << 32) | e.x) + 16ull * g : safe_src;
-        cp_async16_zfill(slots + (is * 32 + m) * kSlotBytes + 16 * g,
+        const uint64_t from = nbytes ? (((uint64_t)e.y << 32) | e.x) + 16ull * gi : safe_src;
+        cp_async16_zfill(dst0 + kPerRound * kSlotBytes * r, reinterpret_cast<const void*>(from),
+                         nbytes);
+      }
+      if (act && (t.addr & 15u) != 0u) {
+        const int32_t v = avail - 16 * kMain;
+        const uint32_t nbytes = v <= 0 ? 0u : (v >= 16 ? 16u : (uint32_t)v);
+        const uint64_t from = nbytes ? g0 + 16ull * kMain : safe_src;
+        cp_async16_zfill(slots + (is * 32 + lane) * kSlotBytes + 16 * kMain,
                          reinterpret_cast<const void*>(from), nbytes);
-        m += 32 / kGranules;
-        g += 32 % kGranules;
-        if (g >= (uint32_t)kGranules) {
-          g -= kGranules;
-          ++m;
-        }
       }
     }
     ++inflight;
