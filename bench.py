@@ -227,6 +227,16 @@ def make_workload(name: str, rank: int, messages: int = 0):
         return ("ragged mixed-algorithm batch: %d messages, log-uniform lengths in [0, 64 KiB], "
                 "1%% at padding boundaries, algorithm per message" % messages,
                 workloads.ragged(messages, shard_seed(2, rank)), True)
+    if name == "c5":
+        # the serving mix as one ragged batch (used by the CPU reference arm)
+        reqs = workloads.serve_requests(messages or 64, 1.0, shard_seed(4, rank))
+        lengths = np.concatenate([r.lengths for r in reqs])
+        algs = np.concatenate([np.full(r.lengths.shape[0], r.alg, np.uint8) for r in reqs])
+        offsets = np.zeros(lengths.shape[0], dtype=np.uint64)
+        offsets[1:] = np.cumsum(lengths.astype(np.uint64))[:-1]
+        packed = workloads.fixed(1, int(lengths.astype(np.int64).sum()), shard_seed(4, rank)).packed
+        return ("serving mix as one batch: %d requests, 1-4096 messages each, lengths log-uniform "
+                "in [16 B, 1 MiB]" % len(reqs), workloads.Batch(packed, offsets, lengths, algs), True)
     if name == "c1":
         return ("plain fixed-length batch: 4096 messages x 64 B, MD5+SHA-1+SM3 per step",
                 workloads.fixed(4096, 64, shard_seed(0, rank)), False)
@@ -517,6 +527,104 @@ def e2e_measure(args, batch, mixed, api, torch):
             "api": "hash_batch_host (pinned host buffers)"}
 
 
+def plain_equal_bytes_ms(api, torch, lengths, algs, reps=3):
+    """Time of the plain (fixed-length) kernels at equal bytes: per algorithm
+    one batch of messages of the set's mean length holding that algorithm's
+    share of the bytes."""
+    L = max(1, int(round(float(lengths.astype(np.float64).mean()))))
+    tot = 0.0
+    for a in (0, 1, 2):
+        nbytes = int(lengths[algs == a].astype(np.int64).sum())
+        n = max(1, nbytes // L)
+        b = workloads.fixed(n, L, 900 + a)
+        p, o, l, _ = api.to_device(b)
+        out = torch.empty((n, 32), dtype=torch.uint8, device="cuda")
+        best = float("inf")
+        for sh in range(len(api.shapes())):
+            fn = lambda: api.hash_batch(a, p, o, l, out=out, shape=sh)
+            fn()
+            torch.cuda.synchronize()
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(); fn(); e1.record(); e1.synchronize()
+                best = min(best, e0.elapsed_time(e1))
+        tot += best
+        del p, o, l, out
+    return tot, L
+
+
+def run_serve(args, dist):
+    """Serving sweep: Poisson request streams at fractions of the ragged
+    path's measured throughput, served under a device-memory budget."""
+    # one hardware queue per serving slot, so a long batch does not hold up
+    # the batches behind it (must be set before CUDA starts)
+    os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+    import torch
+    from paper_2407_09333_b300 import api, build, serve
+
+    if torch.cuda.is_available():
+        torch.cuda.set_device(dist.local_rank)
+    build.build()
+    # reference throughput: the ragged path on the 2^20-message ragged batch
+    rb = workloads.ragged(1 << 20, shard_seed(2, dist.rank))
+    rp, ro, rl, ra = api.to_device(rb)
+    rout = torch.empty((rb.n, 32), dtype=torch.uint8, device="cuda")
+    for _ in range(3):
+        api.hash_batch_mixed(ra, rp, ro, rl, out=rout)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(5):
+        api.hash_batch_mixed(ra, rp, ro, rl, out=rout)
+    e1.record(); e1.synchronize()
+    ref_gbs = 5 * rb.total_bytes / (e0.elapsed_time(e1) * 1e-3) / 1e9
+    del rp, ro, rl, ra, rout, rb
+    torch.cuda.empty_cache()
+
+    pool_bytes = args.pool_mib << 20
+    pool_host = workloads.fixed(1, pool_bytes, shard_seed(4, dist.rank)).packed
+    pool = torch.from_numpy(np.ascontiguousarray(pool_host)).cuda()
+    srv = serve.Server(pool, budget=args.budget_gib << 30, slots=args.slots,
+                       shape=args.serve_shape, warps_per_sm=args.serve_warps)
+    probe = serve.make_requests(args.requests, 1.0, shard_seed(4, dist.rank), pool_bytes)
+    mean_req = float(np.mean([r.nbytes for r in probe]))
+    all_lengths = np.concatenate([r.lengths for r in probe])
+    all_algs = np.concatenate([np.full(r.lengths.shape[0], r.alg, np.uint8) for r in probe])
+    points = []
+    with ClockSampler(torch.cuda.current_device()) as clocks:
+        for k, load in enumerate(args.loads):
+            rate = load * ref_gbs * 1e9 / mean_req
+            reqs = serve.make_requests(args.requests, rate, shard_seed(4, dist.rank) + 17 * k, pool_bytes)
+            srv.run(reqs)
+            st = serve.latency_stats(reqs)
+            st.update({"offered_load": load, "offered_gbs": rate * mean_req / 1e9,
+                       "requests": len(reqs)})
+            points.append(st)
+    srv.close()
+    plain_ms, plain_L = plain_equal_bytes_ms(api, torch, all_lengths, all_algs)
+    plain_gbs = float(all_lengths.astype(np.int64).sum()) / (plain_ms * 1e-3) / 1e9
+    top = max(points, key=lambda p: p["offered_load"])
+    line = {
+        "metric": METRIC, "value": top["gbs"], "unit": "GB/s", "n_gpus": dist.world,
+        "steps": len(points), "warmup": 3, "ms_per_step": None, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic: Poisson arrivals; per request 1-4096 messages (log-uniform count), "
+                "lengths log-uniform in [16 B, 1 MiB], random algorithm; bytes from a %d MiB "
+                "random pool (numpy PCG64)" % args.pool_mib,
+        "config": {"workload": "serving: continuous batching under a %d GiB device budget, "
+                               "%d slots, %d requests per load point" % (args.budget_gib, args.slots, args.requests),
+                   "reference_ragged_gbs": ref_gbs, "mean_request_bytes": mean_req,
+                   "parallelism": "dp%d: independent servers, no collective" % dist.world},
+        "serve": points,
+        "served_vs_plain_equal_bytes": top["gbs"] / plain_gbs,
+        "plain_equal_bytes_gbs": plain_gbs, "plain_mean_length": plain_L,
+        "p50_ms_at_top_load": top["p50_ms"], "p99_ms_at_top_load": top["p99_ms"],
+        "clocks": clocks.summary(),
+    }
+    if dist.rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_int_peak(args, dist):
     """K5: sustained 32-bit operations per clock per SM for each op class."""
     import torch
@@ -551,7 +659,15 @@ def main(argv=None):
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=2000)
     p.add_argument("--warmup", type=int, default=5)
-    p.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4"])
+    p.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5"])
+    p.add_argument("--requests", type=int, default=2000, help="requests per load point (c5)")
+    p.add_argument("--loads", type=float, nargs="+", default=[0.1, 0.3, 0.5, 0.7, 0.9, 1.1],
+                   help="offered loads as fractions of the ragged path's throughput (c5)")
+    p.add_argument("--budget-gib", type=int, default=8, help="device-memory budget (c5)")
+    p.add_argument("--slots", type=int, default=16, help="batches in flight (c5)")
+    p.add_argument("--serve-shape", type=int, default=18, help="launch shape of the serving plans (c5)")
+    p.add_argument("--serve-warps", type=int, default=4, help="warps per SM per batch (c5)")
+    p.add_argument("--pool-mib", type=int, default=2048, help="random-byte pool for requests (c5)")
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--e2e-steps", type=int, default=10)
     p.add_argument("--shape", type=int, default=None,
@@ -571,6 +687,8 @@ def main(argv=None):
     try:
         if args.int_peak:
             run_int_peak(args, dist)
+        elif args.workload == "c5" and args.impl == "ours":
+            run_serve(args, dist)
         elif args.impl == "reference":
             run_reference(args, dist)
         else:

@@ -142,6 +142,71 @@ int hash_batch_mixed_noalloc(const uint8_t *algs, const uint8_t *packed_bytes,
                              uint8_t *digests_out, void *stream);
 
 /*
+ * Plans: the ragged path (as hash_batch_mixed) with scratch owned by the
+ * plan, so that batches on different streams run concurrently, and its
+ * launch sequence (bucketing + persistent kernel) captured once as a CUDA
+ * graph and replayed for batches of any size up to max_n.
+ *
+ * hash_plan_create  -- allocates the plan's scratch for up to max_n < 2^31
+ *                      messages (cudaMalloc) and takes the current device's
+ *                      tuning (shape, warps per SM, bucketing).
+ * hash_plan_run     -- one ragged batch of n <= max_n messages on `stream`
+ *                      with the plan's scratch; grid_blocks 0 = tuned size.
+ * hash_plan_capture -- records the ragged launch sequence for these buffer
+ *                      pointers as a graph (replaces an earlier capture).
+ *                      The buffers must stay valid while the graph is used.
+ * hash_plan_replay  -- sets the message count n <= max_n (a one-thread
+ *                      kernel on `stream`) and launches the graph on
+ *                      `stream`; the messages are the first n entries of the
+ *                      captured algs/offsets/lengths arrays.
+ * hash_plan_configure -- overrides the plan's launch shape (-1 keeps it) and
+ *                      resident warps per SM (-1 keeps it, 0 = as many as
+ *                      fit) before the first capture; HB_ERR_ARG after.
+ * hash_plan_set_completion -- per-request completion for serving: message i
+ *                      of a batch belongs to request msg_req_dev[i] (device
+ *                      uint32); remaining_dev[r] (device uint32) must hold
+ *                      request r's message count when the batch starts; the
+ *                      lane that finishes request r's last message stores 1
+ *                      to done_flags[r] (host memory the device can write:
+ *                      pinned memory on a unified-addressing system) after
+ *                      the request's digests are stored.  All three or none
+ *                      (NULL = off); before the first capture.  done_flags
+ *                      must be page-locked host memory mapped for the device
+ *                      (cudaHostAlloc); other memory returns HB_ERR_ARG.
+ * hash_plan_destroy -- synchronises the device and frees the plan.
+ * A plan's scratch is used by one batch at a time: order the runs and
+ * replays of one plan (same stream, or events); different plans overlap.
+ */
+typedef struct hb_plan hb_plan;
+
+/*
+ * hash_gather -- packs byte ranges on the device: record i copies
+ * copies[i].bytes bytes from device address copies[i].src to copies[i].dst
+ * (one thread block per record; 16-byte vector copies when both addresses
+ * are 16-byte aligned).  copies_dev is a device array of `count` records.
+ * The serving loop uses it to move admitted requests into its arena with
+ * one launch per batch.  Ranges must not overlap.
+ */
+typedef struct hb_copy {
+  uint64_t src;
+  uint64_t dst;
+  uint64_t bytes;
+} hb_copy;
+int hash_gather(const hb_copy *copies_dev, uint32_t count, void *stream);
+int hash_plan_create(uint64_t max_n, hb_plan **plan_out);
+int hash_plan_run(hb_plan *plan, const uint8_t *algs, const uint8_t *packed_bytes,
+                  const uint64_t *offsets, const uint32_t *lengths, uint64_t n,
+                  uint8_t *digests_out, int grid_blocks, void *stream);
+int hash_plan_capture(hb_plan *plan, const uint8_t *algs, const uint8_t *packed_bytes,
+                      const uint64_t *offsets, const uint32_t *lengths, uint8_t *digests_out,
+                      int grid_blocks);
+int hash_plan_replay(hb_plan *plan, uint64_t n, void *stream);
+int hash_plan_configure(hb_plan *plan, int shape_index, int warps_per_sm);
+int hash_plan_set_completion(hb_plan *plan, const uint32_t *msg_req_dev, uint32_t *remaining_dev,
+                             uint32_t *done_flags);
+int hash_plan_destroy(hb_plan *plan);
+
+/*
  * hash_batch_check_bounds -- checks on the device that every message lies in
  * [0, packed_len): offsets[i] + lengths[i] <= packed_len, computed without
  * overflow.  Writes 0 to *status_dev when all messages are in bounds, else

@@ -53,6 +53,14 @@ _SIGNATURES = {
     "hash_int_peak_ops_per_iter": (_c_int, []),
     "hash_selftest_wait_timeout": (_c_int, [_c_u64, _vp]),
     "hash_set_wait_limit_ns": (_c_u64, [_c_u64]),
+    "hash_plan_create": (_c_int, [_c_u64, ctypes.POINTER(_vp)]),
+    "hash_plan_run": (_c_int, [_vp, _vp, _vp, _vp, _vp, _c_u64, _vp, _c_int, _vp]),
+    "hash_plan_capture": (_c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _c_int]),
+    "hash_plan_replay": (_c_int, [_vp, _c_u64, _vp]),
+    "hash_plan_destroy": (_c_int, [_vp]),
+    "hash_plan_configure": (_c_int, [_vp, _c_int, _c_int]),
+    "hash_plan_set_completion": (_c_int, [_vp, _vp, _vp, _vp]),
+    "hash_gather": (_c_int, [_vp, _c_u32, _vp]),
 }
 
 _lib = None
@@ -246,6 +254,76 @@ def set_wait_limit_ns(limit_ns: int) -> int:
 def selftest_wait_timeout(timeout_ns: int, stream=None):
     _check(lib().hash_selftest_wait_timeout(int(timeout_ns), _stream_handle(stream)),
            "hash_selftest_wait_timeout")
+
+
+# ---------------------------------------------------------------------------
+# plans (ragged path with private scratch; captured graphs)
+
+class Plan:
+    """A ragged-path plan for batches of up to `max_n` messages.
+
+    run(...) hashes one batch on a stream with the plan's own scratch;
+    capture(...) records the launch sequence as a CUDA graph for fixed
+    buffers and replay(n) runs it for the first n messages of them.
+    """
+
+    def __init__(self, max_n: int, shape: int = -1, warps_per_sm: int = -1):
+        h = ctypes.c_void_p()
+        _check(lib().hash_plan_create(int(max_n), ctypes.byref(h)), "hash_plan_create")
+        self._h = h
+        self.max_n = int(max_n)
+        self._keep = None
+        if shape >= 0 or warps_per_sm >= 0:
+            _check(lib().hash_plan_configure(h, int(shape), int(warps_per_sm)), "hash_plan_configure")
+
+    def run(self, algs, packed, offsets, lengths, out, n=None, grid=0, stream=None):
+        n = int(offsets.numel()) if n is None else int(n)
+        _check(lib().hash_plan_run(self._h, _dev_ptr(algs, 1, "algs"), _dev_ptr(packed, 1, "packed"),
+                                   _dev_ptr(offsets, 8, "offsets"), _dev_ptr(lengths, 4, "lengths"),
+                                   n, _dev_ptr(out, 1, "out"), int(grid), _stream_handle(stream)),
+               "hash_plan_run")
+        return out
+
+    def set_completion(self, msg_req, remaining, done_flags):
+        """Per-request completion flags (see hash_plan_set_completion):
+        msg_req and remaining are CUDA uint32/int32 tensors, done_flags a
+        pinned CPU int32 tensor."""
+        if done_flags.is_cuda or not done_flags.is_pinned():
+            raise ValueError("done_flags must be pinned host memory")
+        _check(lib().hash_plan_set_completion(self._h, _dev_ptr(msg_req, 4, "msg_req"),
+                                              _dev_ptr(remaining, 4, "remaining"),
+                                              ctypes.c_void_p(done_flags.data_ptr())),
+               "hash_plan_set_completion")
+        self._flags = (msg_req, remaining, done_flags)
+
+    def capture(self, algs, packed, offsets, lengths, out, grid=0):
+        _check(lib().hash_plan_capture(self._h, _dev_ptr(algs, 1, "algs"),
+                                       _dev_ptr(packed, 1, "packed"), _dev_ptr(offsets, 8, "offsets"),
+                                       _dev_ptr(lengths, 4, "lengths"), _dev_ptr(out, 1, "out"),
+                                       int(grid)), "hash_plan_capture")
+        self._keep = (algs, packed, offsets, lengths, out)   # buffers must outlive the graph
+
+    def replay(self, n: int, stream=None):
+        _check(lib().hash_plan_replay(self._h, int(n), _stream_handle(stream)), "hash_plan_replay")
+
+    def close(self):
+        if self._h:
+            lib().hash_plan_destroy(self._h)
+            self._h = None
+            self._keep = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def gather(copies_dev, count: int, stream=None):
+    """Device byte-range copies; copies_dev is a CUDA int64 tensor of shape
+    (>= count, 3) holding (src address, dst address, bytes) per row."""
+    _check(lib().hash_gather(_dev_ptr(copies_dev, 8, "copies"), int(count), _stream_handle(stream)),
+           "hash_gather")
 
 
 # ---------------------------------------------------------------------------

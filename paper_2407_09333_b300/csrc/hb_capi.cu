@@ -143,15 +143,24 @@ int grid_for_elementwise(Ctx* c, uint64_t n) {
 }
 
 // Ragged path on a given workspace (bucketing + persistent kernel).
+struct Completion {
+  const uint32_t* msg_req = nullptr;
+  uint32_t* remaining = nullptr;
+  volatile uint32_t* done = nullptr;
+};
+
 int launch_mixed(Ctx* c, int shape, int grid, const uint8_t* algs, const uint8_t* packed,
                  const uint64_t* offsets, const uint32_t* lengths, uint64_t n, uint8_t* digests,
-                 void* ws, const int* abort_flag, cudaStream_t s) {
+                 void* ws, const int* abort_flag, cudaStream_t s, const uint64_t* n_dev = nullptr,
+                 const hb::BucketCfg* buckets = nullptr, int warps_per_sm = -1,
+                 const Completion* comp = nullptr) {
   if (shape < 0 || shape >= hb::num_shapes()) return HB_ERR_ARG;
   MixedArgs m;
-  m.cfg = c->buckets;
+  m.cfg = buckets ? *buckets : c->buckets;
   m.algs = algs;
   m.lengths = lengths;
   m.n = n;
+  m.n_dev = n_dev;
   m.digests = digests;
   m.ws = static_cast<MixedWorkspace*>(ws);
   m.perm = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + sizeof(MixedWorkspace));
@@ -174,12 +183,18 @@ int launch_mixed(Ctx* c, int shape, int grid, const uint8_t* algs, const uint8_t
   a.abort_flag = abort_flag;
   a.wait_limit_ns = g_wait_limit_ns;
   a.mc = hb::make_mul_consts();
+  if (comp) {
+    a.msg_req = comp->msg_req;
+    a.req_remaining = comp->remaining;
+    a.req_done = comp->done;
+  }
+  if (warps_per_sm < 0) warps_per_sm = c->mixed_warps_per_sm;
   if (grid <= 0) {
     int per_sm = occ;
-    if (c->mixed_warps_per_sm > 0) {
+    if (warps_per_sm > 0) {
       int warps = 0, stages = 0;
       hb::shape_desc(shape, &warps, &stages);
-      per_sm = std::min(occ, std::max(1, c->mixed_warps_per_sm / warps));
+      per_sm = std::min(occ, std::max(1, warps_per_sm / warps));
     }
     grid = c->sms * per_sm;
   }
@@ -492,6 +507,182 @@ uint64_t hash_set_wait_limit_ns(uint64_t limit_ns) {
   const uint64_t old = g_wait_limit_ns;
   if (limit_ns) g_wait_limit_ns = limit_ns;
   return old;
+}
+
+int hash_gather(const hb_copy* copies_dev, uint32_t count, void* stream) {
+  if (count == 0) return HB_OK;
+  if (!copies_dev) return HB_ERR_NULL;
+  Ctx* c = nullptr;
+  int rc = get_ctx(&c);
+  if (rc) return rc;
+  const int grid = (int)std::min<uint32_t>(count, (uint32_t)c->sms * 4);
+  cudaError_t e = hb::launch_gather(copies_dev, count, grid, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? HB_OK : cuda_fail(e);
+}
+
+// ---------------------------------------------------------------------------
+// Plans: the ragged path with private scratch, and its captured graph.
+
+struct hb_plan {
+  int device = -1;
+  uint64_t max_n = 0;
+  void* ws = nullptr;          // bucketing scratch for up to max_n messages
+  uint64_t* n_dev = nullptr;   // message count read by the captured graph
+  int shape = 0;
+  int warps_per_sm = 0;
+  hb::BucketCfg buckets = hb::kDefaultBuckets;
+  Completion completion;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+int hash_plan_configure(hb_plan* p, int shape_index, int warps_per_sm) {
+  if (!p) return HB_ERR_NULL;
+  if (shape_index >= hb::num_shapes() || warps_per_sm > 64) return HB_ERR_ARG;
+  if (p->exec) return HB_ERR_ARG;  // configure before capturing
+  if (shape_index >= 0) p->shape = shape_index;
+  if (warps_per_sm >= 0) p->warps_per_sm = warps_per_sm;
+  return HB_OK;
+}
+
+int hash_plan_set_completion(hb_plan* p, const uint32_t* msg_req_dev, uint32_t* remaining_dev,
+                             uint32_t* done_flags) {
+  if (!p) return HB_ERR_NULL;
+  if (p->exec) return HB_ERR_ARG;  // before capturing
+  const bool any = msg_req_dev || remaining_dev || done_flags;
+  const bool all = msg_req_dev && remaining_dev && done_flags;
+  if (any && !all) return HB_ERR_NULL;
+  uint32_t* done_dev = nullptr;
+  if (done_flags) {
+    // The flags are host memory written by the kernel: take the device-side
+    // address the runtime maps for it, and refuse memory that is not mapped.
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, done_flags) != cudaSuccess ||
+        attr.type != cudaMemoryTypeHost) {
+      cudaGetLastError();
+      return HB_ERR_ARG;
+    }
+    void* d = nullptr;
+    if (cudaHostGetDevicePointer(&d, done_flags, 0) != cudaSuccess || d == nullptr) {
+      cudaGetLastError();
+      return HB_ERR_ARG;
+    }
+    done_dev = static_cast<uint32_t*>(d);
+  }
+  p->completion.msg_req = msg_req_dev;
+  p->completion.remaining = remaining_dev;
+  p->completion.done = done_dev;
+  return HB_OK;
+}
+
+int hash_plan_create(uint64_t max_n, hb_plan** plan_out) {
+  if (!plan_out) return HB_ERR_NULL;
+  *plan_out = nullptr;
+  if (max_n == 0) return HB_ERR_ARG;
+  if (max_n >= kMaxMixedN) return HB_ERR_TOO_LARGE;
+  Ctx* c = nullptr;
+  int rc = get_ctx(&c);
+  if (rc) return rc;
+  hb_plan* p = new hb_plan();
+  p->device = c->device;
+  p->max_n = max_n;
+  p->shape = c->tune_mixed;
+  p->warps_per_sm = c->mixed_warps_per_sm;
+  p->buckets = c->buckets;
+  cudaError_t e = cudaMalloc(&p->ws, hb::mixed_workspace_bytes(max_n));
+  if (e == cudaSuccess) e = cudaMalloc(&p->n_dev, sizeof(uint64_t));
+  if (e != cudaSuccess) {
+    hash_plan_destroy(p);
+    return cuda_fail(e);
+  }
+  *plan_out = p;
+  return HB_OK;
+}
+
+int hash_plan_destroy(hb_plan* p) {
+  if (!p) return HB_OK;
+  if (p->ws || p->n_dev || p->exec) cudaDeviceSynchronize();
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  if (p->ws) cudaFree(p->ws);
+  if (p->n_dev) cudaFree(p->n_dev);
+  delete p;
+  return HB_OK;
+}
+
+int hash_plan_run(hb_plan* p, const uint8_t* algs, const uint8_t* packed_bytes,
+                  const uint64_t* offsets, const uint32_t* lengths, uint64_t n,
+                  uint8_t* digests_out, int grid_blocks, void* stream) {
+  if (!p) return HB_ERR_NULL;
+  if (n == 0) return HB_OK;
+  if (n > p->max_n) return HB_ERR_TOO_LARGE;
+  int rc = check_common(packed_bytes, offsets, lengths, n, digests_out);
+  if (rc) return rc;
+  if (!algs) return HB_ERR_NULL;
+  Ctx* c = nullptr;
+  if ((rc = get_ctx(&c))) return rc;
+  if (c->device != p->device) return HB_ERR_ARG;
+  return launch_mixed(c, p->shape, grid_blocks, algs, packed_bytes, offsets, lengths, n,
+                      digests_out, p->ws, nullptr, static_cast<cudaStream_t>(stream), nullptr,
+                      &p->buckets, p->warps_per_sm, &p->completion);
+}
+
+int hash_plan_capture(hb_plan* p, const uint8_t* algs, const uint8_t* packed_bytes,
+                      const uint64_t* offsets, const uint32_t* lengths, uint8_t* digests_out,
+                      int grid_blocks) {
+  if (!p) return HB_ERR_NULL;
+  int rc = check_common(packed_bytes, offsets, lengths, 1, digests_out);
+  if (rc) return rc;
+  if (!algs) return HB_ERR_NULL;
+  Ctx* c = nullptr;
+  if ((rc = get_ctx(&c))) return rc;
+  if (c->device != p->device) return HB_ERR_ARG;
+  int occ = 0;
+  if ((rc = occupancy(c, true, 0, p->shape, &occ))) return rc;  // set-up before capture
+  if (p->exec) {
+    cudaGraphExecDestroy(p->exec);
+    p->exec = nullptr;
+  }
+  if (p->graph) {
+    cudaGraphDestroy(p->graph);
+    p->graph = nullptr;
+  }
+  cudaStream_t s = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_fail(e);
+  e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    // Grids of the grid-stride bucketing kernels are sized for max_n; the
+    // kernels read the actual count from n_dev when the graph runs.
+    rc = launch_mixed(c, p->shape, grid_blocks, algs, packed_bytes, offsets, lengths, p->max_n,
+                      digests_out, p->ws, nullptr, s, p->n_dev, &p->buckets, p->warps_per_sm,
+                      &p->completion);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(s, &g);
+    if (rc == HB_OK && e2 != cudaSuccess) rc = cuda_fail(e2);
+    if (rc == HB_OK) {
+      e = cudaGraphInstantiate(&p->exec, g, 0);
+      if (e != cudaSuccess) rc = cuda_fail(e);
+    }
+    if (rc == HB_OK)
+      p->graph = g;
+    else if (g)
+      cudaGraphDestroy(g);
+  } else {
+    rc = cuda_fail(e);
+  }
+  cudaStreamDestroy(s);
+  return rc;
+}
+
+int hash_plan_replay(hb_plan* p, uint64_t n, void* stream) {
+  if (!p) return HB_ERR_NULL;
+  if (!p->exec) return HB_ERR_ARG;
+  if (n > p->max_n) return HB_ERR_TOO_LARGE;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = hb::launch_set_count(p->n_dev, n, s);
+  if (e == cudaSuccess) e = cudaGraphLaunch(p->exec, s);
+  return e == cudaSuccess ? HB_OK : cuda_fail(e);
 }
 
 }  // extern "C"

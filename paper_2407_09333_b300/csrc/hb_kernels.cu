@@ -57,12 +57,17 @@ __device__ __forceinline__ uint32_t cost_group(uint32_t len, uint32_t alg, Bucke
   return desc * 3u + alg;
 }
 
+__device__ __forceinline__ uint64_t batch_size(const MixedArgs& m) {
+  return m.n_dev ? *m.n_dev : m.n;
+}
+
 __global__ void hb_hist_kernel(MixedArgs m) {
   __shared__ uint32_t counts[kGroups];
   for (uint32_t g = threadIdx.x; g < kGroups; g += blockDim.x) counts[g] = 0;
   __syncthreads();
+  const uint64_t n = batch_size(m);
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m.n; i += stride) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     const uint32_t alg = m.algs[i];
     if (alg <= HB_SM3) {
       atomicAdd(&counts[cost_group(m.lengths[i], alg, m.cfg)], 1u);
@@ -106,11 +111,12 @@ __global__ void hb_scan_kernel(MixedArgs m) {
 
 __global__ void hb_scatter_kernel(MixedArgs m) {
   const uint32_t lane = threadIdx.x & 31u;
+  const uint64_t n = batch_size(m);
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  const uint64_t n_up = (m.n + 31u) & ~31ull;
+  const uint64_t n_up = (n + 31u) & ~31ull;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_up; i += stride) {
     uint32_t key = 0xFFFFFFFFu;
-    if (i < m.n) {
+    if (i < n) {
       const uint32_t alg = m.algs[i];
       if (alg <= HB_SM3) key = cost_group(m.lengths[i], alg, m.cfg);
     }
@@ -252,7 +258,10 @@ __global__ void hb_selftest_wait_kernel(uint64_t limit_ns, int* status) {
   X(14, 8, 2, 2, true)   \
   X(15, 8, 3, 2, true)   \
   X(16, 4, 3, 2, true)   \
-  X(17, 4, 4, 2, true)
+  X(17, 4, 4, 2, true)   \
+  X(18, 1, 3, 4, true)   \
+  X(19, 1, 2, 4, true)   \
+  X(20, 1, 4, 2, true)
 
 struct ShapeDesc {
   int warps, stages, kb;
@@ -369,6 +378,39 @@ cudaError_t launch_int_peak(int op, int blocks, int threads, int iters, unsigned
                              int_peak_launch<12>};
   if (op < 0 || op >= (int)(sizeof(table) / sizeof(table[0]))) return cudaErrorInvalidValue;
   table[op](blocks, threads, iters, cycles, sink, stream);
+  return cudaGetLastError();
+}
+
+__global__ void hb_set_count_kernel(uint64_t* n_dev, uint64_t n) { *n_dev = n; }
+
+// Byte copies described by {src, dst, bytes} records, one block per record
+// (grid-stride over records): 16-byte vector copies when both ends are
+// 16-byte aligned, byte copies otherwise and for the tail.
+__global__ void hb_gather_kernel(const HbCopy* copies, uint32_t count) {
+  for (uint32_t r = blockIdx.x; r < count; r += gridDim.x) {
+    const HbCopy c = copies[r];
+    const uint8_t* src = reinterpret_cast<const uint8_t*>(c.src);
+    uint8_t* dst = reinterpret_cast<uint8_t*>(c.dst);
+    uint64_t done = 0;
+    if (((c.src | c.dst) & 15u) == 0) {
+      const uint64_t nv = c.bytes / 16;
+      const uint4* s4 = reinterpret_cast<const uint4*>(src);
+      uint4* d4 = reinterpret_cast<uint4*>(dst);
+      for (uint64_t k = threadIdx.x; k < nv; k += blockDim.x) d4[k] = __ldg(s4 + k);
+      done = nv * 16;
+    }
+    for (uint64_t k = done + threadIdx.x; k < c.bytes; k += blockDim.x) dst[k] = src[k];
+  }
+}
+
+cudaError_t launch_gather(const HbCopy* copies, uint32_t count, int grid, cudaStream_t stream) {
+  if (count == 0) return cudaSuccess;
+  hb_gather_kernel<<<grid, 256, 0, stream>>>(copies, count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_count(uint64_t* n_dev, uint64_t n, cudaStream_t stream) {
+  hb_set_count_kernel<<<1, 1, 0, stream>>>(n_dev, n);
   return cudaGetLastError();
 }
 

@@ -40,6 +40,12 @@ struct KernelArgs {
   const int* abort_flag;      // optional: skip all work when *abort_flag != 0
   uint64_t wait_limit_ns;
   MulConsts mc;
+  // Optional per-request completion (serving): message i belongs to request
+  // msg_req[i]; the lane that finishes a request's last message sets
+  // req_done[request] = 1 (host-visible memory) after its digests are stored.
+  const uint32_t* msg_req;
+  uint32_t* req_remaining;
+  volatile uint32_t* req_done;
 };
 
 // Ragged-path bucketing: groups are (cost bucket, algorithm) pairs ordered
@@ -88,6 +94,7 @@ struct MixedArgs {
   const uint8_t* algs;
   const uint32_t* lengths;
   uint64_t n;
+  const uint64_t* n_dev;  // when set, the message count is read from here (captured graphs)
   uint8_t* digests;
   MixedWorkspace* ws;
   uint32_t* perm;
@@ -108,5 +115,10 @@ cudaError_t launch_bounds(const uint64_t* offsets, const uint32_t* lengths, uint
 cudaError_t launch_int_peak(int op, int blocks, int threads, int iters, unsigned long long* cycles,
                             uint32_t* sink, cudaStream_t stream);
 cudaError_t launch_selftest_wait(uint64_t limit_ns, int* status, cudaStream_t stream);
+// Request-packing copies of the serving path (hash_gather).
+using HbCopy = hb_copy;
+cudaError_t launch_gather(const HbCopy* copies, uint32_t count, int grid, cudaStream_t stream);
+// Writes the message count a captured ragged graph reads (one tiny kernel).
+cudaError_t launch_set_count(uint64_t* n_dev, uint64_t n, cudaStream_t stream);
 
 }  // namespace hb

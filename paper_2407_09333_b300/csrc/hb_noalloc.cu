@@ -101,6 +101,7 @@ extern "C" int hash_batch_mixed_noalloc(const uint8_t* algs, const uint8_t* pack
   m.algs = algs;
   m.lengths = lengths;
   m.n = n;
+  m.n_dev = nullptr;
   m.digests = digests_out;
   m.ws = ws;
   m.perm = perm;

@@ -224,10 +224,23 @@ __device__ __forceinline__ void read_block_words(uint32_t slot, uint32_t s, uint
   for (int i = 0; i < 16; ++i) w[i] = prmt(x[i], x[i + 1], sel);
 }
 
+// Per-request completion for the serving path: counts down the request's
+// messages and raises its host-visible flag after the last one.
+__device__ __forceinline__ void note_message_done(const KernelArgs& a, uint64_t msg) {
+  if (a.msg_req == nullptr) return;
+  __threadfence();  // this message's digest is visible before the count drops
+  const uint32_t r = a.msg_req[msg];
+  if (atomicSub(&a.req_remaining[r], 1u) == 1u) {
+    __threadfence_system();
+    a.req_done[r] = 1u;
+  }
+}
+
 template <int ALG>
 __device__ __forceinline__ void process_block(uint32_t (&st)[8], uint32_t slot, uint32_t s,
                                               uint32_t len, uint32_t b, uint64_t msg,
-                                              uint8_t* digests, const MulConsts& mc) {
+                                              uint8_t* digests, const MulConsts& mc,
+                                              const KernelArgs& a) {
   constexpr bool BE = AlgTraits<ALG>::kBigEndian;
   const int64_t rem = (int64_t)len - 64 * (int64_t)b;  // message bytes from this block on
   if (rem >= 0 && rem < 64) sts8(slot + s + (uint32_t)rem, 0x80u);
@@ -247,6 +260,7 @@ __device__ __forceinline__ void process_block(uint32_t (&st)[8], uint32_t slot, 
     uint8_t* dst = digests + msg * HB_SLOT_BYTES;
     stg128_cs(dst, o[0], o[1], o[2], o[3]);
     stg128_cs(dst + 16, o[4], o[5], o[6], o[7]);
+    note_message_done(a, msg);
   }
 }
 
@@ -259,12 +273,12 @@ __device__ __forceinline__ void process_block(uint32_t (&st)[8], uint32_t slot, 
 template <int ALG, int KB>
 __device__ __forceinline__ void process_stage(uint32_t (&st)[8], uint32_t slot, uint32_t s,
                                               uint32_t len, uint32_t b0, uint64_t msg,
-                                              uint8_t* digests, const MulConsts& mc) {
+                                              const KernelArgs& a) {
   const uint32_t nb = padded_blocks(len);
 #pragma unroll 1
   for (int j = 0; j < KB; ++j) {
     if (b0 + j >= nb) break;
-    process_block<ALG>(st, slot + 64 * j, s, len, b0 + j, msg, digests, mc);
+    process_block<ALG>(st, slot + 64 * j, s, len, b0 + j, msg, a.digests, a.mc, a);
   }
 }
 
@@ -391,13 +405,13 @@ __device__ __forceinline__ void warp_pipeline(Source& src, uint8_t* wsm, const K
       if constexpr (MIXED) {
         const uint32_t alg = rec.y >> 28;
         if (alg == HB_MD5)
-          process_stage<HB_MD5, KB>(st, slot, s, rec.z, rec.w, msg, a.digests, a.mc);
+          process_stage<HB_MD5, KB>(st, slot, s, rec.z, rec.w, msg, a);
         else if (alg == HB_SHA1)
-          process_stage<HB_SHA1, KB>(st, slot, s, rec.z, rec.w, msg, a.digests, a.mc);
+          process_stage<HB_SHA1, KB>(st, slot, s, rec.z, rec.w, msg, a);
         else
-          process_stage<HB_SM3, KB>(st, slot, s, rec.z, rec.w, msg, a.digests, a.mc);
+          process_stage<HB_SM3, KB>(st, slot, s, rec.z, rec.w, msg, a);
       } else {
-        process_stage<ALG, KB>(st, slot, s, rec.z, rec.w, msg, a.digests, a.mc);
+        process_stage<ALG, KB>(st, slot, s, rec.z, rec.w, msg, a);
       }
     }
     --inflight;

@@ -258,3 +258,59 @@ def test_int_peak_microbenchmark_runs(hb):
         cyc = hb.int_peak(op, sms, 128, 10)
         torch.cuda.synchronize()
         assert int(cyc.min().item()) > 0
+
+
+# ---------------------------------------------------------------------------
+# plans: private scratch, concurrent streams, captured graphs
+
+def test_plan_run_matches_mixed_path(hb):
+    b = workloads.ragged(9000, seed=41, max_len=5000)
+    packed, off, ln, algs = hb.to_device(b)
+    want = hb.hash_batch_mixed(algs, packed, off, ln).cpu().numpy()
+    plan = hb.Plan(b.n)
+    out = torch.zeros((b.n, 32), dtype=torch.uint8, device="cuda")
+    plan.run(algs, packed, off, ln, out)
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy(), want)
+    with pytest.raises(hb.HashBatchError):
+        plan.run(algs, packed, off, ln, out, n=b.n + 1)
+    plan.close()
+
+
+def test_two_plans_on_two_streams(hb, oracle_mod):
+    b1 = workloads.ragged(6000, seed=42, max_len=9000)
+    b2 = workloads.ragged(4000, seed=43, max_len=3000)
+    d1, d2 = hb.to_device(b1), hb.to_device(b2)
+    p1, p2 = hb.Plan(b1.n), hb.Plan(b2.n)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    o1 = torch.zeros((b1.n, 32), dtype=torch.uint8, device="cuda")
+    o2 = torch.zeros((b2.n, 32), dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+    for _ in range(3):
+        p1.run(d1[3], d1[0], d1[1], d1[2], o1, stream=s1)
+        p2.run(d2[3], d2[0], d2[1], d2[2], o2, stream=s2)
+    torch.cuda.synchronize()
+    _assert_slots_equal(o1.cpu().numpy(), _oracle_slots(oracle_mod, b1, None), "plan 1")
+    _assert_slots_equal(o2.cpu().numpy(), _oracle_slots(oracle_mod, b2, None), "plan 2")
+    p1.close()
+    p2.close()
+
+
+def test_captured_graph_replays_for_any_batch_size(hb):
+    b = workloads.ragged(12000, seed=44, max_len=6000)
+    packed, off, ln, algs = hb.to_device(b)
+    plan = hb.Plan(b.n)
+    out = torch.zeros((b.n, 32), dtype=torch.uint8, device="cuda")
+    plan.capture(algs, packed, off, ln, out)
+    for n in (b.n, 1, 33, 5000, b.n):
+        out.zero_()
+        plan.replay(n)
+        torch.cuda.synchronize()
+        want = hb.hash_batch_mixed(algs[:n].contiguous(), packed, off[:n].contiguous(),
+                                   ln[:n].contiguous()).cpu().numpy()
+        got = out.cpu().numpy()
+        assert np.array_equal(got[:n], want), n
+        assert not got[n:].any()
+    with pytest.raises(hb.HashBatchError):
+        plan.replay(b.n + 1)
+    plan.close()
