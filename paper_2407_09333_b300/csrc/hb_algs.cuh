@@ -19,6 +19,14 @@ namespace hb {
 
 // Algorithm descriptors -------------------------------------------------------
 
+// Whether an algorithm moves its adds to the FMA pipe (hb_device.cuh).  SHA-1
+// and SM3 are bound by the ALU pipe and gain; MD5's round is one long chain of
+// dependent operations, and at a few warps per SM sub-partition (long
+// messages) the IMAD's longer latency costs more than the freed ALU slots.
+constexpr bool kMd5Fma = false;
+constexpr bool kSha1Fma = true;
+constexpr bool kSm3Fma = true;
+
 template <int ALG>
 struct AlgTraits;
 
@@ -54,17 +62,17 @@ __device__ __forceinline__ void md5_init(uint32_t (&st)[8]) {
 }
 
 // One operation a = b + ((a + g(b,c,d) + X[k] + T[i]) <<< s).  The sum
-// a + X[k] + T[i] does not depend on b, c, d and is one IADD3; the rest
-// alternates between two splits: V = 1 puts the rotate-and-add on the FMA
-// pipe (ALU 2, FMA 3), V = 0 rotates on the ALU (ALU 3, FMA 2).
-#define HB_MD5_OP(LUT, a, b, c, d, xk, t, s, V)     \
-  do {                                             \
-    a += (xk) + (t);                               \
-    a = add_f(lop3<LUT>(b, c, d), a, mc);          \
-    if (V)                                         \
-      a = rotl_add_f<s>(a, b, mc);                 \
-    else                                           \
-      a = add_f(rotl<s>(a), b, mc);                \
+// a + X[k] + T[i] does not depend on b, c, d and is one IADD3.  (V selects
+// between two equivalent forms of the rotate-and-add; they differ only when
+// the adds go to the FMA pipe.)
+#define HB_MD5_OP(LUT, a, b, c, d, xk, t, s, V)           \
+  do {                                                   \
+    a += (xk) + (t);                                     \
+    a = add_f<kMd5Fma>(lop3<LUT>(b, c, d), a, mc);       \
+    if (V)                                               \
+      a = rotl_add_f<s, kMd5Fma>(a, b, mc);              \
+    else                                                 \
+      a = add_f<kMd5Fma>(rotl<s>(a), b, mc);             \
   } while (0)
 
 // Round 2's G(x,y,z) = (x & z) | (y & ~z): LUT built with x->a, y->b, z->c.
@@ -140,10 +148,10 @@ __device__ __forceinline__ void md5_compress(uint32_t (&st)[8], const uint32_t (
   HB_MD5_OP(LUT_MD5_I, d, a, b, c, X[11], T[61], 10, 0);
   HB_MD5_OP(LUT_MD5_I, c, d, a, b, X[2], T[62], 15, 1);
   HB_MD5_OP(LUT_MD5_I, b, c, d, a, X[9], T[63], 21, 0);
-  st[0] = add_f(st[0], a, mc);
-  st[1] = add_f(st[1], b, mc);
-  st[2] = add_f(st[2], c, mc);
-  st[3] = add_f(st[3], d, mc);
+  st[0] = add_f<kMd5Fma>(st[0], a, mc);
+  st[1] = add_f<kMd5Fma>(st[1], b, mc);
+  st[2] = add_f<kMd5Fma>(st[2], c, mc);
+  st[3] = add_f<kMd5Fma>(st[3], d, mc);
 }
 #undef HB_MD5_OP
 
@@ -175,26 +183,27 @@ __device__ __forceinline__ constexpr uint32_t sha1_k() {
 }
 
 // Rounds T .. 79 by compile-time recursion; W is the 16-word schedule ring.
-// Split per round: the schedule word (two LOP3 and a rotate), f and
-// e + W + K (IADD3) on the ALU; (f + that) and the rotate-and-add of a on the
-// FMA pipe; ROTL30(b) on the FMA pipe while the schedule runs (ALU 5, FMA 5),
-// on the ALU before it (ALU 3, FMA 3).
+// Split per round: the schedule word (two LOP3 and a rotate), f, ROTL30(b)
+// and the shift-and-add half of ROTL5(a) + sum on the ALU; the adds
+// e + W, + K, + f and the multiply half of ROTL5(a) + sum on the FMA pipe
+// (ALU 6, FMA 4 while the schedule runs).
 template <int T>
 __device__ __forceinline__ void sha1_rounds(uint32_t& a, uint32_t& b, uint32_t& c, uint32_t& d,
                                             uint32_t& e, uint32_t (&W)[16], const MulConsts& mc) {
   if constexpr (T < 80) {
+    // The round constant as a register operand of an IMAD (one MOV per group
+    // of twenty rounds after the compiler hoists it).
+    uint32_t k = sha1_k<T>();
+    asm("" : "+r"(k));
     if constexpr (T >= 16) {
       W[T & 15] = rotl<1>(lop3<LUT_XOR3>(W[(T - 3) & 15], W[(T - 8) & 15], W[(T - 14) & 15]) ^
                           W[T & 15]);
     }
-    const uint32_t ewk = e + W[T & 15] + sha1_k<T>();
-    const uint32_t t = rotl_add_f<5>(a, add_f(sha1_f<T>(b, c, d), ewk, mc), mc);
+    const uint32_t ewk = add_f<kSha1Fma>(add_f<kSha1Fma>(e, W[T & 15], mc), k, mc);
+    const uint32_t t = rotl_add_f<5, kSha1Fma>(a, add_f<kSha1Fma>(sha1_f<T>(b, c, d), ewk, mc), mc);
     e = d;
     d = c;
-    if constexpr (T >= 16)
-      c = rotl_f<30>(b, mc);
-    else
-      c = rotl<30>(b);
+    c = rotl<30>(b);
     b = a;
     a = t;
     sha1_rounds<T + 1>(a, b, c, d, e, W, mc);
@@ -208,11 +217,11 @@ __device__ __forceinline__ void sha1_compress(uint32_t (&st)[8], const uint32_t 
   for (int i = 0; i < 16; ++i) W[i] = X[i];
   uint32_t a = st[0], b = st[1], c = st[2], d = st[3], e = st[4];
   sha1_rounds<0>(a, b, c, d, e, W, mc);
-  st[0] = add_f(st[0], a, mc);
-  st[1] = add_f(st[1], b, mc);
-  st[2] = add_f(st[2], c, mc);
-  st[3] = add_f(st[3], d, mc);
-  st[4] = add_f(st[4], e, mc);
+  st[0] = add_f<kSha1Fma>(st[0], a, mc);
+  st[1] = add_f<kSha1Fma>(st[1], b, mc);
+  st[2] = add_f<kSha1Fma>(st[2], c, mc);
+  st[3] = add_f<kSha1Fma>(st[3], d, mc);
+  st[4] = add_f<kSha1Fma>(st[4], e, mc);
 }
 
 // ---------------------------------------------------------------------------
@@ -247,18 +256,16 @@ __device__ __forceinline__ uint32_t sm3_p1(uint32_t x) {
 
 // Rounds J .. 63.  W is a 16-word ring holding W_{J} .. W_{J+3} (and older
 // words still needed); round J first extends it with W_{J+4} (Sec. 5.3.2),
-// so that W'_J = W_J ^ W_{J+4} is available.  Split per round: rotations
-// feeding XORs, the Boolean functions, P0 and SS1's sum on the ALU; the six
-// adds of TT1 and TT2 and the standalone rotations B<<<9 and F<<<19 on the
-// FMA pipe (ALU 10, FMA 10); the expansion adds three LOP3 and P1's two
-// rotations on the ALU and its two word rotations on the FMA pipe.
+// so that W'_J = W_J ^ W_{J+4} is available.  Split per round: rotations,
+// the Boolean functions, P0 and SS1's sum on the ALU; the six adds of TT1 and
+// TT2 on the FMA pipe; the expansion (three LOP3, four rotations) on the ALU.
 template <int J>
 __device__ __forceinline__ void sm3_rounds(uint32_t (&v)[8], uint32_t (&W)[16], const MulConsts& mc) {
   if constexpr (J < 64) {
     constexpr int M = J + 4;  // index of the word produced this round
     if constexpr (M >= 16 && M < 68) {
-      const uint32_t x = lop3<LUT_XOR3>(W[(M - 16) & 15], W[(M - 9) & 15], rotl_f<15>(W[(M - 3) & 15], mc));
-      W[M & 15] = lop3<LUT_XOR3>(sm3_p1(x), rotl_f<7>(W[(M - 13) & 15], mc), W[(M - 6) & 15]);
+      const uint32_t x = lop3<LUT_XOR3>(W[(M - 16) & 15], W[(M - 9) & 15], rotl<15>(W[(M - 3) & 15]));
+      W[M & 15] = lop3<LUT_XOR3>(sm3_p1(x), rotl<7>(W[(M - 13) & 15]), W[(M - 6) & 15]);
     }
     uint32_t& A = v[0];
     uint32_t& B = v[1];
@@ -281,14 +288,14 @@ __device__ __forceinline__ void sm3_rounds(uint32_t (&v)[8], uint32_t (&W)[16], 
       ff = lop3<LUT_MAJ>(A, B, C);
       gg = lop3<LUT_CHOOSE>(E, F, G);
     }
-    const uint32_t tt1 = add_f(ss2, add_f(ff, add_f(D, wpj, mc), mc), mc);
-    const uint32_t tt2 = add_f(ss1, add_f(gg, add_f(H, wj, mc), mc), mc);
+    const uint32_t tt1 = add_f<kSm3Fma>(ss2, add_f<kSm3Fma>(ff, add_f<kSm3Fma>(D, wpj, mc), mc), mc);
+    const uint32_t tt2 = add_f<kSm3Fma>(ss1, add_f<kSm3Fma>(gg, add_f<kSm3Fma>(H, wj, mc), mc), mc);
     D = C;
-    C = rotl_f<9>(B, mc);
+    C = rotl<9>(B);
     B = A;
     A = tt1;
     H = G;
-    G = rotl_f<19>(F, mc);
+    G = rotl<19>(F);
     F = E;
     E = sm3_p0(tt2);
     sm3_rounds<J + 1>(v, W, mc);

@@ -39,16 +39,20 @@ __device__ __forceinline__ uint32_t rotl(uint32_t x) {
 
 // ---------------------------------------------------------------------------
 // Work for the multiply-add pipe.  The SM's 32-bit integer ALU pipe (LOP3,
-// IADD3, SHF, PRMT) retires 64 results per clock per SM; the multiply-add
-// (FMA) pipe retires another 64 IMAD results per clock concurrently.  An add
-// becomes x * 1 + y and a rotation becomes the two halves of x * 2^s, with
-// the factors read from kernel arguments so that the compiler cannot turn the
-// multiplications back into ALU adds and shifts:
-//   rotl(x, s) + y = mad.hi(x, 2^s, mad.lo(x, 2^s, y))   (s = 1..31)
-// because x * 2^s = (x >> (32 - s)) * 2^32 + (x << s) and the two parts do not
-// overlap.  HB_FMA_OFFLOAD=0 builds the plain ALU forms for comparison.
+// IADD3, SHF, LEA, PRMT) retires 64 results per clock per SM; the multiply-add
+// (FMA) pipe retires another 64 IMAD results per clock at the same time.  A
+// two-input add becomes x * 1 + y, and a rotate-and-add splits into one ALU
+// and one FMA instruction:
+//   rotl(x, s) + y = x * 2^s + ((x >> (32 - s)) + y)       (s = 1..31)
+// because x * 2^s mod 2^32 = x << s and the two parts of the rotation do not
+// overlap; the shift-and-add is one LEA.HI.  The factors 1 and 2^s are kernel
+// arguments, so the compiler cannot turn the multiplications back into ALU
+// adds and shifts.  Standalone rotations stay one SHF on the ALU: moving one
+// to the FMA pipe takes an IMAD.HI, which retires at a quarter of IMAD's rate.
+// Each algorithm chooses (template argument F) whether its adds go to the
+// FMA pipe; HB_FMA_OFFLOAD=0 forces the plain ALU forms everywhere.
 #ifndef HB_FMA_OFFLOAD
-#define HB_FMA_OFFLOAD 0
+#define HB_FMA_OFFLOAD 1
 #endif
 
 __device__ __forceinline__ uint32_t mad_lo(uint32_t a, uint32_t b, uint32_t c) {
@@ -57,36 +61,18 @@ __device__ __forceinline__ uint32_t mad_lo(uint32_t a, uint32_t b, uint32_t c) {
   return d;
 }
 
-__device__ __forceinline__ uint32_t mad_hi(uint32_t a, uint32_t b, uint32_t c) {
-  uint32_t d;
-  asm("mad.hi.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
-  return d;
-}
-
-// x + y on the FMA pipe.
+// x + y, on the FMA pipe when F.
+template <bool F>
 __device__ __forceinline__ uint32_t add_f(uint32_t x, uint32_t y, const MulConsts& m) {
-#if HB_FMA_OFFLOAD
-  return mad_lo(x, m.one, y);
-#else
-  return x + y;
-#endif
+  if constexpr (F && HB_FMA_OFFLOAD) return mad_lo(x, m.one, y);
+  else return x + y;
 }
 
-// rotl(x, S) + y on the FMA pipe (two IMADs).
-template <int S>
+// rotl(x, S) + y; when F, one ALU shift-and-add and one FMA multiply-add.
+template <int S, bool F>
 __device__ __forceinline__ uint32_t rotl_add_f(uint32_t x, uint32_t y, const MulConsts& m) {
-#if HB_FMA_OFFLOAD
-  const uint32_t p = m.pow2[S];
-  return mad_hi(x, p, mad_lo(x, p, y));
-#else
-  return __funnelshift_l(x, x, S) + y;
-#endif
-}
-
-// rotl(x, S) on the FMA pipe (two IMADs).
-template <int S>
-__device__ __forceinline__ uint32_t rotl_f(uint32_t x, const MulConsts& m) {
-  return rotl_add_f<S>(x, 0u, m);
+  if constexpr (F && HB_FMA_OFFLOAD) return mad_lo(x, m.pow2[S], (x >> (32 - S)) + y);
+  else return __funnelshift_l(x, x, S) + y;
 }
 
 // Byte permute (PRMT): bytes of the 64-bit value {hi:lo} picked by `sel`.

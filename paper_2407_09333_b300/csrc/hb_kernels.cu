@@ -167,7 +167,8 @@ __global__ void hb_bounds_kernel(const uint64_t* offsets, const uint32_t* length
 // (IMAD) that the compiler cannot turn back into a plain add.
 //   0 LOP3   1 IADD3   2 SHF   3 PRMT   4 LOP3/IADD3/SHF   5 IMAD x*y+z
 //   6 LOP3/IMAD   7 IADD3/IMAD   8 SHF/IMAD   9 LOP3/FFMA   10 IMAD x*1+y
-//   11 LOP3/(x*1+y)   12 LOP3/SHF/IADD3/(x*1+y)
+//   11 LOP3/(x*1+y)   12 LOP3/SHF/IADD3/(x*1+y)   13 IMAD.HI x*2^7+y
+//   14 LOP3/IMAD.HI   15 LOP3 + rotation as IMAD.HI(x, 2^7, IMAD(x, 2^7, 0))
 
 template <int OP>
 __device__ __forceinline__ uint32_t peak_step(int u, uint32_t x, uint32_t y, uint32_t z, uint32_t one) {
@@ -187,6 +188,23 @@ __device__ __forceinline__ uint32_t peak_step(int u, uint32_t x, uint32_t y, uin
     return lop3<0x96>(x, y, z);
   } else if constexpr (OP == 10) return x * one + y;
   else if constexpr (OP == 11) return (u & 1) ? x * one + y : lop3<0x96>(x, y, z);
+  else if constexpr (OP == 13) {
+    uint32_t d;
+    asm("mad.hi.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(x), "r"(one << 7), "r"(y));
+    return d;
+  } else if constexpr (OP == 14) {
+    if (!(u & 1)) return lop3<0x96>(x, y, z);
+    uint32_t d;
+    asm("mad.hi.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(x), "r"(one << 7), "r"(y));
+    return d;
+  } else if constexpr (OP == 15) {
+    // one LOP3 and one two-IMAD rotation per pair of chain steps
+    if (!(u & 1)) return lop3<0x96>(x, y, z);
+    uint32_t lo, d;
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(lo) : "r"(x), "r"(one << 7), "r"(0u));
+    asm("mad.hi.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(x), "r"(one << 7), "r"(lo));
+    return d;
+  }
   else {
     const int m = u & 3;
     return m == 0 ? lop3<0x96>(x, y, z) : m == 1 ? __funnelshift_l(x, y, 7)
@@ -375,7 +393,8 @@ cudaError_t launch_int_peak(int op, int blocks, int threads, int iters, unsigned
                              int_peak_launch<3>, int_peak_launch<4>, int_peak_launch<5>,
                              int_peak_launch<6>, int_peak_launch<7>, int_peak_launch<8>,
                              int_peak_launch<9>, int_peak_launch<10>, int_peak_launch<11>,
-                             int_peak_launch<12>};
+                             int_peak_launch<12>, int_peak_launch<13>, int_peak_launch<14>,
+                             int_peak_launch<15>};
   if (op < 0 || op >= (int)(sizeof(table) / sizeof(table[0]))) return cudaErrorInvalidValue;
   table[op](blocks, threads, iters, cycles, sink, stream);
   return cudaGetLastError();
