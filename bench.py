@@ -203,14 +203,20 @@ class Dist:
             else:
                 self.pg.barrier()
 
-    def max(self, value: float) -> float:
-        if not self.pg:
-            return value
+    def _reduce(self, value: float, op) -> float:
         import torch
         dev = "cuda" if self.pg.get_backend() == "nccl" else "cpu"
         t = torch.tensor([value], dtype=torch.float64, device=dev)
-        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        self.pg.all_reduce(t, op=op)
         return float(t.item())
+
+    def max(self, value: float) -> float:
+        """Largest value over ranks (the job's time is its slowest rank's)."""
+        return self._reduce(value, self.pg.ReduceOp.MAX) if self.pg else value
+
+    def sum(self, value: float) -> float:
+        """Sum over ranks (the job's bytes are every rank's shard)."""
+        return self._reduce(value, self.pg.ReduceOp.SUM) if self.pg else value
 
     def close(self):
         if self.pg:
@@ -220,6 +226,11 @@ class Dist:
 def shard_seed(base: int, rank: int) -> int:
     """Each rank hashes its own disjoint synthetic shard."""
     return base + 1000 * rank
+
+
+def job_rate(dist, local_units: float, local_seconds: float) -> float:
+    """Whole-job rate: every rank's units over the slowest rank's time."""
+    return dist.sum(local_units) / dist.max(local_seconds)
 
 
 # ---------------------------------------------------------------------------
@@ -304,7 +315,14 @@ def run_reference(args, dist):
     import oracle
     threads = oracle.host_threads()
     sub = oracle_sample(batch, mixed, 1 << 18 if args.workload != "c4" else 1 << 10)
-    for _ in range(args.warmup):
+    # keep the whole run within about two minutes: shrink the per-step sample
+    # if one step of it would make warm-up plus timed steps take longer
+    dt, _, _ = time_oracle(sub, mixed, threads)
+    budget_s = 120.0
+    runs = args.warmup + args.steps
+    if dt * runs > budget_s and sub.n > 64:
+        sub = oracle_sample(batch, mixed, max(64, int(sub.n * budget_s / (dt * runs))))
+    for _ in range(args.warmup - 1):
         time_oracle(sub, mixed, threads)
     tot_t = tot_b = tot_m = 0
     for _ in range(args.steps):
@@ -434,13 +452,15 @@ def run_ours(args, dist):
     dist.barrier()
     ms_local = t_start.elapsed_time(t_end)
     ms = dist.max(ms_local)
+    job_bytes = dist.sum(float(bytes_per_step) * args.steps)
+    job_msgs = dist.sum(float(msgs_per_step) * args.steps)
     status = api.device_status()
     if status:
         raise SystemExit("device status reported error bits %#x" % status)
 
     per_launch_ms = [statistics.median([ev[k][j][0].elapsed_time(ev[k][j][1]) for k in range(args.steps)])
                      for j in range(nl)]
-    value = dist.world * bytes_per_step * args.steps / (ms * 1e-3) / 1e9
+    value = job_bytes / (ms * 1e-3) / 1e9
     peaks = load_peaks()
     clk = clocks.summary()
     sm_mhz = clk["sm_mhz"] or peaks["sm_max_mhz"]
@@ -490,7 +510,7 @@ def run_ours(args, dist):
         "config": {"workload": desc, "messages_per_gpu": n, "bytes_per_gpu": batch.total_bytes,
                    "l2": "no flush: inputs larger than the 126 MB L2",
                    "parallelism": "dp%d: disjoint message shards, no collective on the data path" % dist.world},
-        "mhash_per_s": dist.world * msgs_per_step * args.steps / (ms * 1e-3) / 1e6,
+        "mhash_per_s": job_msgs / (ms * 1e-3) / 1e6,
         "per_alg": per_alg,
         "tuned_shapes": tuned,
         "roofline": roofline,
@@ -501,17 +521,18 @@ def run_ours(args, dist):
     }
 
     if not args.no_e2e:
-        line["e2e"] = e2e_measure(args, batch, mixed, api, torch)
+        line["e2e"] = e2e_measure(args, batch, mixed, api, torch, dist)
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(batch, mixed)
     if dist.rank == 0:
         print(json.dumps(line), flush=True)
 
 
-def e2e_measure(args, batch, mixed, api, torch):
+def e2e_measure(args, batch, mixed, api, torch, dist):
     """Same metric through hash_batch_host with pinned host buffers: the
     host->device copy of the step's inputs and the device->host copy of its
-    digests are inside the timed region."""
+    digests are inside the timed region.  Whole job: every rank's bytes over
+    the slowest rank's time."""
     n = batch.n
     packed_h = torch.from_numpy(np.ascontiguousarray(batch.packed)).pin_memory()
     off_h = torch.from_numpy(batch.offsets.view(np.int64)).pin_memory()
@@ -527,12 +548,16 @@ def e2e_measure(args, batch, mixed, api, torch):
     steps = max(1, min(args.steps, args.e2e_steps))
     for _ in range(max(1, min(args.warmup, 3))):
         step()
+    torch.cuda.synchronize()
+    dist.barrier()
     t0 = time.perf_counter()
     for _ in range(steps):
         step()
+    torch.cuda.synchronize()
     dt = time.perf_counter() - t0
+    dist.barrier()
     per_call_in = batch.packed.nbytes + 12 * n + (n if mixed else 0)
-    return {"value": len(calls) * batch.total_bytes * steps / dt / 1e9, "unit": "GB/s",
+    return {"value": job_rate(dist, len(calls) * batch.total_bytes * steps, dt) / 1e9, "unit": "GB/s",
             "h2d_bytes_per_step": len(calls) * per_call_in,
             "d2h_bytes_per_step": len(calls) * 32 * n, "steps": steps,
             "api": "hash_batch_host (pinned host buffers)"}
@@ -615,8 +640,9 @@ def run_serve(args, dist):
     plain_ms, plain_L = plain_equal_bytes_ms(api, torch, all_lengths, all_algs)
     plain_gbs = float(all_lengths.astype(np.int64).sum()) / (plain_ms * 1e-3) / 1e9
     top = max(points, key=lambda p: p["offered_load"])
+    job_gbs = job_rate(dist, top["bytes"], top["span_s"]) / 1e9
     line = {
-        "metric": METRIC, "value": top["gbs"], "unit": "GB/s", "n_gpus": dist.world,
+        "metric": METRIC, "value": job_gbs, "unit": "GB/s", "n_gpus": dist.world,
         "steps": len(points), "warmup": 3, "ms_per_step": None, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic: Poisson arrivals; per request 1-4096 messages (log-uniform count), "
