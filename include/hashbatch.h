@@ -37,8 +37,8 @@
  * Asynchrony.  Device calls are enqueued on `stream` (a cudaStream_t; NULL
  * is the legacy default stream) and return without waiting.  The return
  * value reports argument and launch errors only.  Errors found by a kernel
- * (a bulk-copy wait that timed out, a bounds violation seen by the checker)
- * are OR-ed into a per-device status word read by hash_device_status().
+ * (a bounded wait that timed out, a bounds violation seen by the checker,
+ * a malformed segment) are OR-ed into a per-device status word read by hash_device_status().
  *
  * Errors.  0 is success; negative values are the HB_ERR_* codes below;
  * hash_strerror() names them.  n == 0 is a successful no-op.
@@ -77,6 +77,9 @@ extern "C" {
 #define HB_DEV_TIMEOUT 0x1        /* a kernel's bounded wait expired         */
 #define HB_DEV_BOUNDS 0x2         /* hash_batch_check_bounds found a message
                                      outside [0, packed_len)                 */
+#define HB_DEV_SEGMENT 0x4        /* a segment that is not the last was not a
+                                     whole number of 64-byte blocks, or its
+                                     prior byte count was not (message skipped) */
 
 /* Digest size in bytes of an algorithm (16, 20, 32); 0 for an unknown code. */
 size_t hash_digest_size(int alg);
@@ -91,8 +94,8 @@ const char *hash_last_cuda_error(void);
 /*
  * hash_batch -- one algorithm for the whole batch (paper Sec. IV-B, parallel
  * op; Sec. V-D, separate slots).  One message per GPU thread; each warp stages
- * the next 64-byte block of its 32 messages into shared memory with bulk
- * copies while it compresses the current one.
+ * the next 64-byte blocks of its 32 messages into shared memory with
+ * asynchronous 16-byte copies while it compresses the current ones.
  * Returns HB_OK, HB_ERR_INVALID_ALG, HB_ERR_NULL, HB_ERR_ALIGN, HB_ERR_CUDA.
  * Limits: n < 2^40.
  */
@@ -115,6 +118,36 @@ int hash_batch_mixed(const uint8_t *algs, const uint8_t *packed_bytes,
                      uint8_t *digests_out, void *stream);
 
 /*
+ * hash_batch_segments -- hash_batch_mixed over pieces ("segments") of
+ * messages, so that a long message can be hashed over several calls with only
+ * its current piece in device memory (the serving loop streams long messages
+ * this way).  The iterated compression of RFC 1321 Sec. 3.4, FIPS 180-4
+ * Sec. 6.1.2 / the SHA-1 loop, and GB/T 32905 Sec. 5.3 only needs the chaining
+ * value between blocks; it travels from one segment to the next in the
+ * message's 32-byte slot.
+ *   seg[i] = P | (more ? HB_SEG_MORE : 0): P = bytes of message i hashed by
+ *   earlier calls (a multiple of 64, below 2^61); HB_SEG_MORE marks a segment
+ *   that is not the message's last.  packed_bytes + offsets[i] holds the
+ *   segment's lengths[i] bytes.
+ *   - P == 0: the chain starts from the algorithm's initial value.
+ *     P > 0: slots_inout[i] must hold what the call with the previous
+ *     segment left in its slot (copy the 32 bytes if the index changes).
+ *   - more: lengths[i] must be a multiple of 64; afterwards slot i holds the
+ *     chaining value (internal format, 32 bytes; pass it back unchanged).
+ *   - last: slot i receives the digest of the whole message (P + lengths[i]
+ *     bytes), exactly as hash_batch_mixed would for the whole message.
+ *   A segment that breaks a multiple-of-64 rule is skipped and sets
+ *   HB_DEV_SEGMENT in the device status (hash_device_status).
+ * Consecutive segments of one message must be ordered (same stream, or an
+ * event between the calls).  Limits and return codes as hash_batch_mixed.
+ */
+#define HB_SEG_MORE (1ull << 63)
+int hash_batch_segments(const uint8_t *algs, const uint8_t *packed_bytes,
+                        const uint64_t *offsets, const uint32_t *lengths,
+                        const uint64_t *seg, uint64_t n, uint8_t *slots_inout,
+                        void *stream);
+
+/*
  * hash_batch_mixed_noalloc -- hash_batch_mixed for callers that cannot
  * allocate device memory.  The paper has no counterpart: it exists because
  * hash_batch_mixed may call cudaMalloc (its scratch area and the per-device
@@ -122,7 +155,7 @@ int hash_batch_mixed(const uint8_t *algs, const uint8_t *packed_bytes,
  * device memory belongs to another owner under a fixed budget, or a
  * latency-critical loop that must not meet the device-wide synchronisation
  * an allocation can cause.  This variant allocates nothing: its bucketing
- * scratch is a fixed array of about 4.34 MB compiled into the library, held
+ * scratch is a fixed array of about 4.30 MB compiled into the library, held
  * by every GPU that loads the library until the process exits.
  *   - n must be at most HB_NOALLOC_MAX_MESSAGES; larger batches return
  *     HB_ERR_TOO_LARGE without touching the GPU.  n == 0 is a no-op.
@@ -173,6 +206,11 @@ int hash_batch_mixed_noalloc(const uint8_t *algs, const uint8_t *packed_bytes,
  *                      (NULL = off); before the first capture.  done_flags
  *                      must be page-locked host memory mapped for the device
  *                      (cudaHostAlloc); other memory returns HB_ERR_ARG.
+ * hash_plan_set_segments -- the plan's batches are segments as in
+ *                      hash_batch_segments: seg_dev[i] (device uint64) describes
+ *                      message i of a batch, and the digest slots carry
+ *                      chaining values between segments.  NULL = whole
+ *                      messages.  Before the first capture; HB_ERR_ARG after.
  * hash_plan_destroy -- synchronises the device and frees the plan.
  * A plan's scratch is used by one batch at a time: order the runs and
  * replays of one plan (same stream, or events); different plans overlap.
@@ -204,6 +242,7 @@ int hash_plan_replay(hb_plan *plan, uint64_t n, void *stream);
 int hash_plan_configure(hb_plan *plan, int shape_index, int warps_per_sm);
 int hash_plan_set_completion(hb_plan *plan, const uint32_t *msg_req_dev, uint32_t *remaining_dev,
                              uint32_t *done_flags);
+int hash_plan_set_segments(hb_plan *plan, const uint64_t *seg_dev);
 int hash_plan_destroy(hb_plan *plan);
 
 /*

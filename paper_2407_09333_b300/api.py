@@ -21,6 +21,8 @@ ALG_CODES = {v: k for k, v in ALG_NAMES.items()}
 
 DEV_TIMEOUT = 0x1
 DEV_BOUNDS = 0x2
+DEV_SEGMENT = 0x4
+SEG_MORE = 1 << 63
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 # HB_LIBRARY may name another build of the same library (e.g. an A/B variant).
@@ -35,6 +37,7 @@ _SIGNATURES = {
     "hash_batch": (_c_int, [_c_int, _vp, _vp, _vp, _c_u64, _vp, _vp]),
     "hash_batch_mixed": (_c_int, [_vp, _vp, _vp, _vp, _c_u64, _vp, _vp]),
     "hash_batch_mixed_noalloc": (_c_int, [_vp, _vp, _vp, _vp, _c_u64, _vp, _vp]),
+    "hash_batch_segments": (_c_int, [_vp, _vp, _vp, _vp, _vp, _c_u64, _vp, _vp]),
     "hash_batch_check_bounds": (_c_int, [_vp, _vp, _c_u64, _c_u64, _vp, _vp]),
     "hash_batch_host": (_c_int, [_c_int, _vp, _vp, _c_u64, _vp, _vp, _c_u64, _vp, _vp]),
     "hash_device_status": (_c_int, [_vp, ctypes.POINTER(_c_int)]),
@@ -60,6 +63,7 @@ _SIGNATURES = {
     "hash_plan_destroy": (_c_int, [_vp]),
     "hash_plan_configure": (_c_int, [_vp, _c_int, _c_int]),
     "hash_plan_set_completion": (_c_int, [_vp, _vp, _vp, _vp]),
+    "hash_plan_set_segments": (_c_int, [_vp, _vp]),
     "hash_gather": (_c_int, [_vp, _c_u32, _vp]),
 }
 
@@ -174,6 +178,32 @@ def hash_batch_mixed(algs, packed, offsets, lengths, out=None, stream=None,
         _dev_ptr(out, 1, "out"), int(shape), int(grid), _stream_handle(stream))
     _check(rc, "hash_batch_mixed")
     return out
+
+
+def seg_words(prior, more):
+    """Segment descriptors for hash_batch_segments: prior byte counts (a
+    multiple of 64) with SEG_MORE set where more segments follow, as int64
+    (the bit pattern of the C-ABI's uint64)."""
+    prior = np.asarray(prior, dtype=np.uint64)
+    more = np.asarray(more, dtype=bool)
+    return (prior | np.where(more, np.uint64(SEG_MORE), np.uint64(0))).view(np.int64)
+
+
+def hash_batch_segments(algs, packed, offsets, lengths, seg, slots, stream=None):
+    """One call over message segments; `slots` (n, 32) uint8 carries the
+    chaining values between calls and receives the digests of messages whose
+    last segment this is (see hash_batch_segments in the C header)."""
+    n = int(offsets.numel())
+    if lengths.numel() != n or algs.numel() != n or seg.numel() != n:
+        raise ValueError("algs, offsets, lengths and seg must have one entry per message")
+    if slots.dtype.itemsize != 1 or slots.numel() < n * SLOT_BYTES or not slots.is_contiguous():
+        raise ValueError("slots must be a contiguous uint8 tensor of n*32 bytes")
+    rc = lib().hash_batch_segments(
+        _dev_ptr(algs, 1, "algs"), _dev_ptr(packed, 1, "packed"),
+        _dev_ptr(offsets, 8, "offsets"), _dev_ptr(lengths, 4, "lengths"),
+        _dev_ptr(seg, 8, "seg"), n, _dev_ptr(slots, 1, "slots"), _stream_handle(stream))
+    _check(rc, "hash_batch_segments")
+    return slots
 
 
 NOALLOC_MAX_MESSAGES = 1 << 20
@@ -295,6 +325,13 @@ class Plan:
                                               ctypes.c_void_p(done_flags.data_ptr())),
                "hash_plan_set_completion")
         self._flags = (msg_req, remaining, done_flags)
+
+    def set_segments(self, seg):
+        """Batches of this plan are message segments described by the CUDA
+        int64 tensor `seg` (see seg_words); before the first capture."""
+        _check(lib().hash_plan_set_segments(self._h, _dev_ptr(seg, 8, "seg")),
+               "hash_plan_set_segments")
+        self._seg = seg
 
     def capture(self, algs, packed, offsets, lengths, out, grid=0):
         _check(lib().hash_plan_capture(self._h, _dev_ptr(algs, 1, "algs"),

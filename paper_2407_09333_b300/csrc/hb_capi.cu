@@ -56,6 +56,7 @@ struct Ctx {
   int* status = nullptr;                 // device word of HB_DEV_* bits
   int occ_plain[3][kMaxShapes] = {};     // resident blocks per SM, 0 = not prepared
   int occ_mixed[kMaxShapes] = {};
+  int occ_mixed_seg[kMaxShapes] = {};    // segment-aware variant
   int tune_plain[3] = {0, 0, 0};
   int tune_mixed = hb::kDefaultMixedShape;
   int mixed_warps_per_sm = hb::kDefaultMixedWarpsPerSm;  // 0 = full occupancy
@@ -102,12 +103,13 @@ int get_ctx(Ctx** out) {
   return HB_OK;
 }
 
-int occupancy(Ctx* c, bool mixed, int alg, int shape, int* occ) {
+int occupancy(Ctx* c, bool mixed, int alg, int shape, int* occ, bool seg = false) {
   if (shape < 0 || shape >= kMaxShapes || shape >= hb::num_shapes()) return HB_ERR_ARG;
-  int& slot = mixed ? c->occ_mixed[shape] : c->occ_plain[alg][shape];
+  seg = seg && mixed;
+  int& slot = seg ? c->occ_mixed_seg[shape] : mixed ? c->occ_mixed[shape] : c->occ_plain[alg][shape];
   if (slot == 0) {
     int b = 0;
-    cudaError_t e = hb::prepare_kernel(mixed, alg, shape, &b);
+    cudaError_t e = hb::prepare_kernel(mixed, alg, shape, &b, seg);
     if (e != cudaSuccess) return cuda_fail(e);
     slot = b > 0 ? b : 1;
   }
@@ -153,7 +155,7 @@ int launch_mixed(Ctx* c, int shape, int grid, const uint8_t* algs, const uint8_t
                  const uint64_t* offsets, const uint32_t* lengths, uint64_t n, uint8_t* digests,
                  void* ws, const int* abort_flag, cudaStream_t s, const uint64_t* n_dev = nullptr,
                  const hb::BucketCfg* buckets = nullptr, int warps_per_sm = -1,
-                 const Completion* comp = nullptr) {
+                 const Completion* comp = nullptr, const uint64_t* seg = nullptr) {
   if (shape < 0 || shape >= hb::num_shapes()) return HB_ERR_ARG;
   MixedArgs m;
   m.cfg = buckets ? *buckets : c->buckets;
@@ -167,9 +169,10 @@ int launch_mixed(Ctx* c, int shape, int grid, const uint8_t* algs, const uint8_t
   cudaError_t e = hb::launch_bucketing(m, grid_for_elementwise(c, n), s);
   if (e != cudaSuccess) return cuda_fail(e);
   int occ = 0;
-  int rc = occupancy(c, true, 0, shape, &occ);
+  int rc = occupancy(c, true, 0, shape, &occ, seg != nullptr);
   if (rc) return rc;
   KernelArgs a{};
+  a.seg = seg;
   a.packed = packed;
   a.offsets = offsets;
   a.lengths = lengths;
@@ -269,9 +272,15 @@ int hash_batch(int alg, const uint8_t* packed_bytes, const uint64_t* offsets,
   return hash_batch_shape(alg, packed_bytes, offsets, lengths, n, digests_out, -1, 0, stream);
 }
 
-int hash_batch_mixed_shape(const uint8_t* algs, const uint8_t* packed_bytes,
-                           const uint64_t* offsets, const uint32_t* lengths, uint64_t n,
-                           uint8_t* digests_out, int shape_index, int grid_blocks, void* stream) {
+}  // extern "C"
+
+namespace {
+
+// hash_batch_mixed(_shape) and hash_batch_segments: the ragged path on the
+// per-device scratch.
+int mixed_on_ctx(const uint8_t* algs, const uint8_t* packed_bytes, const uint64_t* offsets,
+                 const uint32_t* lengths, const uint64_t* seg, uint64_t n, uint8_t* digests_out,
+                 int shape_index, int grid_blocks, void* stream) {
   if (n == 0) return HB_OK;
   if (n >= kMaxMixedN) return HB_ERR_TOO_LARGE;
   int rc = check_common(packed_bytes, offsets, lengths, n, digests_out);
@@ -284,11 +293,30 @@ int hash_batch_mixed_shape(const uint8_t* algs, const uint8_t* packed_bytes,
   if ((rc = reserve_ws(c, n))) return rc;
   if (c->ws_used && cudaStreamWaitEvent(s, c->ws_event, 0) != cudaSuccess) return cuda_fail(cudaGetLastError());
   rc = launch_mixed(c, shape_index, grid_blocks, algs, packed_bytes, offsets, lengths, n,
-                    digests_out, c->ws.p, nullptr, s);
+                    digests_out, c->ws.p, nullptr, s, nullptr, nullptr, -1, nullptr, seg);
   if (rc) return rc;
   if (cudaEventRecord(c->ws_event, s) != cudaSuccess) return cuda_fail(cudaGetLastError());
   c->ws_used = true;
   return HB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hash_batch_mixed_shape(const uint8_t* algs, const uint8_t* packed_bytes,
+                           const uint64_t* offsets, const uint32_t* lengths, uint64_t n,
+                           uint8_t* digests_out, int shape_index, int grid_blocks, void* stream) {
+  return mixed_on_ctx(algs, packed_bytes, offsets, lengths, nullptr, n, digests_out, shape_index,
+                      grid_blocks, stream);
+}
+
+int hash_batch_segments(const uint8_t* algs, const uint8_t* packed_bytes,
+                        const uint64_t* offsets, const uint32_t* lengths, const uint64_t* seg,
+                        uint64_t n, uint8_t* slots_inout, void* stream) {
+  if (n == 0) return HB_OK;
+  if (!seg) return HB_ERR_NULL;
+  return mixed_on_ctx(algs, packed_bytes, offsets, lengths, seg, n, slots_inout, -1, 0, stream);
 }
 
 int hash_batch_mixed(const uint8_t* algs, const uint8_t* packed_bytes, const uint64_t* offsets,
@@ -532,6 +560,7 @@ struct hb_plan {
   int warps_per_sm = 0;
   hb::BucketCfg buckets = hb::kDefaultBuckets;
   Completion completion;
+  const uint64_t* seg = nullptr;  // segment descriptors (hash_plan_set_segments)
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
 };
@@ -572,6 +601,13 @@ int hash_plan_set_completion(hb_plan* p, const uint32_t* msg_req_dev, uint32_t* 
   p->completion.msg_req = msg_req_dev;
   p->completion.remaining = remaining_dev;
   p->completion.done = done_dev;
+  return HB_OK;
+}
+
+int hash_plan_set_segments(hb_plan* p, const uint64_t* seg_dev) {
+  if (!p) return HB_ERR_NULL;
+  if (p->exec) return HB_ERR_ARG;  // before capturing
+  p->seg = seg_dev;
   return HB_OK;
 }
 
@@ -624,7 +660,7 @@ int hash_plan_run(hb_plan* p, const uint8_t* algs, const uint8_t* packed_bytes,
   if (c->device != p->device) return HB_ERR_ARG;
   return launch_mixed(c, p->shape, grid_blocks, algs, packed_bytes, offsets, lengths, n,
                       digests_out, p->ws, nullptr, static_cast<cudaStream_t>(stream), nullptr,
-                      &p->buckets, p->warps_per_sm, &p->completion);
+                      &p->buckets, p->warps_per_sm, &p->completion, p->seg);
 }
 
 int hash_plan_capture(hb_plan* p, const uint8_t* algs, const uint8_t* packed_bytes,
@@ -638,7 +674,7 @@ int hash_plan_capture(hb_plan* p, const uint8_t* algs, const uint8_t* packed_byt
   if ((rc = get_ctx(&c))) return rc;
   if (c->device != p->device) return HB_ERR_ARG;
   int occ = 0;
-  if ((rc = occupancy(c, true, 0, p->shape, &occ))) return rc;  // set-up before capture
+  if ((rc = occupancy(c, true, 0, p->shape, &occ, p->seg != nullptr))) return rc;  // set-up before capture
   if (p->exec) {
     cudaGraphExecDestroy(p->exec);
     p->exec = nullptr;
@@ -656,7 +692,7 @@ int hash_plan_capture(hb_plan* p, const uint8_t* algs, const uint8_t* packed_byt
     // kernels read the actual count from n_dev when the graph runs.
     rc = launch_mixed(c, p->shape, grid_blocks, algs, packed_bytes, offsets, lengths, p->max_n,
                       digests_out, p->ws, nullptr, s, p->n_dev, &p->buckets, p->warps_per_sm,
-                      &p->completion);
+                      &p->completion, p->seg);
     cudaGraph_t g = nullptr;
     const cudaError_t e2 = cudaStreamEndCapture(s, &g);
     if (rc == HB_OK && e2 != cudaSuccess) rc = cuda_fail(e2);

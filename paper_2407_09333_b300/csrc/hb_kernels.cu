@@ -32,7 +32,7 @@ __global__ void __launch_bounds__(WARPS * 32) hb_plain_kernel(KernelArgs a) {
   const uint64_t gwarp = (uint64_t)blockIdx.x * WARPS + warp;
   const uint64_t nwarps = (uint64_t)gridDim.x * WARPS;
   StaticSource<ALG> src(a, gwarp, nwarps, lane);
-  warp_pipeline<STAGES, KB, COOP, ALG, false>(src, wsm, a, lane);
+  warp_pipeline<STAGES, KB, COOP, ALG, false, false>(src, wsm, a, lane);
 }
 
 // ---------------------------------------------------------------------------
@@ -131,15 +131,16 @@ __global__ void hb_scatter_kernel(MixedArgs m) {
   }
 }
 
-template <int WARPS, int STAGES, int KB, bool COOP>
+// SEG: messages arrive as segments (a.seg), see hb_pipeline.cuh.
+template <int WARPS, int STAGES, int KB, bool COOP, bool SEG>
 __global__ void __launch_bounds__(WARPS * 32) hb_mixed_kernel(KernelArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t warp = threadIdx.x >> 5;
   if (a.abort_flag && *a.abort_flag) return;
-  uint8_t* wsm = smem + warp * WarpSmem<STAGES, KB>::kBytes;
-  DynamicSource src(a, lane);
-  warp_pipeline<STAGES, KB, COOP, HB_MD5, true>(src, wsm, a, lane);
+  uint8_t* wsm = smem + warp * WarpSmem<STAGES, KB, SEG>::kBytes;
+  DynamicSource<SEG> src(a, lane);
+  warp_pipeline<STAGES, KB, COOP, HB_MD5, true, SEG>(src, wsm, a, lane);
 }
 
 // ---------------------------------------------------------------------------
@@ -302,9 +303,9 @@ static KernelFn plain_fn(int shape) {
 #undef HB_PLAIN_CASE
 }
 
-static KernelFn mixed_fn(int shape) {
+static KernelFn mixed_fn(int shape, bool seg) {
 #define HB_MIXED_CASE(i, w, st, kb, co) \
-  case i: return hb_mixed_kernel<w, st, kb, co>;
+  case i: return seg ? hb_mixed_kernel<w, st, kb, co, true> : hb_mixed_kernel<w, st, kb, co, false>;
   switch (shape) {
     HB_SHAPES(HB_MIXED_CASE)
     default: return nullptr;
@@ -312,9 +313,9 @@ static KernelFn mixed_fn(int shape) {
 #undef HB_MIXED_CASE
 }
 
-static int shape_smem(int shape) {
+static int shape_smem(int shape, bool seg) {
 #define HB_SMEM_CASE(i, w, st, kb, co) \
-  case i: return w * WarpSmem<st, kb>::kBytes;
+  case i: return w * (seg ? WarpSmem<st, kb, true>::kBytes : WarpSmem<st, kb, false>::kBytes);
   switch (shape) {
     HB_SHAPES(HB_SMEM_CASE)
     default: return 0;
@@ -333,10 +334,10 @@ bool shape_desc(int shape, int* warps, int* stages, int* kb, int* coop) {
   return true;
 }
 
-int shape_smem_bytes(int shape) { return shape_smem(shape); }
+int shape_smem_bytes(int shape, bool seg) { return shape_smem(shape, seg); }
 
-static KernelFn pick(bool mixed, int alg, int shape) {
-  if (mixed) return mixed_fn(shape);
+static KernelFn pick(bool mixed, int alg, int shape, bool seg) {
+  if (mixed) return mixed_fn(shape, seg);
   switch (alg) {
     case HB_MD5: return plain_fn<HB_MD5>(shape);
     case HB_SHA1: return plain_fn<HB_SHA1>(shape);
@@ -345,10 +346,10 @@ static KernelFn pick(bool mixed, int alg, int shape) {
   }
 }
 
-cudaError_t prepare_kernel(bool mixed, int alg, int shape, int* blocks_per_sm) {
-  KernelFn fn = pick(mixed, alg, shape);
+cudaError_t prepare_kernel(bool mixed, int alg, int shape, int* blocks_per_sm, bool seg) {
+  KernelFn fn = pick(mixed, alg, shape, seg && mixed);
   if (!fn) return cudaErrorInvalidValue;
-  const int smem = shape_smem(shape);
+  const int smem = shape_smem(shape, seg && mixed);
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, kShapes[shape].warps * 32,
@@ -357,9 +358,10 @@ cudaError_t prepare_kernel(bool mixed, int alg, int shape, int* blocks_per_sm) {
 
 cudaError_t launch_hash(bool mixed, int alg, int shape, int grid, const KernelArgs& a,
                         cudaStream_t stream) {
-  KernelFn fn = pick(mixed, alg, shape);
+  const bool seg = mixed && a.seg != nullptr;
+  KernelFn fn = pick(mixed, alg, shape, seg);
   if (!fn || grid <= 0) return cudaErrorInvalidValue;
-  fn<<<grid, kShapes[shape].warps * 32, shape_smem(shape), stream>>>(a);
+  fn<<<grid, kShapes[shape].warps * 32, shape_smem(shape, seg), stream>>>(a);
   return cudaGetLastError();
 }
 

@@ -46,6 +46,10 @@ struct KernelArgs {
   const uint32_t* msg_req;
   uint32_t* req_remaining;
   volatile uint32_t* req_done;
+  // Optional segments (mixed path): seg[i] = bytes of message i hashed by
+  // earlier calls (a multiple of 64) | HB_SEG_MORE when more segments follow.
+  // Between segments the message's 32-byte slot carries its chaining value.
+  const uint64_t* seg;
 };
 
 // Ragged-path bucketing: groups are (cost bucket, algorithm) pairs ordered
@@ -102,10 +106,12 @@ struct MixedArgs {
 
 int num_shapes();
 bool shape_desc(int shape, int* warps, int* stages, int* kb = nullptr, int* coop = nullptr);
-int shape_smem_bytes(int shape);
+int shape_smem_bytes(int shape, bool seg = false);
 
-// Sets the kernel's shared-memory attribute and returns its occupancy.
-cudaError_t prepare_kernel(bool mixed, int alg, int shape, int* blocks_per_sm);
+// Sets the kernel's shared-memory attribute and returns its occupancy.  `seg`
+// selects the segment-aware variant of the mixed kernel.
+cudaError_t prepare_kernel(bool mixed, int alg, int shape, int* blocks_per_sm, bool seg = false);
+// The mixed path launches the segment-aware variant when a.seg is set.
 cudaError_t launch_hash(bool mixed, int alg, int shape, int grid, const KernelArgs& a,
                         cudaStream_t stream);
 cudaError_t launch_bucketing(const MixedArgs& m, int grid, cudaStream_t stream);

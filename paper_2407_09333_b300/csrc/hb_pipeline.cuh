@@ -28,6 +28,14 @@
 // last two words are replaced by the 64-bit bit length in registers.  Words
 // are read with 32-bit shared loads and realigned with one PRMT each, which
 // also applies the big-endian byte swap for SHA-1 and SM3.
+//
+// Segments (SEG, mixed path only): a message may arrive in pieces over
+// several launches.  A piece that is not the last is a whole number of
+// blocks and gets no padding; its last block's chaining value is stored raw
+// in the message's 32-byte slot.  A later piece starts from that value
+// instead of the initial one: the issuing lane copies it into shared memory
+// together with the piece's first window, so the consumer never waits on a
+// global load.  The last piece is padded with the whole message's length.
 #pragma once
 
 #include <cstdint>
@@ -48,12 +56,16 @@ constexpr int kItemBytes = 16;   // item record per lane per stage
 constexpr uint32_t kFull = 0xFFFFFFFFu;
 constexpr uint32_t kNoBlock = 0xFFFFFFFFu;
 
-template <int STAGES, int KB>
+template <int STAGES, int KB, bool SEG = false>
 struct WarpSmem {
   static constexpr int kSlots = STAGES * 32 * Slot<KB>::kBytes;
   static constexpr int kItems = STAGES * 32 * kItemBytes;
   static constexpr int kTable = 32 * 16;  // per-lane copy descriptors (cooperative copies)
-  static constexpr int kBytes = kSlots + kItems + kTable;  // multiple of 128
+  // segments: a second item record (prior bytes, more flag) and a staged
+  // chaining value per lane per stage
+  static constexpr int kSegItems = SEG ? STAGES * 32 * kItemBytes : 0;
+  static constexpr int kStates = SEG ? STAGES * 32 * HB_SLOT_BYTES : 0;
+  static constexpr int kBytes = kSlots + kItems + kTable + kSegItems + kStates;  // multiple of 128
 };
 
 // Padded block count: message + 0x80 + 8 length bytes, rounded up to 64.
@@ -68,7 +80,21 @@ struct LaneTask {
   uint32_t len;    // message length in bytes
   uint32_t nb;     // padded block count, 0 for an idle lane
   uint32_t alg;    // algorithm code
+  uint64_t seg;    // segments only: prior bytes | HB_SEG_MORE
 };
+
+// Blocks of a segment: whole blocks only when more segments follow, else
+// the padded count.  A segment that breaks the multiple-of-64 rules gets 0
+// blocks and raises HB_DEV_SEGMENT.
+__device__ __forceinline__ uint32_t segment_blocks(uint32_t len, uint64_t seg, int* status) {
+  const bool more = (seg & HB_SEG_MORE) != 0;
+  const uint64_t prior = seg & ~HB_SEG_MORE;
+  if ((prior & 63u) != 0 || (more && (len & 63u) != 0)) {
+    atomicOr(status, HB_DEV_SEGMENT);
+    return 0u;
+  }
+  return more ? (len >> 6) : padded_blocks(len);
+}
 
 
 // ---------------------------------------------------------------------------
@@ -122,6 +148,7 @@ struct StaticSource {
     t.len = pf_len;
     t.nb = valid ? padded_blocks(pf_len) : 0u;
     t.alg = ALG;
+    t.seg = 0;
     prefetch();
     return true;
   }
@@ -133,12 +160,15 @@ struct StaticSource {
 // is tied to a warp long before the warp can start it: the pop, the
 // permutation load and the metadata loads are spread over the last three
 // items (hint), and `take` finishes whatever is still outstanding.
+template <bool SEG = false>
 struct DynamicSource {
   const uint8_t* packed;
   const uint64_t* offsets;
   const uint32_t* lengths;
   const uint8_t* algs;
   const uint32_t* perm;
+  const uint64_t* segs;
+  int* status;
   uint32_t* counter;
   uint32_t lane, nchunks;
   int stage;         // 0 nothing reserved, 1 popped, 2 perm loaded, 3 metadata loaded
@@ -146,6 +176,7 @@ struct DynamicSource {
   uint32_t msg;      // this lane's message in it (stage >= 2)
   uint64_t off;      // stage 3
   uint32_t len, alg;
+  uint64_t seg;      // stage 3, segments only
 
   __device__ DynamicSource(const KernelArgs& args, uint32_t lane_)
       : packed(args.packed),
@@ -153,6 +184,8 @@ struct DynamicSource {
         lengths(args.lengths),
         algs(args.algs),
         perm(args.perm),
+        segs(args.seg),
+        status(args.status),
         counter(args.chunk_counter),
         lane(lane_),
         stage(0) {
@@ -173,10 +206,12 @@ struct DynamicSource {
       off = 0;
       len = 0;
       alg = 0;
+      seg = 0;
       if (chunk < nchunks && msg != 0xFFFFFFFFu) {
         off = ldg_nc_u64(offsets + msg);
         len = ldg_nc_u32(lengths + msg);
         alg = __ldg(algs + msg);
+        if constexpr (SEG) seg = ldg_nc_u64(segs + msg);
       }
       stage = 3;
     }
@@ -198,7 +233,11 @@ struct DynamicSource {
     t.msg = msg;
     t.addr = reinterpret_cast<uint64_t>(packed) + off;
     t.len = len;
-    t.nb = valid ? padded_blocks(len) : 0u;
+    t.seg = seg;
+    if constexpr (SEG)
+      t.nb = valid ? segment_blocks(len, seg, status) : 0u;
+    else
+      t.nb = valid ? padded_blocks(len) : 0u;
     // Codes outside {0,1,2} were excluded by the bucketing step; the chunk's
     // algorithm is that of lane 0 (every chunk starts with a real message).
     t.alg = __shfl_sync(kFull, alg, 0);
@@ -236,23 +275,42 @@ __device__ __forceinline__ void note_message_done(const KernelArgs& a, uint64_t 
   }
 }
 
-template <int ALG>
+// Segment context of the block being consumed (SEG only): the bytes hashed
+// by earlier segments, whether more follow, and the staged chaining value.
+struct SegCtx {
+  uint64_t prior;
+  bool more;
+  uint32_t state;  // shared address of the staged chaining value
+};
+
+template <int ALG, bool SEG = false>
 __device__ __forceinline__ void process_block(uint32_t (&st)[8], uint32_t slot, uint32_t s,
                                               uint32_t len, uint32_t b, uint64_t msg,
                                               uint8_t* digests, const MulConsts& mc,
-                                              const KernelArgs& a) {
+                                              const KernelArgs& a, const SegCtx& sc = SegCtx{}) {
   constexpr bool BE = AlgTraits<ALG>::kBigEndian;
   const int64_t rem = (int64_t)len - 64 * (int64_t)b;  // message bytes from this block on
-  if (rem >= 0 && rem < 64) sts8(slot + s + (uint32_t)rem, 0x80u);
+  const bool more = SEG && sc.more;
+  if (!more && rem >= 0 && rem < 64) sts8(slot + s + (uint32_t)rem, 0x80u);
   uint32_t w[16];
   read_block_words<BE>(slot, s, w);
-  const bool final_block = rem <= 55;
+  const bool final_block = !more && rem <= 55;
   if (final_block) {
-    const uint32_t lo = len << 3, hi = len >> 29;  // bit length mod 2^64
+    // bit length of the whole message mod 2^64
+    const uint64_t bits = SEG ? (sc.prior + len) << 3 : (uint64_t)len << 3;
+    const uint32_t lo = (uint32_t)bits, hi = (uint32_t)(bits >> 32);
     w[14] = BE ? hi : lo;
     w[15] = BE ? lo : hi;
   }
-  if (b == 0) alg_init<ALG>(st);
+  if (b == 0) {
+    if (SEG && sc.prior != 0) {
+      const uint4 v0 = lds128(sc.state), v1 = lds128(sc.state + 16);
+      st[0] = v0.x; st[1] = v0.y; st[2] = v0.z; st[3] = v0.w;
+      st[4] = v1.x; st[5] = v1.y; st[6] = v1.z; st[7] = v1.w;
+    } else {
+      alg_init<ALG>(st);
+    }
+  }
   alg_compress<ALG>(st, w, mc);
   if (final_block) {
     uint32_t o[8];
@@ -261,6 +319,14 @@ __device__ __forceinline__ void process_block(uint32_t (&st)[8], uint32_t slot, 
     stg128_cs(dst, o[0], o[1], o[2], o[3]);
     stg128_cs(dst + 16, o[4], o[5], o[6], o[7]);
     note_message_done(a, msg);
+  } else if (more && rem == 64) {
+    // last block of a segment that is not the message's last: keep the
+    // chaining value (words past the algorithm's state are zero)
+    constexpr int kW = AlgTraits<ALG>::kStateWords;
+    uint8_t* dst = digests + msg * HB_SLOT_BYTES;
+    stg128_cs(dst, st[0], st[1], st[2], st[3]);
+    stg128_cs(dst + 16, kW > 4 ? st[4] : 0u, kW > 5 ? st[5] : 0u, kW > 6 ? st[6] : 0u,
+              kW > 7 ? st[7] : 0u);
   }
 }
 
@@ -270,15 +336,15 @@ __device__ __forceinline__ void process_block(uint32_t (&st)[8], uint32_t slot, 
 
 // Consumes the KB blocks of one stage for one lane (blocks past the
 // message's padded length are skipped).
-template <int ALG, int KB>
+template <int ALG, int KB, bool SEG = false>
 __device__ __forceinline__ void process_stage(uint32_t (&st)[8], uint32_t slot, uint32_t s,
                                               uint32_t len, uint32_t b0, uint64_t msg,
-                                              const KernelArgs& a) {
-  const uint32_t nb = padded_blocks(len);
+                                              const KernelArgs& a, const SegCtx& sc = SegCtx{}) {
+  const uint32_t nb = (SEG && sc.more) ? (len >> 6) : padded_blocks(len);
 #pragma unroll 1
   for (int j = 0; j < KB; ++j) {
     if (b0 + j >= nb) break;
-    process_block<ALG>(st, slot + 64 * j, s, len, b0 + j, msg, a.digests, a.mc, a);
+    process_block<ALG, SEG>(st, slot + 64 * j, s, len, b0 + j, msg, a.digests, a.mc, a, sc);
   }
 }
 
@@ -289,15 +355,17 @@ __device__ __forceinline__ void process_stage(uint32_t (&st)[8], uint32_t slot, 
 // distinct pages per instruction when the messages lie far apart.  Lanes then
 // read windows that other lanes copied, so the warp synchronises after the
 // copy wait and before a stage is reused.
-template <int STAGES, int KB, bool COOP, int ALG, bool MIXED, class Source>
+template <int STAGES, int KB, bool COOP, int ALG, bool MIXED, bool SEG, class Source>
 __device__ __forceinline__ void warp_pipeline(Source& src, uint8_t* wsm, const KernelArgs& a,
                                               uint32_t lane) {
-  using L = WarpSmem<STAGES, KB>;
+  using L = WarpSmem<STAGES, KB, SEG>;
   constexpr int kSlotBytes = Slot<KB>::kBytes;
   constexpr int kGranules = 4 * KB + 1;
   const uint32_t slots = smem_addr(wsm);
   const uint32_t items = slots + L::kSlots;
   const uint32_t table = items + L::kItems;
+  const uint32_t seg_items = table + L::kTable;      // SEG only
+  const uint32_t states = seg_items + L::kSegItems;  // SEG only
   const uint64_t safe_src = reinterpret_cast<uint64_t>(a.packed) & ~15ull;
 
   // Issuing side state (warp-uniform except the LaneTask fields).
@@ -320,6 +388,17 @@ __device__ __forceinline__ void warp_pipeline(Source& src, uint8_t* wsm, const K
     rec.z = t.len;
     rec.w = act ? ib : kNoBlock;
     sts128(items + (is * 32 + lane) * kItemBytes, rec);
+    if constexpr (SEG) {
+      sts128(seg_items + (is * 32 + lane) * kItemBytes,
+             make_uint4((uint32_t)t.seg, (uint32_t)(t.seg >> 32), 0u, 0u));
+      // a continued message's first item also stages its chaining value
+      if (act && ib == 0 && (t.seg & ~HB_SEG_MORE) != 0) {
+        const uint8_t* cv = a.digests + t.msg * HB_SLOT_BYTES;
+        const uint32_t dst = states + (is * 32 + lane) * HB_SLOT_BYTES;
+        cp_async16_zfill(dst, cv, 16u);
+        cp_async16_zfill(dst + 16, cv + 16, 16u);
+      }
+    }
     // This lane's window: first granule and message bytes from there on.
     uint64_t g0 = 0;
     int32_t avail = 0;
@@ -404,12 +483,20 @@ __device__ __forceinline__ void warp_pipeline(Source& src, uint8_t* wsm, const K
       const uint32_t slot = slots + (cs * 32 + lane) * kSlotBytes;
       if constexpr (MIXED) {
         const uint32_t alg = rec.y >> 28;
+        SegCtx sc{};
+        if constexpr (SEG) {
+          const uint4 r2 = lds128(seg_items + (cs * 32 + lane) * kItemBytes);
+          const uint64_t sg = (uint64_t)r2.x | ((uint64_t)r2.y << 32);
+          sc.prior = sg & ~HB_SEG_MORE;
+          sc.more = (sg & HB_SEG_MORE) != 0;
+          sc.state = states + (cs * 32 + lane) * HB_SLOT_BYTES;
+        }
         if (alg == HB_MD5)
-          process_stage<HB_MD5, KB>(st, slot, s, rec.z, rec.w, msg, a);
+          process_stage<HB_MD5, KB, SEG>(st, slot, s, rec.z, rec.w, msg, a, sc);
         else if (alg == HB_SHA1)
-          process_stage<HB_SHA1, KB>(st, slot, s, rec.z, rec.w, msg, a);
+          process_stage<HB_SHA1, KB, SEG>(st, slot, s, rec.z, rec.w, msg, a, sc);
         else
-          process_stage<HB_SM3, KB>(st, slot, s, rec.z, rec.w, msg, a);
+          process_stage<HB_SM3, KB, SEG>(st, slot, s, rec.z, rec.w, msg, a, sc);
       } else {
         process_stage<ALG, KB>(st, slot, s, rec.z, rec.w, msg, a);
       }
