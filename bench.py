@@ -520,6 +520,12 @@ def run_ours(args, dist):
         "clocks": clk,
     }
 
+    if mixed:
+        # the ragged launch against the plain kernels at equal bytes
+        pg, pl = plain_equal_bytes_gbs(api, torch, batch.lengths, batch.algs, packed)
+        line["plain_equal_bytes_gbs"] = pg
+        line["plain_mean_length"] = pl
+        line["ragged_vs_plain_equal_bytes"] = per_alg["mixed"]["GB/s"] / pg
     if not args.no_e2e:
         line["e2e"] = e2e_measure(args, batch, mixed, api, torch, dist)
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
@@ -563,30 +569,41 @@ def e2e_measure(args, batch, mixed, api, torch, dist):
             "api": "hash_batch_host (pinned host buffers)"}
 
 
-def plain_equal_bytes_ms(api, torch, lengths, algs, reps=3):
-    """Time of the plain (fixed-length) kernels at equal bytes: per algorithm
-    one batch of messages of the set's mean length holding that algorithm's
-    share of the bytes."""
+def plain_equal_bytes_gbs(api, torch, lengths, algs, pool, reps=3, max_msgs=1 << 18):
+    """Rate of the plain (fixed-length) kernels at equal bytes: per algorithm
+    a batch of messages of the set's mean length, timed with its best launch
+    shape; the set's bytes of each algorithm at that algorithm's rate.  The
+    batch holds the algorithm's bytes of the set or max_msgs messages,
+    whichever is fewer (enough to fill the GPU: the rate no longer depends on
+    the batch size), read from `pool` (device random bytes) at spread
+    16-byte aligned offsets.  Returns (GB/s, mean length)."""
     L = max(1, int(round(float(lengths.astype(np.float64).mean()))))
-    tot = 0.0
+    span = max(1, (pool.numel() - L) // 16)
+    t_total = 0.0
+    b_total = 0
     for a in (0, 1, 2):
         nbytes = int(lengths[algs == a].astype(np.int64).sum())
-        n = max(1, nbytes // L)
-        b = workloads.fixed(n, L, 900 + a)
-        p, o, l, _ = api.to_device(b)
-        out = torch.empty((n, 32), dtype=torch.uint8, device="cuda")
+        if nbytes == 0:
+            continue
+        n = max(1, min(nbytes // L, max_msgs))
+        i = torch.arange(n, dtype=torch.int64, device=pool.device)
+        o = ((i * 2654435761) % span) * 16
+        l = torch.full((n,), L, dtype=torch.int32, device=pool.device)
+        out = torch.empty((n, 32), dtype=torch.uint8, device=pool.device)
         best = float("inf")
         for sh in range(len(api.shapes())):
-            fn = lambda: api.hash_batch(a, p, o, l, out=out, shape=sh)
+            fn = lambda: api.hash_batch(a, pool, o, l, out=out, shape=sh)
             fn()
             torch.cuda.synchronize()
             for _ in range(reps):
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record(); fn(); e1.record(); e1.synchronize()
                 best = min(best, e0.elapsed_time(e1))
-        tot += best
-        del p, o, l, out
-    return tot, L
+        rate = n * L / (best * 1e-3)               # bytes per second
+        t_total += nbytes / rate
+        b_total += nbytes
+        del o, l, out
+    return b_total / t_total / 1e9, L
 
 
 def run_serve(args, dist):
@@ -620,8 +637,10 @@ def run_serve(args, dist):
     pool_bytes = args.pool_mib << 20
     pool_host = workloads.fixed(1, pool_bytes, shard_seed(4, dist.rank)).packed
     pool = torch.from_numpy(np.ascontiguousarray(pool_host)).cuda()
-    srv = serve.Server(pool, budget=args.budget_gib << 30, slots=args.slots,
-                       shape=args.serve_shape, warps_per_sm=args.serve_warps)
+    srv = serve.Server(pool, budget=args.budget_gib << 30, rounds=args.rounds,
+                       segment_bytes=(3 * args.segment_kib << 10, 2 * args.segment_kib << 10,
+                                      args.segment_kib << 10), shape=args.serve_shape,
+                       warps_per_sm=args.serve_warps)
     probe = serve.make_requests(args.requests, 1.0, shard_seed(4, dist.rank), pool_bytes)
     mean_req = float(np.mean([r.nbytes for r in probe]))
     all_lengths = np.concatenate([r.lengths for r in probe])
@@ -631,16 +650,22 @@ def run_serve(args, dist):
         for k, load in enumerate(args.loads):
             rate = load * ref_gbs * 1e9 / mean_req
             reqs = serve.make_requests(args.requests, rate, shard_seed(4, dist.rank) + 17 * k, pool_bytes)
+            r0, s0 = srv.rounds_launched, srv.segments
             srv.run(reqs)
             st = serve.latency_stats(reqs)
             st.update({"offered_load": load, "offered_gbs": rate * mean_req / 1e9,
-                       "requests": len(reqs)})
+                       "requests": len(reqs), "rounds": srv.rounds_launched - r0,
+                       "segments": srv.segments - s0})
             points.append(st)
+    budget_used = {"ring_and_rounds": serve.device_bytes(srv.book.capacity, srv.book.req_capacity,
+                                                         len(srv.slots), srv.max_msgs),
+                   "staging": srv.staging_per_round * len(srv.slots)}
     srv.close()
-    plain_ms, plain_L = plain_equal_bytes_ms(api, torch, all_lengths, all_algs)
-    plain_gbs = float(all_lengths.astype(np.int64).sum()) / (plain_ms * 1e-3) / 1e9
+    plain_gbs, plain_L = plain_equal_bytes_gbs(api, torch, all_lengths, all_algs, pool)
     top = max(points, key=lambda p: p["offered_load"])
-    job_gbs = job_rate(dist, top["bytes"], top["span_s"]) / 1e9
+    # sustained rate: requests finishing between the 10th and 90th percentile
+    # of finishing times at the highest offered load (every rank's servers)
+    job_gbs = dist.sum(top["steady_gbs"])
     line = {
         "metric": METRIC, "value": job_gbs, "unit": "GB/s", "n_gpus": dist.world,
         "steps": len(points), "warmup": 3, "ms_per_step": None, "higher_is_better": True,
@@ -649,11 +674,14 @@ def run_serve(args, dist):
                 "lengths log-uniform in [16 B, 1 MiB], random algorithm; bytes from a %d MiB "
                 "random pool (numpy PCG64)" % args.pool_mib,
         "config": {"workload": "serving: continuous batching under a %d GiB device budget, "
-                               "%d slots, %d requests per load point" % (args.budget_gib, args.slots, args.requests),
+                               "%d streaming rounds, %d KiB segments, %d requests per load point"
+                               % (args.budget_gib, args.rounds, args.segment_kib, args.requests),
                    "reference_ragged_gbs": ref_gbs, "mean_request_bytes": mean_req,
                    "parallelism": "dp%d: independent servers, no collective" % dist.world},
         "serve": points,
         "served_vs_plain_equal_bytes": top["gbs"] / plain_gbs,
+        "steady_vs_plain_equal_bytes": top["steady_gbs"] / plain_gbs,
+        "device_budget_bytes": budget_used,
         "plain_equal_bytes_gbs": plain_gbs, "plain_mean_length": plain_L,
         "p50_ms_at_top_load": top["p50_ms"], "p99_ms_at_top_load": top["p99_ms"],
         "clocks": clocks.summary(),
@@ -698,13 +726,15 @@ def main(argv=None):
     p.add_argument("--steps", type=int, default=2000)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5"])
-    p.add_argument("--requests", type=int, default=2000, help="requests per load point (c5)")
+    p.add_argument("--requests", type=int, default=20000, help="requests per load point (c5)")
     p.add_argument("--loads", type=float, nargs="+", default=[0.1, 0.3, 0.5, 0.7, 0.9, 1.1],
                    help="offered loads as fractions of the ragged path's throughput (c5)")
     p.add_argument("--budget-gib", type=int, default=8, help="device-memory budget (c5)")
-    p.add_argument("--slots", type=int, default=16, help="batches in flight (c5)")
-    p.add_argument("--serve-shape", type=int, default=18, help="launch shape of the serving plans (c5)")
-    p.add_argument("--serve-warps", type=int, default=4, help="warps per SM per batch (c5)")
+    p.add_argument("--rounds", type=int, default=8, help="streaming rounds in flight (c5)")
+    p.add_argument("--segment-kib", type=int, default=64,
+                   help="SM3 segment of long messages; SHA-1 2x, MD5 3x (c5)")
+    p.add_argument("--serve-shape", type=int, default=11, help="launch shape of the rounds (c5)")
+    p.add_argument("--serve-warps", type=int, default=8, help="resident warps per SM per round (c5)")
     p.add_argument("--pool-mib", type=int, default=2048, help="random-byte pool for requests (c5)")
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--e2e-steps", type=int, default=10)

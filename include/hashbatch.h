@@ -76,7 +76,9 @@ extern "C" {
 /* Device status bits (hash_device_status). */
 #define HB_DEV_TIMEOUT 0x1        /* a kernel's bounded wait expired         */
 #define HB_DEV_BOUNDS 0x2         /* hash_batch_check_bounds found a message
-                                     outside [0, packed_len)                 */
+                                     outside [0, packed_len), or a streaming
+                                     round met a request index outside its
+                                     table                                   */
 #define HB_DEV_SEGMENT 0x4        /* a segment that is not the last was not a
                                      whole number of 64-byte blocks, or its
                                      prior byte count was not (message skipped) */
@@ -138,14 +140,17 @@ int hash_batch_mixed(const uint8_t *algs, const uint8_t *packed_bytes,
  *     bytes), exactly as hash_batch_mixed would for the whole message.
  *   A segment that breaks a multiple-of-64 rule is skipped and sets
  *   HB_DEV_SEGMENT in the device status (hash_device_status).
+ *   slot_index (optional, device uint32): message i uses slot
+ *   slots_inout + 32 * slot_index[i] instead of slot i, so a message can keep
+ *   one slot while its position changes from call to call.  NULL = slot i.
  * Consecutive segments of one message must be ordered (same stream, or an
  * event between the calls).  Limits and return codes as hash_batch_mixed.
  */
 #define HB_SEG_MORE (1ull << 63)
 int hash_batch_segments(const uint8_t *algs, const uint8_t *packed_bytes,
                         const uint64_t *offsets, const uint32_t *lengths,
-                        const uint64_t *seg, uint64_t n, uint8_t *slots_inout,
-                        void *stream);
+                        const uint64_t *seg, const uint32_t *slot_index, uint64_t n,
+                        uint8_t *slots_inout, void *stream);
 
 /*
  * hash_batch_mixed_noalloc -- hash_batch_mixed for callers that cannot
@@ -208,9 +213,10 @@ int hash_batch_mixed_noalloc(const uint8_t *algs, const uint8_t *packed_bytes,
  *                      (cudaHostAlloc); other memory returns HB_ERR_ARG.
  * hash_plan_set_segments -- the plan's batches are segments as in
  *                      hash_batch_segments: seg_dev[i] (device uint64) describes
- *                      message i of a batch, and the digest slots carry
- *                      chaining values between segments.  NULL = whole
- *                      messages.  Before the first capture; HB_ERR_ARG after.
+ *                      message i of a batch, slot_index_dev (optional) maps
+ *                      it to its slot, and the slots carry chaining values
+ *                      between segments.  seg_dev NULL = whole messages.
+ *                      Before the first capture; HB_ERR_ARG after.
  * hash_plan_destroy -- synchronises the device and frees the plan.
  * A plan's scratch is used by one batch at a time: order the runs and
  * replays of one plan (same stream, or events); different plans overlap.
@@ -242,8 +248,75 @@ int hash_plan_replay(hb_plan *plan, uint64_t n, void *stream);
 int hash_plan_configure(hb_plan *plan, int shape_index, int warps_per_sm);
 int hash_plan_set_completion(hb_plan *plan, const uint32_t *msg_req_dev, uint32_t *remaining_dev,
                              uint32_t *done_flags);
-int hash_plan_set_segments(hb_plan *plan, const uint64_t *seg_dev);
+int hash_plan_set_segments(hb_plan *plan, const uint64_t *seg_dev,
+                           const uint32_t *slot_index_dev);
 int hash_plan_destroy(hb_plan *plan);
+
+/*
+ * Streaming rounds -- the device side of a serving loop whose messages arrive
+ * over time and may be long.  The caller keeps a ring of message entries in
+ * device memory (hb_ring, all arrays caller-owned); a round, launched on a
+ * stream, does on the device:
+ *   1. claim: every entry of the window [head, tail) (counters taken modulo
+ *      capacity) in state HB_RING_READY, oldest first, becomes HB_RING_BUSY
+ *      while its next segment fits the round's limits (max_msgs segments,
+ *      staging_bytes of staging, each segment starting 16-byte aligned).
+ *      A segment is the next min(len - prior, segment_bytes[alg]) bytes;
+ *   2. copy: the segments' bytes go from src + prior to the staging area;
+ *   3. hash: the ragged path over the segments (hash_batch_segments with
+ *      slot_index = the entry), so each entry's 32-byte slot carries its
+ *      chaining value between rounds and finally its digest;
+ *   4. advance: prior grows by the segment; a finished message's entry
+ *      becomes HB_RING_FREE and request req[k]'s counter req_remaining drops
+ *      by one -- the lane that drops it to zero stores 1 to req_done[req]
+ *      (page-locked host memory mapped for the device, after the digests);
+ *      an unfinished entry becomes HB_RING_READY again.
+ * So only the segments of a round occupy staging memory: a long message
+ * holds segment_bytes of it at a time however long its serial chain runs.
+ * Rounds on different streams may run at the same time over one ring: the
+ * claim is atomic, so a message is in at most one round at a time.
+ * The caller fills an entry (src, len, req, alg, prior = 0, its request's
+ * counter) before it sets the entry READY, orders those writes before the
+ * round that covers the entry (same stream or an event), and reuses an entry
+ * only when it is FREE and its digest has been read.
+ *
+ * hash_round_create -- allocates the round's batch arrays and scratch
+ *   (cudaMalloc) and captures its launch sequence as a CUDA graph.
+ *   segment_bytes[3]: per algorithm code, multiples of 64 (a cheaper
+ *   algorithm can take longer segments for the same chain time);
+ *   max_msgs < 2^23; staging must be
+ *   16-byte aligned.  Sets up every kernel first: call it outside any capture.
+ * hash_round_launch -- runs one round for the window [head, tail)
+ *   (tail - head <= capacity) on `stream`.  Do not launch a round again until
+ *   its previous launch has finished.
+ * hash_round_report -- segments and staged bytes the last finished launch
+ *   claimed (call after that launch completed).
+ * hash_round_destroy -- synchronises the device and frees the round.
+ * The paper has no counterpart; it is the serving loop's device side.
+ */
+#define HB_RING_FREE 0u
+#define HB_RING_READY 1u
+#define HB_RING_BUSY 2u
+typedef struct hb_ring {
+  uint64_t capacity;        /* entries, a power of two                       */
+  const uint64_t *src;      /* device address of each message's first byte  */
+  uint64_t *prior;          /* bytes of each message hashed so far           */
+  const uint32_t *len;      /* message length                                */
+  const uint32_t *req;      /* request of each message (< req_capacity)      */
+  const uint8_t *alg;       /* algorithm code 0, 1 or 2                      */
+  uint32_t *state;          /* HB_RING_FREE / READY / BUSY                   */
+  uint8_t *slots;           /* capacity * 32 bytes: chaining value, digest   */
+  uint32_t *req_remaining;  /* device: messages of the request not finished  */
+  uint32_t *req_done;       /* mapped host memory: 1 once the request is done */
+  uint64_t req_capacity;
+} hb_ring;
+typedef struct hb_round hb_round;
+int hash_round_create(const hb_ring *ring, uint32_t max_msgs, uint8_t *staging,
+                      uint64_t staging_bytes, const uint32_t *segment_bytes,
+                      int shape_index, int warps_per_sm, hb_round **round_out);
+int hash_round_launch(hb_round *round, uint64_t head, uint64_t tail, void *stream);
+int hash_round_report(hb_round *round, uint64_t *segments, uint64_t *bytes);
+int hash_round_destroy(hb_round *round);
 
 /*
  * hash_batch_check_bounds -- checks on the device that every message lies in

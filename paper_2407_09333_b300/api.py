@@ -37,7 +37,7 @@ _SIGNATURES = {
     "hash_batch": (_c_int, [_c_int, _vp, _vp, _vp, _c_u64, _vp, _vp]),
     "hash_batch_mixed": (_c_int, [_vp, _vp, _vp, _vp, _c_u64, _vp, _vp]),
     "hash_batch_mixed_noalloc": (_c_int, [_vp, _vp, _vp, _vp, _c_u64, _vp, _vp]),
-    "hash_batch_segments": (_c_int, [_vp, _vp, _vp, _vp, _vp, _c_u64, _vp, _vp]),
+    "hash_batch_segments": (_c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _c_u64, _vp, _vp]),
     "hash_batch_check_bounds": (_c_int, [_vp, _vp, _c_u64, _c_u64, _vp, _vp]),
     "hash_batch_host": (_c_int, [_c_int, _vp, _vp, _c_u64, _vp, _vp, _c_u64, _vp, _vp]),
     "hash_device_status": (_c_int, [_vp, ctypes.POINTER(_c_int)]),
@@ -63,9 +63,23 @@ _SIGNATURES = {
     "hash_plan_destroy": (_c_int, [_vp]),
     "hash_plan_configure": (_c_int, [_vp, _c_int, _c_int]),
     "hash_plan_set_completion": (_c_int, [_vp, _vp, _vp, _vp]),
-    "hash_plan_set_segments": (_c_int, [_vp, _vp]),
+    "hash_plan_set_segments": (_c_int, [_vp, _vp, _vp]),
     "hash_gather": (_c_int, [_vp, _c_u32, _vp]),
+    "hash_round_create": (_c_int, [_vp, _c_u32, _vp, _c_u64, ctypes.POINTER(_c_u32), _c_int,
+                                   _c_int, ctypes.POINTER(_vp)]),
+    "hash_round_launch": (_c_int, [_vp, _c_u64, _c_u64, _vp]),
+    "hash_round_report": (_c_int, [_vp, ctypes.POINTER(_c_u64), ctypes.POINTER(_c_u64)]),
+    "hash_round_destroy": (_c_int, [_vp]),
 }
+
+RING_FREE, RING_READY, RING_BUSY = 0, 1, 2
+
+
+class HbRing(ctypes.Structure):
+    """struct hb_ring of include/hashbatch.h."""
+    _fields_ = [("capacity", _c_u64), ("src", _vp), ("prior", _vp), ("len", _vp),
+                ("req", _vp), ("alg", _vp), ("state", _vp), ("slots", _vp),
+                ("req_remaining", _vp), ("req_done", _vp), ("req_capacity", _c_u64)]
 
 _lib = None
 
@@ -189,19 +203,28 @@ def seg_words(prior, more):
     return (prior | np.where(more, np.uint64(SEG_MORE), np.uint64(0))).view(np.int64)
 
 
-def hash_batch_segments(algs, packed, offsets, lengths, seg, slots, stream=None):
-    """One call over message segments; `slots` (n, 32) uint8 carries the
-    chaining values between calls and receives the digests of messages whose
-    last segment this is (see hash_batch_segments in the C header)."""
+def hash_batch_segments(algs, packed, offsets, lengths, seg, slots, slot_index=None,
+                        stream=None):
+    """One call over message segments; `slots` (uint8, 32 bytes per slot)
+    carries the chaining values between calls and receives the digests of
+    messages whose last segment this is; message i uses slot slot_index[i]
+    (CUDA int32 tensor) or, without it, slot i (see hash_batch_segments in
+    the C header)."""
     n = int(offsets.numel())
     if lengths.numel() != n or algs.numel() != n or seg.numel() != n:
         raise ValueError("algs, offsets, lengths and seg must have one entry per message")
-    if slots.dtype.itemsize != 1 or slots.numel() < n * SLOT_BYTES or not slots.is_contiguous():
-        raise ValueError("slots must be a contiguous uint8 tensor of n*32 bytes")
+    if slot_index is None and slots.numel() < n * SLOT_BYTES:
+        raise ValueError("slots must hold n*32 bytes")
+    if slot_index is not None and slot_index.numel() != n:
+        raise ValueError("slot_index must have one entry per message")
+    if slots.dtype.itemsize != 1 or not slots.is_contiguous():
+        raise ValueError("slots must be a contiguous uint8 tensor")
     rc = lib().hash_batch_segments(
         _dev_ptr(algs, 1, "algs"), _dev_ptr(packed, 1, "packed"),
         _dev_ptr(offsets, 8, "offsets"), _dev_ptr(lengths, 4, "lengths"),
-        _dev_ptr(seg, 8, "seg"), n, _dev_ptr(slots, 1, "slots"), _stream_handle(stream))
+        _dev_ptr(seg, 8, "seg"),
+        None if slot_index is None else _dev_ptr(slot_index, 4, "slot_index"), n,
+        _dev_ptr(slots, 1, "slots"), _stream_handle(stream))
     _check(rc, "hash_batch_segments")
     return slots
 
@@ -326,12 +349,15 @@ class Plan:
                "hash_plan_set_completion")
         self._flags = (msg_req, remaining, done_flags)
 
-    def set_segments(self, seg):
+    def set_segments(self, seg, slot_index=None):
         """Batches of this plan are message segments described by the CUDA
-        int64 tensor `seg` (see seg_words); before the first capture."""
-        _check(lib().hash_plan_set_segments(self._h, _dev_ptr(seg, 8, "seg")),
-               "hash_plan_set_segments")
-        self._seg = seg
+        int64 tensor `seg` (see seg_words), message i using slot
+        slot_index[i] if given; before the first capture."""
+        _check(lib().hash_plan_set_segments(
+            self._h, _dev_ptr(seg, 8, "seg"),
+            None if slot_index is None else _dev_ptr(slot_index, 4, "slot_index")),
+            "hash_plan_set_segments")
+        self._seg = (seg, slot_index)
 
     def capture(self, algs, packed, offsets, lengths, out, grid=0):
         _check(lib().hash_plan_capture(self._h, _dev_ptr(algs, 1, "algs"),
@@ -346,6 +372,64 @@ class Plan:
     def close(self):
         if self._h:
             lib().hash_plan_destroy(self._h)
+            self._h = None
+            self._keep = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Round:
+    """A streaming round over a message ring (hash_round_* in the C header).
+
+    `ring` is a dict of tensors: src/prior (CUDA int64), len/req/state (CUDA
+    int32), alg (CUDA uint8), slots (CUDA uint8, capacity x 32),
+    req_remaining (CUDA int32) and req_done (pinned CPU int32); `staging` a
+    CUDA uint8 tensor (16-byte aligned) of which the round uses
+    staging_bytes from the start.
+    """
+
+    def __init__(self, ring: dict, max_msgs: int, staging, staging_bytes: int,
+                 segment_bytes, shape: int = -1, warps_per_sm: int = 0):
+        """segment_bytes: one size for every algorithm, or (MD5, SHA-1, SM3)."""
+        cap = int(ring["state"].numel())
+        if ring["req_done"].is_cuda or not ring["req_done"].is_pinned():
+            raise ValueError("req_done must be pinned host memory")
+        if int(staging_bytes) > staging.numel():
+            raise ValueError("staging_bytes exceeds the staging tensor")
+        self._ring = HbRing(
+            cap, _dev_ptr(ring["src"], 8, "src"), _dev_ptr(ring["prior"], 8, "prior"),
+            _dev_ptr(ring["len"], 4, "len"), _dev_ptr(ring["req"], 4, "req"),
+            _dev_ptr(ring["alg"], 1, "alg"), _dev_ptr(ring["state"], 4, "state"),
+            _dev_ptr(ring["slots"], 1, "slots"), _dev_ptr(ring["req_remaining"], 4, "req_remaining"),
+            ctypes.c_void_p(ring["req_done"].data_ptr()), int(ring["req_remaining"].numel()))
+        if isinstance(segment_bytes, int):
+            segment_bytes = (segment_bytes,) * 3
+        seg = (_c_u32 * 3)(*[int(x) for x in segment_bytes])
+        h = ctypes.c_void_p()
+        _check(lib().hash_round_create(ctypes.byref(self._ring), int(max_msgs),
+                                       _dev_ptr(staging, 1, "staging"), int(staging_bytes),
+                                       seg, int(shape), int(warps_per_sm),
+                                       ctypes.byref(h)), "hash_round_create")
+        self._h = h
+        self._keep = (ring, staging)
+
+    def launch(self, head: int, tail: int, stream=None):
+        _check(lib().hash_round_launch(self._h, int(head), int(tail), _stream_handle(stream)),
+               "hash_round_launch")
+
+    def report(self) -> tuple[int, int]:
+        seg, nb = _c_u64(0), _c_u64(0)
+        _check(lib().hash_round_report(self._h, ctypes.byref(seg), ctypes.byref(nb)),
+               "hash_round_report")
+        return int(seg.value), int(nb.value)
+
+    def close(self):
+        if self._h:
+            lib().hash_round_destroy(self._h)
             self._h = None
             self._keep = None
 

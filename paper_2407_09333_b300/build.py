@@ -16,7 +16,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libhashbatch.so")
-SOURCES = ["hb_kernels.cu", "hb_capi.cu", "hb_noalloc.cu"]
+SOURCES = ["hb_kernels.cu", "hb_capi.cu", "hb_noalloc.cu", "hb_stream.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

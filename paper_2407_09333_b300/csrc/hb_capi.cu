@@ -155,10 +155,12 @@ int launch_mixed(Ctx* c, int shape, int grid, const uint8_t* algs, const uint8_t
                  const uint64_t* offsets, const uint32_t* lengths, uint64_t n, uint8_t* digests,
                  void* ws, const int* abort_flag, cudaStream_t s, const uint64_t* n_dev = nullptr,
                  const hb::BucketCfg* buckets = nullptr, int warps_per_sm = -1,
-                 const Completion* comp = nullptr, const uint64_t* seg = nullptr) {
+                 const Completion* comp = nullptr, const uint64_t* seg = nullptr,
+                 const uint32_t* slot_index = nullptr) {
   if (shape < 0 || shape >= hb::num_shapes()) return HB_ERR_ARG;
-  MixedArgs m;
+  MixedArgs m{};
   m.cfg = buckets ? *buckets : c->buckets;
+  m.slot_index = slot_index;
   m.algs = algs;
   m.lengths = lengths;
   m.n = n;
@@ -173,6 +175,7 @@ int launch_mixed(Ctx* c, int shape, int grid, const uint8_t* algs, const uint8_t
   if (rc) return rc;
   KernelArgs a{};
   a.seg = seg;
+  a.slot_index = seg ? slot_index : nullptr;
   a.packed = packed;
   a.offsets = offsets;
   a.lengths = lengths;
@@ -279,8 +282,9 @@ namespace {
 // hash_batch_mixed(_shape) and hash_batch_segments: the ragged path on the
 // per-device scratch.
 int mixed_on_ctx(const uint8_t* algs, const uint8_t* packed_bytes, const uint64_t* offsets,
-                 const uint32_t* lengths, const uint64_t* seg, uint64_t n, uint8_t* digests_out,
-                 int shape_index, int grid_blocks, void* stream) {
+                 const uint32_t* lengths, const uint64_t* seg, const uint32_t* slot_index,
+                 uint64_t n, uint8_t* digests_out, int shape_index, int grid_blocks,
+                 void* stream) {
   if (n == 0) return HB_OK;
   if (n >= kMaxMixedN) return HB_ERR_TOO_LARGE;
   int rc = check_common(packed_bytes, offsets, lengths, n, digests_out);
@@ -293,7 +297,8 @@ int mixed_on_ctx(const uint8_t* algs, const uint8_t* packed_bytes, const uint64_
   if ((rc = reserve_ws(c, n))) return rc;
   if (c->ws_used && cudaStreamWaitEvent(s, c->ws_event, 0) != cudaSuccess) return cuda_fail(cudaGetLastError());
   rc = launch_mixed(c, shape_index, grid_blocks, algs, packed_bytes, offsets, lengths, n,
-                    digests_out, c->ws.p, nullptr, s, nullptr, nullptr, -1, nullptr, seg);
+                    digests_out, c->ws.p, nullptr, s, nullptr, nullptr, -1, nullptr, seg,
+                    slot_index);
   if (rc) return rc;
   if (cudaEventRecord(c->ws_event, s) != cudaSuccess) return cuda_fail(cudaGetLastError());
   c->ws_used = true;
@@ -302,21 +307,30 @@ int mixed_on_ctx(const uint8_t* algs, const uint8_t* packed_bytes, const uint64_
 
 }  // namespace
 
+namespace hb {
+int* current_status_word() {
+  Ctx* c = nullptr;
+  return get_ctx(&c) == HB_OK ? c->status : nullptr;
+}
+}  // namespace hb
+
 extern "C" {
 
 int hash_batch_mixed_shape(const uint8_t* algs, const uint8_t* packed_bytes,
                            const uint64_t* offsets, const uint32_t* lengths, uint64_t n,
                            uint8_t* digests_out, int shape_index, int grid_blocks, void* stream) {
-  return mixed_on_ctx(algs, packed_bytes, offsets, lengths, nullptr, n, digests_out, shape_index,
-                      grid_blocks, stream);
+  return mixed_on_ctx(algs, packed_bytes, offsets, lengths, nullptr, nullptr, n, digests_out,
+                      shape_index, grid_blocks, stream);
 }
 
 int hash_batch_segments(const uint8_t* algs, const uint8_t* packed_bytes,
                         const uint64_t* offsets, const uint32_t* lengths, const uint64_t* seg,
-                        uint64_t n, uint8_t* slots_inout, void* stream) {
+                        const uint32_t* slot_index, uint64_t n, uint8_t* slots_inout,
+                        void* stream) {
   if (n == 0) return HB_OK;
   if (!seg) return HB_ERR_NULL;
-  return mixed_on_ctx(algs, packed_bytes, offsets, lengths, seg, n, slots_inout, -1, 0, stream);
+  return mixed_on_ctx(algs, packed_bytes, offsets, lengths, seg, slot_index, n, slots_inout, -1,
+                      0, stream);
 }
 
 int hash_batch_mixed(const uint8_t* algs, const uint8_t* packed_bytes, const uint64_t* offsets,
@@ -561,6 +575,7 @@ struct hb_plan {
   hb::BucketCfg buckets = hb::kDefaultBuckets;
   Completion completion;
   const uint64_t* seg = nullptr;  // segment descriptors (hash_plan_set_segments)
+  const uint32_t* slot_index = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
 };
@@ -604,10 +619,12 @@ int hash_plan_set_completion(hb_plan* p, const uint32_t* msg_req_dev, uint32_t* 
   return HB_OK;
 }
 
-int hash_plan_set_segments(hb_plan* p, const uint64_t* seg_dev) {
+int hash_plan_set_segments(hb_plan* p, const uint64_t* seg_dev, const uint32_t* slot_index_dev) {
   if (!p) return HB_ERR_NULL;
   if (p->exec) return HB_ERR_ARG;  // before capturing
+  if (slot_index_dev && !seg_dev) return HB_ERR_NULL;
   p->seg = seg_dev;
+  p->slot_index = slot_index_dev;
   return HB_OK;
 }
 
@@ -660,7 +677,7 @@ int hash_plan_run(hb_plan* p, const uint8_t* algs, const uint8_t* packed_bytes,
   if (c->device != p->device) return HB_ERR_ARG;
   return launch_mixed(c, p->shape, grid_blocks, algs, packed_bytes, offsets, lengths, n,
                       digests_out, p->ws, nullptr, static_cast<cudaStream_t>(stream), nullptr,
-                      &p->buckets, p->warps_per_sm, &p->completion, p->seg);
+                      &p->buckets, p->warps_per_sm, &p->completion, p->seg, p->slot_index);
 }
 
 int hash_plan_capture(hb_plan* p, const uint8_t* algs, const uint8_t* packed_bytes,
@@ -692,7 +709,7 @@ int hash_plan_capture(hb_plan* p, const uint8_t* algs, const uint8_t* packed_byt
     // kernels read the actual count from n_dev when the graph runs.
     rc = launch_mixed(c, p->shape, grid_blocks, algs, packed_bytes, offsets, lengths, p->max_n,
                       digests_out, p->ws, nullptr, s, p->n_dev, &p->buckets, p->warps_per_sm,
-                      &p->completion, p->seg);
+                      &p->completion, p->seg, p->slot_index);
     cudaGraph_t g = nullptr;
     const cudaError_t e2 = cudaStreamEndCapture(s, &g);
     if (rc == HB_OK && e2 != cudaSuccess) rc = cuda_fail(e2);

@@ -73,7 +73,7 @@ __global__ void hb_hist_kernel(MixedArgs m) {
       atomicAdd(&counts[cost_group(m.lengths[i], alg, m.cfg)], 1u);
     } else {
       // Unknown code: the slot stays all zero and the message is not hashed.
-      uint8_t* dst = m.digests + i * HB_SLOT_BYTES;
+      uint8_t* dst = m.digests + (m.slot_index ? (uint64_t)m.slot_index[i] : i) * HB_SLOT_BYTES;
       stg128_cs(dst, 0, 0, 0, 0);
       stg128_cs(dst + 16, 0, 0, 0, 0);
     }
@@ -280,7 +280,10 @@ __global__ void hb_selftest_wait_kernel(uint64_t limit_ns, int* status) {
   X(17, 4, 4, 2, true)   \
   X(18, 1, 3, 4, true)   \
   X(19, 1, 2, 4, true)   \
-  X(20, 1, 4, 2, true)
+  X(20, 1, 4, 2, true)   \
+  X(21, 1, 2, 2, true)   \
+  X(22, 1, 3, 2, true)   \
+  X(23, 2, 2, 2, true)
 
 struct ShapeDesc {
   int warps, stages, kb;

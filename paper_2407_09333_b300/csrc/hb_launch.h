@@ -50,6 +50,8 @@ struct KernelArgs {
   // earlier calls (a multiple of 64) | HB_SEG_MORE when more segments follow.
   // Between segments the message's 32-byte slot carries its chaining value.
   const uint64_t* seg;
+  // Optional with segments: message i's slot is slot_index[i] instead of i.
+  const uint32_t* slot_index;
 };
 
 // Ragged-path bucketing: groups are (cost bucket, algorithm) pairs ordered
@@ -102,6 +104,7 @@ struct MixedArgs {
   uint8_t* digests;
   MixedWorkspace* ws;
   uint32_t* perm;
+  const uint32_t* slot_index;  // optional (segments): slot of message i
 };
 
 int num_shapes();
@@ -126,5 +129,10 @@ using HbCopy = hb_copy;
 cudaError_t launch_gather(const HbCopy* copies, uint32_t count, int grid, cudaStream_t stream);
 // Writes the message count a captured ragged graph reads (one tiny kernel).
 cudaError_t launch_set_count(uint64_t* n_dev, uint64_t n, cudaStream_t stream);
+
+// The current device's status word (HB_DEV_* bits, read by
+// hash_device_status); creates the device context on first use.  nullptr
+// when that fails.
+int* current_status_word();
 
 }  // namespace hb

@@ -96,7 +96,7 @@ extern "C" int hash_batch_mixed_noalloc(const uint8_t* algs, const uint8_t* pack
   hb::MixedWorkspace* ws = reinterpret_cast<hb::MixedWorkspace*>(s->scratch + kStatusBytes);
   uint32_t* perm = reinterpret_cast<uint32_t*>(s->scratch + kStatusBytes + sizeof(hb::MixedWorkspace));
 
-  hb::MixedArgs m;
+  hb::MixedArgs m{};
   m.cfg = hb::kDefaultBuckets;
   m.algs = algs;
   m.lengths = lengths;

@@ -81,6 +81,7 @@ struct LaneTask {
   uint32_t nb;     // padded block count, 0 for an idle lane
   uint32_t alg;    // algorithm code
   uint64_t seg;    // segments only: prior bytes | HB_SEG_MORE
+  uint32_t slot;   // segments only: the message's 32-byte slot
 };
 
 // Blocks of a segment: whole blocks only when more segments follow, else
@@ -149,6 +150,7 @@ struct StaticSource {
     t.nb = valid ? padded_blocks(pf_len) : 0u;
     t.alg = ALG;
     t.seg = 0;
+    t.slot = 0;
     prefetch();
     return true;
   }
@@ -168,6 +170,7 @@ struct DynamicSource {
   const uint8_t* algs;
   const uint32_t* perm;
   const uint64_t* segs;
+  const uint32_t* slot_index;
   int* status;
   uint32_t* counter;
   uint32_t lane, nchunks;
@@ -177,6 +180,7 @@ struct DynamicSource {
   uint64_t off;      // stage 3
   uint32_t len, alg;
   uint64_t seg;      // stage 3, segments only
+  uint32_t slot;     // stage 3, segments only
 
   __device__ DynamicSource(const KernelArgs& args, uint32_t lane_)
       : packed(args.packed),
@@ -185,6 +189,7 @@ struct DynamicSource {
         algs(args.algs),
         perm(args.perm),
         segs(args.seg),
+        slot_index(args.slot_index),
         status(args.status),
         counter(args.chunk_counter),
         lane(lane_),
@@ -207,11 +212,15 @@ struct DynamicSource {
       len = 0;
       alg = 0;
       seg = 0;
+      slot = msg;
       if (chunk < nchunks && msg != 0xFFFFFFFFu) {
         off = ldg_nc_u64(offsets + msg);
         len = ldg_nc_u32(lengths + msg);
         alg = __ldg(algs + msg);
-        if constexpr (SEG) seg = ldg_nc_u64(segs + msg);
+        if constexpr (SEG) {
+          seg = ldg_nc_u64(segs + msg);
+          if (slot_index) slot = ldg_nc_u32(slot_index + msg);
+        }
       }
       stage = 3;
     }
@@ -234,6 +243,7 @@ struct DynamicSource {
     t.addr = reinterpret_cast<uint64_t>(packed) + off;
     t.len = len;
     t.seg = seg;
+    t.slot = slot;
     if constexpr (SEG)
       t.nb = valid ? segment_blocks(len, seg, status) : 0u;
     else
@@ -281,6 +291,7 @@ struct SegCtx {
   uint64_t prior;
   bool more;
   uint32_t state;  // shared address of the staged chaining value
+  uint32_t slot;   // the message's 32-byte slot
 };
 
 template <int ALG, bool SEG = false>
@@ -315,7 +326,7 @@ __device__ __forceinline__ void process_block(uint32_t (&st)[8], uint32_t slot, 
   if (final_block) {
     uint32_t o[8];
     alg_digest_words<ALG>(st, o);
-    uint8_t* dst = digests + msg * HB_SLOT_BYTES;
+    uint8_t* dst = digests + (SEG ? (uint64_t)sc.slot : msg) * HB_SLOT_BYTES;
     stg128_cs(dst, o[0], o[1], o[2], o[3]);
     stg128_cs(dst + 16, o[4], o[5], o[6], o[7]);
     note_message_done(a, msg);
@@ -323,7 +334,7 @@ __device__ __forceinline__ void process_block(uint32_t (&st)[8], uint32_t slot, 
     // last block of a segment that is not the message's last: keep the
     // chaining value (words past the algorithm's state are zero)
     constexpr int kW = AlgTraits<ALG>::kStateWords;
-    uint8_t* dst = digests + msg * HB_SLOT_BYTES;
+    uint8_t* dst = digests + (uint64_t)sc.slot * HB_SLOT_BYTES;
     stg128_cs(dst, st[0], st[1], st[2], st[3]);
     stg128_cs(dst + 16, kW > 4 ? st[4] : 0u, kW > 5 ? st[5] : 0u, kW > 6 ? st[6] : 0u,
               kW > 7 ? st[7] : 0u);
@@ -390,10 +401,10 @@ __device__ __forceinline__ void warp_pipeline(Source& src, uint8_t* wsm, const K
     sts128(items + (is * 32 + lane) * kItemBytes, rec);
     if constexpr (SEG) {
       sts128(seg_items + (is * 32 + lane) * kItemBytes,
-             make_uint4((uint32_t)t.seg, (uint32_t)(t.seg >> 32), 0u, 0u));
+             make_uint4((uint32_t)t.seg, (uint32_t)(t.seg >> 32), t.slot, 0u));
       // a continued message's first item also stages its chaining value
       if (act && ib == 0 && (t.seg & ~HB_SEG_MORE) != 0) {
-        const uint8_t* cv = a.digests + t.msg * HB_SLOT_BYTES;
+        const uint8_t* cv = a.digests + (uint64_t)t.slot * HB_SLOT_BYTES;
         const uint32_t dst = states + (is * 32 + lane) * HB_SLOT_BYTES;
         cp_async16_zfill(dst, cv, 16u);
         cp_async16_zfill(dst + 16, cv + 16, 16u);
@@ -490,6 +501,7 @@ __device__ __forceinline__ void warp_pipeline(Source& src, uint8_t* wsm, const K
           sc.prior = sg & ~HB_SEG_MORE;
           sc.more = (sg & HB_SEG_MORE) != 0;
           sc.state = states + (cs * 32 + lane) * HB_SLOT_BYTES;
+          sc.slot = r2.z;
         }
         if (alg == HB_MD5)
           process_stage<HB_MD5, KB, SEG>(st, slot, s, rec.z, rec.w, msg, a, sc);

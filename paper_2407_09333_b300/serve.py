@@ -1,32 +1,33 @@
-"""Continuous-batching hash server on one GPU.
+"""Continuous-batching hash server on one GPU, streaming long messages.
 
-Requests (one algorithm each, 1..4096 messages) arrive over time.  The
-server keeps every admitted request's bytes in a device arena whose size is
-the memory budget; a request is admitted (first come, first served) as soon
-as its bytes fit, and waits otherwise.  Up to `slots` batches are on the GPU
-at once, each slot with its own CUDA stream, its own ragged-path plan
-(private bucketing scratch) and a CUDA graph captured once over the slot's
-fixed metadata and digest buffers.  Whenever a slot is free, every admitted
-request that is not yet on the GPU is packed into one batch:
+Requests (one algorithm each, 1..4096 messages of up to 1 MiB) arrive over
+time.  A message is a serial chain of compressions (the Merkle-Damgard
+iteration of RFC 1321 Sec. 3.4, FIPS 180-4 Sec. 6, GB/T 32905 Sec. 5.3):
+a 1 MiB SM3 message takes tens of milliseconds however many SMs are free.  A
+server that held each admitted request's bytes in device memory until its
+last message finished would tie its memory budget to those chains; this one
+streams every message through the device in segments (`segment_bytes`, per
+algorithm) instead, keeping only each message's 32-byte chaining value between them
+("state kept on device").
 
-  1. the batch's metadata (message offsets into the arena, lengths,
-     algorithm codes) and the request copy records go to the device in one
-     host-to-device copy per section;
-  2. one gather kernel moves the requests' bytes into their arena places;
-  3. the slot's graph hashes the batch (longest-first chunks, persistent);
-  4. the digest slots come back to pinned host memory; an event marks the end.
+Device side (one budget, fixed at start):
+  * a ring of message entries (source address, length, progress, request,
+    algorithm, state, 32-byte slot) and per-request counters;
+  * `rounds` streaming rounds (hash_round_* in the C-ABI), each with its own
+    CUDA stream, staging area and captured graph.  A round claims the oldest
+    ready messages, copies their next segments into its staging area, hashes
+    them with the ragged path and advances them; a message whose last
+    segment is hashed leaves its digest in its slot, and the last message of
+    a request raises the request's done flag in host memory.
+Rounds run concurrently on their streams, so the copies and the hashing of
+different rounds overlap, and a message's next segment goes to whichever
+round is free next.
 
-A request is finished as soon as the kernel raises its done flag (host
-memory the device writes after the request's last message): its latency
-(completion minus arrival) is recorded and its arena space is released,
-which lets waiting requests in, while longer requests of the same batch are
-still running.  A slot is free again when its batch's event has completed;
-requests that arrive meanwhile join the next batch on another slot and run
-concurrently with the earlier ones.
-
-The arena bookkeeping (`Arena`) and the admission/batching policy
-(`Scheduler`) are plain Python and testable without a GPU; `Server` adds the
-device work.
+Host side (this module, plain Python): admission in arrival order while the
+ring and the request table have room (`RingBook`), one batch of metadata
+copies per loop for the newly admitted requests, round launches, and the
+done flags.  Digests stay on the device; `keep_digests` copies each request's
+digests out when it completes (for tests).
 """
 from __future__ import annotations
 
@@ -36,53 +37,64 @@ import time
 
 import numpy as np
 
-ALIGN = 256
+RING_ENTRY_BYTES = 8 + 8 + 4 + 4 + 1 + 4 + 32      # src, prior, len, req, alg, state, slot
+ROUND_ENTRY_BYTES = 1 + 8 + 4 + 8 + 4 + 24 + 4     # batch arrays, copy record, permutation
 
 
-class Arena:
-    """First-fit allocator over [0, capacity) in ALIGN-byte units."""
+class RingBook:
+    """Bookkeeping of the message ring and the request table.
 
-    def __init__(self, capacity: int, align: int = ALIGN):
-        self.capacity = int(capacity) // align * align
-        self.align = align
-        self.free = [(0, self.capacity)]  # sorted, coalesced (start, size)
-        self.used = 0
-        self.peak = 0
+    Messages take consecutive ring positions (counters modulo `capacity`);
+    requests take consecutive request slots (modulo `req_capacity`).  A
+    request is admitted when both have room; positions are reused once every
+    earlier request has finished (the head only moves past finished
+    requests, in admission order).
+    """
 
-    def round(self, size: int) -> int:
-        return max(self.align, (int(size) + self.align - 1) // self.align * self.align)
+    def __init__(self, capacity: int, req_capacity: int):
+        if capacity & (capacity - 1) or req_capacity & (req_capacity - 1):
+            raise ValueError("capacities must be powers of two")
+        self.capacity = capacity
+        self.req_capacity = req_capacity
+        self.head = self.tail = 0          # message counters
+        self.req_head = self.req_tail = 0  # request counters
+        self.open = collections.deque()    # [req counter, first, m, finished]
+        self.by_req = {}
 
-    def alloc(self, size: int):
-        """(start, rounded size), or None when no free range is large enough."""
-        size = self.round(size)
-        for i, (st, sz) in enumerate(self.free):
-            if sz >= size:
-                if sz == size:
-                    del self.free[i]
-                else:
-                    self.free[i] = (st + size, sz - size)
-                self.used += size
-                self.peak = max(self.peak, self.used)
-                return st, size
-        return None
+    def fits(self, m: int) -> bool:
+        return (self.tail + m - self.head <= self.capacity and
+                self.req_tail + 1 - self.req_head <= self.req_capacity)
 
-    def release(self, start: int, size: int):
-        lo, hi = 0, len(self.free)
-        while lo < hi:
-            mid = (lo + hi) // 2
-            if self.free[mid][0] < start:
-                lo = mid + 1
-            else:
-                hi = mid
-        self.free.insert(lo, (start, size))
-        # coalesce with the neighbours
-        if lo + 1 < len(self.free) and self.free[lo][0] + self.free[lo][1] == self.free[lo + 1][0]:
-            self.free[lo] = (self.free[lo][0], self.free[lo][1] + self.free[lo + 1][1])
-            del self.free[lo + 1]
-        if lo > 0 and self.free[lo - 1][0] + self.free[lo - 1][1] == self.free[lo][0]:
-            self.free[lo - 1] = (self.free[lo - 1][0], self.free[lo - 1][1] + self.free[lo][1])
-            del self.free[lo]
-        self.used -= size
+    def admit(self, m: int) -> tuple[int, int]:
+        """(request counter, first message counter) of a request of m messages."""
+        if not self.fits(m):
+            raise ValueError("no room")
+        rc, first = self.req_tail, self.tail
+        self.req_tail += 1
+        self.tail += m
+        ent = [rc, first, m, False]
+        self.open.append(ent)
+        self.by_req[rc] = ent
+        return rc, first
+
+    def finish(self, rc: int):
+        self.by_req.pop(rc)[3] = True
+        while self.open and self.open[0][3]:
+            _, _, m, _ = self.open.popleft()
+            self.head += m
+            self.req_head += 1
+
+    def spans(self, first: int, count: int, capacity: int | None = None) -> list:
+        """[(ring position, offset into the run, length)] of counters
+        [first, first + count), split where the ring wraps."""
+        cap = capacity or self.capacity
+        out, done = [], 0
+        while done < count:
+            pos = (first + done) % cap
+            take = min(count - done, cap - pos)
+            out.append((pos, done, take))
+            done += take
+        return out
 
 
 @dataclasses.dataclass
@@ -91,266 +103,240 @@ class Req:
     arrival: float               # seconds since the start of the run
     alg: int
     lengths: np.ndarray          # uint32 per message
-    segments: list               # [(pool offset, bytes)] whose concatenation is the payload
+    src: np.ndarray              # uint64 pool offset of each message
     nbytes: int = 0
-    local_offsets: np.ndarray | None = None
-    arena: tuple | None = None   # (start, rounded size) once admitted
+    counter: int = -1            # request counter once admitted
+    first: int = -1              # first message counter once admitted
     admitted: float = -1.0
     done: float = -1.0
     digests: np.ndarray | None = None
 
     def __post_init__(self):
         self.lengths = np.asarray(self.lengths, dtype=np.uint32)
+        self.src = np.asarray(self.src, dtype=np.uint64)
         self.nbytes = int(self.lengths.astype(np.uint64).sum())
-        offs = np.zeros(self.lengths.shape[0], dtype=np.uint64)
-        if self.lengths.shape[0]:
-            offs[1:] = np.cumsum(self.lengths.astype(np.uint64))[:-1]
-        self.local_offsets = offs
 
 
-class Scheduler:
-    """Admission and batching policy, independent of the device.
-
-    `arrive` queues a request; `admit` moves queued requests (in arrival
-    order) into the arena while they fit -- a request larger than the whole
-    budget is rejected; `next_batch` hands every admitted, not yet launched
-    request to a free slot, up to max_msgs messages and max_reqs requests;
-    `finish` releases a batch's arena space.
-    """
-
-    def __init__(self, budget: int, max_msgs: int, max_reqs: int):
-        self.arena = Arena(budget)
-        self.max_msgs = max_msgs
-        self.max_reqs = max_reqs
-        self.waiting = collections.deque()
-        self.ready = collections.deque()
-        self.rejected = []
-
-    def arrive(self, req: Req):
-        self.waiting.append(req)
-
-    def admit(self, now: float) -> int:
-        n = 0
-        while self.waiting:
-            req = self.waiting[0]
-            if self.arena.round(req.nbytes) > self.arena.capacity or \
-                    req.lengths.shape[0] > self.max_msgs:
-                self.waiting.popleft()
-                self.rejected.append(req)
-                continue
-            got = self.arena.alloc(req.nbytes)
-            if got is None:
-                break  # first come, first served: wait for space
-            self.waiting.popleft()
-            req.arena = got
-            req.admitted = now
-            self.ready.append(req)
-            n += 1
-        return n
-
-    def next_batch(self) -> list:
-        batch, msgs = [], 0
-        while self.ready and len(batch) < self.max_reqs:
-            m = int(self.ready[0].lengths.shape[0])
-            if batch and msgs + m > self.max_msgs:
-                break
-            batch.append(self.ready.popleft())
-            msgs += m
-        return batch
-
-    def finish(self, batch: list):
-        for req in batch:
-            self.arena.release(*req.arena)
-            req.arena = None
+def device_bytes(capacity: int, req_capacity: int, rounds: int, max_msgs: int) -> int:
+    """Device memory of everything but the staging areas."""
+    ws = 6272 + 4 * (max_msgs + 31 * 768)
+    return capacity * RING_ENTRY_BYTES + req_capacity * 4 + rounds * (
+        max_msgs * ROUND_ENTRY_BYTES + ws + 256)
 
 
-class _Slot:
-    def __init__(self, server, max_msgs: int, max_reqs: int):
+class _RoundSlot:
+    def __init__(self, server, staging, nbytes):
         torch, api = server.torch, server.api
-        dev = server.device
-        self.stream = torch.cuda.Stream(device=dev)
-        self.plan = api.Plan(max_msgs, shape=server.shape, warps_per_sm=server.warps_per_sm)
-        self.d_algs = torch.zeros(max_msgs, dtype=torch.uint8, device=dev)
-        self.d_offsets = torch.zeros(max_msgs, dtype=torch.int64, device=dev)
-        self.d_lengths = torch.zeros(max_msgs, dtype=torch.int32, device=dev)
-        self.d_digests = torch.zeros((max_msgs, 32), dtype=torch.uint8, device=dev)
-        self.d_copies = torch.zeros((max_reqs * 4, 3), dtype=torch.int64, device=dev)
-        self.h_algs = torch.zeros(max_msgs, dtype=torch.uint8).pin_memory()
-        self.h_offsets = torch.zeros(max_msgs, dtype=torch.int64).pin_memory()
-        self.h_lengths = torch.zeros(max_msgs, dtype=torch.int32).pin_memory()
-        self.h_copies = torch.zeros((max_reqs * 4, 3), dtype=torch.int64).pin_memory()
-        self.h_digests = torch.zeros((max_msgs, 32), dtype=torch.uint8).pin_memory()
-        # per-request completion: message -> request, messages left, done flags
-        self.d_msg_req = torch.zeros(max_msgs, dtype=torch.int32, device=dev)
-        self.d_remaining = torch.zeros(max_reqs, dtype=torch.int32, device=dev)
-        self.h_msg_req = torch.zeros(max_msgs, dtype=torch.int32).pin_memory()
-        self.h_remaining = torch.zeros(max_reqs, dtype=torch.int32).pin_memory()
-        self.h_done = torch.zeros(max_reqs, dtype=torch.int32).pin_memory()
-        self.done_np = self.h_done.numpy()
-        self.plan.set_completion(self.d_msg_req, self.d_remaining, self.h_done)
-        self.plan.capture(self.d_algs, server.arena_dev, self.d_offsets, self.d_lengths,
-                          self.d_digests, grid=server.grid)
+        self.stream = torch.cuda.Stream(device=server.device)
+        self.round = api.Round(server.ring, server.max_msgs, staging, nbytes,
+                               server.segment_bytes, server.shape, server.warps_per_sm)
         self.event = torch.cuda.Event()
-        self.batch = None
-        self.open = None   # indices of the batch's requests not yet finished
-        self.nmsgs = 0
+        self.busy = False
+        self.again = False   # its last launch claimed work: launch it again
 
 
 class Server:
-    """The device side: arena tensor, payload pool, slots."""
+    """Streaming server: ring, rounds and the host loop."""
 
-    def __init__(self, pool, budget: int = 8 << 30, slots: int = 16, max_msgs: int = 1 << 17,
-                 max_reqs: int = 512, grid: int = 0, shape: int = 18, warps_per_sm: int = 4,
-                 min_batch_bytes: int = 0, max_wait_ms: float = 0.0, device="cuda"):
+    # Segments per algorithm (MD5, SHA-1, SM3): about the same chain time each
+    # (an SM3 block costs about three MD5 blocks and two SHA-1 blocks).
+    DEFAULT_SEGMENTS = (192 << 10, 128 << 10, 64 << 10)
+
+    def __init__(self, pool, budget: int = 8 << 30, rounds: int = 8,
+                 segment_bytes=DEFAULT_SEGMENTS, max_msgs: int = 1 << 17,
+                 capacity: int = 1 << 21, req_capacity: int = 1 << 14,
+                 shape: int = 11, warps_per_sm: int = 8, device="cuda"):
         import torch
         from . import api
         self.torch, self.api, self.device = torch, api, device
         self.pool = pool                                     # device uint8 tensor
         self.pool_addr = pool.data_ptr()
-        self.sched = Scheduler(budget, max_msgs, max_reqs)
-        self.arena_dev = torch.empty(self.sched.arena.capacity, dtype=torch.uint8, device=device)
-        self.arena_addr = self.arena_dev.data_ptr()
-        # One-warp blocks: a warp that runs out of chunks leaves at once and
-        # frees its SM resources for other batches, while warps holding long
-        # serial chains keep running.
-        self.grid = grid
+        self.max_msgs = max_msgs
         self.shape = shape
         self.warps_per_sm = warps_per_sm
-        # Batch formation: a free slot takes the admitted requests at once
-        # when nothing else is running, when they hold min_batch_bytes, or
-        # when the oldest of them has waited max_wait_ms; otherwise it waits
-        # for more (every batch lasts at least its longest serial chain, so
-        # larger batches carry more bytes per slot-time).
-        self.min_batch_bytes = min_batch_bytes
-        self.max_wait_s = max_wait_ms * 1e-3
-        self.slots = [_Slot(self, max_msgs, max_reqs) for _ in range(slots)]
-        self.batches = 0
-        self.batched_reqs = 0
+        if isinstance(segment_bytes, int):
+            segment_bytes = (segment_bytes,) * 3
+        self.segment_bytes = tuple(int(x) for x in segment_bytes)
+        fixed = device_bytes(capacity, req_capacity, rounds, max_msgs)
+        staging_total = (budget - fixed) // rounds // 256 * 256 * rounds
+        if staging_total < rounds * max(self.segment_bytes):
+            raise ValueError("budget too small for the ring and the rounds")
+        self.budget = budget
+        self.staging_per_round = staging_total // rounds
+        self.book = RingBook(capacity, req_capacity)
+        dev = device
+        self.ring = {
+            "src": torch.zeros(capacity, dtype=torch.int64, device=dev),
+            "prior": torch.zeros(capacity, dtype=torch.int64, device=dev),
+            "len": torch.zeros(capacity, dtype=torch.int32, device=dev),
+            "req": torch.zeros(capacity, dtype=torch.int32, device=dev),
+            "alg": torch.zeros(capacity, dtype=torch.uint8, device=dev),
+            "state": torch.zeros(capacity, dtype=torch.int32, device=dev),
+            "slots": torch.zeros((capacity, 32), dtype=torch.uint8, device=dev),
+            "req_remaining": torch.zeros(req_capacity, dtype=torch.int32, device=dev),
+            "req_done": torch.zeros(req_capacity, dtype=torch.int32).pin_memory(),
+        }
+        self.done_np = self.ring["req_done"].numpy()
+        self.staging = torch.empty(staging_total, dtype=torch.uint8, device=dev)
+        self.slots = [_RoundSlot(self, self.staging[i * self.staging_per_round:],
+                                 self.staging_per_round) for i in range(rounds)]
+        # host staging of admissions (pinned; reused once the last admission's
+        # copies have finished)
+        self.h_src = torch.zeros(capacity, dtype=torch.int64).pin_memory()
+        self.h_len = torch.zeros(capacity, dtype=torch.int32).pin_memory()
+        self.h_req = torch.zeros(capacity, dtype=torch.int32).pin_memory()
+        self.h_alg = torch.zeros(capacity, dtype=torch.uint8).pin_memory()
+        self.h_rem = torch.zeros(req_capacity, dtype=torch.int32).pin_memory()
+        # constant sources for progress (0) and state (READY): admission only
+        # copies, so it never waits for an SM while the rounds fill the GPU
+        self.h_zero = torch.zeros(capacity, dtype=torch.int64).pin_memory()
+        self.h_ready = torch.full((capacity,), api.RING_READY, dtype=torch.int32).pin_memory()
+        self.fin_np = np.zeros(req_capacity, dtype=bool)     # finished, by request slot
+        self.admit_stream = torch.cuda.Stream(device=dev)
+        self.admit_event = torch.cuda.Event()
+        self.admit_event.record(self.admit_stream)
+        self.rounds_launched = 0
+        self.segments = 0
+        self.loop_iters = 0
+        self.admit_s = 0.0
 
-    def _launch(self, slot: _Slot, batch: list):
-        torch, api = self.torch, self.api
-        n = 0
-        c = 0
-        slot.done_np[:len(batch)] = 0
-        for j, req in enumerate(batch):
-            m = int(req.lengths.shape[0])
-            base = req.arena[0]
-            slot.h_offsets.numpy()[n:n + m] = (req.local_offsets + np.uint64(base)).view(np.int64)
-            slot.h_lengths.numpy()[n:n + m] = req.lengths.view(np.int32)
-            slot.h_algs.numpy()[n:n + m] = req.alg
-            slot.h_msg_req.numpy()[n:n + m] = j
-            slot.h_remaining.numpy()[j] = m
-            dst = self.arena_addr + base
-            for off, ln in req.segments:
-                slot.h_copies.numpy()[c] = (self.pool_addr + off, dst, ln)
-                dst += ln
-                c += 1
-            n += m
-        with torch.cuda.stream(slot.stream):
-            slot.d_offsets[:n].copy_(slot.h_offsets[:n], non_blocking=True)
-            slot.d_lengths[:n].copy_(slot.h_lengths[:n], non_blocking=True)
-            slot.d_algs[:n].copy_(slot.h_algs[:n], non_blocking=True)
-            slot.d_copies[:c].copy_(slot.h_copies[:c], non_blocking=True)
-            slot.d_msg_req[:n].copy_(slot.h_msg_req[:n], non_blocking=True)
-            slot.d_remaining[:len(batch)].copy_(slot.h_remaining[:len(batch)], non_blocking=True)
-            api.gather(slot.d_copies, c, stream=slot.stream)
-            slot.plan.replay(n, stream=slot.stream)
-            slot.h_digests[:n].copy_(slot.d_digests[:n], non_blocking=True)
-            slot.event.record(slot.stream)
-        slot.batch = batch
-        slot.open = list(range(len(batch)))
-        slot.nmsgs = n
-        self.batches += 1
-        self.batched_reqs += len(batch)
+    # -- admission -------------------------------------------------------
+    def _write_admissions(self, reqs: list):
+        """Ring entries and request counters of newly admitted requests (one
+        contiguous run of message and request counters)."""
+        torch, book, ring = self.torch, self.book, self.ring
+        self.admit_event.synchronize()          # host staging is free again
+        first = reqs[0].first
+        total = sum(int(r.lengths.shape[0]) for r in reqs)
+        src = np.concatenate([r.src for r in reqs]).view(np.int64) + self.pool_addr
+        ln = np.concatenate([r.lengths for r in reqs]).view(np.int32)
+        rq = np.concatenate([np.full(r.lengths.shape[0], r.counter % book.req_capacity, np.int32)
+                             for r in reqs])
+        al = np.concatenate([np.full(r.lengths.shape[0], r.alg, np.uint8) for r in reqs])
+        rem = np.array([r.lengths.shape[0] for r in reqs], dtype=np.int32)
+        for r in reqs:
+            q = r.counter % book.req_capacity
+            self.done_np[q] = 0
+            self.fin_np[q] = False
+        hs, hl, hr, ha = (self.h_src.numpy(), self.h_len.numpy(), self.h_req.numpy(),
+                          self.h_alg.numpy())
+        hs[:total], hl[:total], hr[:total], ha[:total] = src, ln, rq, al
+        self.h_rem.numpy()[:rem.shape[0]] = rem
+        with torch.cuda.stream(self.admit_stream):
+            spans = book.spans(first, total)
+            for pos, off, cnt in spans:
+                ring["src"][pos:pos + cnt].copy_(self.h_src[off:off + cnt], non_blocking=True)
+                ring["len"][pos:pos + cnt].copy_(self.h_len[off:off + cnt], non_blocking=True)
+                ring["req"][pos:pos + cnt].copy_(self.h_req[off:off + cnt], non_blocking=True)
+                ring["alg"][pos:pos + cnt].copy_(self.h_alg[off:off + cnt], non_blocking=True)
+                ring["prior"][pos:pos + cnt].copy_(self.h_zero[:cnt], non_blocking=True)
+            for pos, off, cnt in book.spans(reqs[0].counter, len(reqs), book.req_capacity):
+                ring["req_remaining"][pos:pos + cnt].copy_(self.h_rem[off:off + cnt],
+                                                           non_blocking=True)
+            for pos, off, cnt in spans:                  # ready last
+                ring["state"][pos:pos + cnt].copy_(self.h_ready[:cnt], non_blocking=True)
+            self.admit_event.record(self.admit_stream)
 
-    def _batch_due(self, now: float) -> bool:
-        if self.min_batch_bytes <= 0 and self.max_wait_s <= 0:
-            return True
-        if all(slot.batch is None for slot in self.slots):
-            return True
-        ready = self.sched.ready
-        if now - ready[0].admitted >= self.max_wait_s > 0:
-            return True
-        return sum(r.nbytes for r in ready) >= self.min_batch_bytes > 0
-
-    def _poll_requests(self, slot: _Slot, now: float) -> int:
-        """Finish the requests whose done flag the kernel has raised: their
-        arena space is free again even though the batch is still running."""
-        count = 0
-        still = []
-        for j in slot.open:
-            if slot.done_np[j]:
-                req = slot.batch[j]
-                req.done = now
-                self.sched.arena.release(*req.arena)
-                req.arena = None
-                count += 1
-            else:
-                still.append(j)
-        slot.open = still
-        return count
-
-    def _complete(self, slot: _Slot, now: float, keep_digests: bool) -> int:
-        count = self._poll_requests(slot, now)
-        for j in slot.open:   # flags read before the event completed
-            req = slot.batch[j]
-            if req.done < 0:
-                req.done = now
-            self.sched.arena.release(*req.arena)
-            req.arena = None
-            count += 1
-        if keep_digests:
-            n = 0
-            digests = slot.h_digests.numpy()
-            for req in slot.batch:
-                m = int(req.lengths.shape[0])
-                req.digests = digests[n:n + m].copy()
-                n += m
-        slot.batch = None
-        slot.open = None
-        return count
-
+    # -- the loop ----------------------------------------------------------
     def run(self, requests: list, keep_digests: bool = False, time_limit_s: float = 600.0):
         """Serve `requests` (sorted by arrival) in real time; returns them,
-        finished (done >= 0) or rejected."""
-        torch = self.torch
+        finished (done >= 0) or rejected (done < 0)."""
+        torch, book = self.torch, self.book
         torch.cuda.synchronize()
-        sched = self.sched
         nreq = len(requests)
-        finished = 0
+        pending = collections.deque()
+        inflight = {}                 # request slot -> Req
+        finished = rejected = 0
+        wake_all = False
         i = 0
         t0 = time.perf_counter()
-        while finished + len(sched.rejected) < nreq:
+        while finished + rejected < nreq:
             now = time.perf_counter() - t0
             if now > time_limit_s:
                 raise RuntimeError("serving run exceeded %.0f s" % time_limit_s)
             while i < nreq and requests[i].arrival <= now:
-                sched.arrive(requests[i])
+                pending.append(requests[i])
                 i += 1
-            for slot in self.slots:
-                if slot.batch is None:
+            # admission, first come first served
+            new = []
+            while pending:
+                r = pending[0]
+                m = int(r.lengths.shape[0])
+                if m > book.capacity:
+                    pending.popleft()
+                    rejected += 1
                     continue
-                if slot.event.query():
-                    finished += self._complete(slot, time.perf_counter() - t0, keep_digests)
-                elif slot.open:
-                    finished += self._poll_requests(slot, time.perf_counter() - t0)
-            sched.admit(time.perf_counter() - t0)
-            if sched.ready and self._batch_due(time.perf_counter() - t0):
-                for slot in self.slots:
-                    if slot.batch is None and sched.ready:
-                        self._launch(slot, sched.next_batch())
-        # every request is finished; let the last batches end (their digests
-        # come back with the batch)
-        for slot in self.slots:
-            if slot.batch is not None:
-                slot.event.synchronize()
-                self._complete(slot, time.perf_counter() - t0, keep_digests)
+                if not book.fits(m):
+                    break
+                pending.popleft()
+                r.counter, r.first = book.admit(m)
+                r.admitted = now
+                inflight[r.counter % book.req_capacity] = r
+                new.append(r)
+            self.loop_iters += 1
+            if new:
+                ta = time.perf_counter()
+                self._write_admissions(new)
+                self.admit_s += time.perf_counter() - ta
+                wake_all = True
+            # rounds: a round that comes back with work is launched again (its
+            # unfinished messages are ready again); all idle rounds are woken
+            # by an admission or by a round that filled its batch (more ready
+            # work is likely waiting)
+            for s in self.slots:
+                if s.busy and s.event.query():
+                    s.busy = False
+                    seg, nb = s.round.report()
+                    self.segments += seg
+                    s.again = seg > 0
+                    if seg >= self.max_msgs or nb + max(self.segment_bytes) > self.staging_per_round:
+                        wake_all = True
+            if inflight:
+                for s in self.slots:
+                    if not s.busy and (s.again or wake_all):
+                        s.stream.wait_event(self.admit_event)
+                        s.round.launch(book.head, book.tail, stream=s.stream)
+                        s.event.record(s.stream)
+                        s.busy = True
+                        s.again = False
+                        self.rounds_launched += 1
+            wake_all = False
+            # completions: done flags of the open requests, by request slot
+            lo, hi, R = book.req_head, book.req_tail, book.req_capacity
+            if hi > lo:
+                a, b = lo % R, (hi - 1) % R + 1
+                parts = [np.arange(a, b)] if a < b else [np.arange(a, R), np.arange(0, b)]
+                hit = []
+                for idx in parts:
+                    sel = idx[(self.done_np[idx] != 0) & ~self.fin_np[idx]]
+                    if sel.size:
+                        hit.append(sel)
+                if hit:
+                    t = time.perf_counter() - t0
+                    for q in np.concatenate(hit).tolist():
+                        r = inflight.pop(q)
+                        r.done = t
+                        self.fin_np[q] = True
+                        if keep_digests:
+                            r.digests = self._digests(r)
+                        book.finish(r.counter)
+                        finished += 1
+        for s in self.slots:
+            if s.busy:
+                s.event.synchronize()
+                s.busy = False
         torch.cuda.synchronize()
         return requests
 
+    def _digests(self, r: Req) -> np.ndarray:
+        m = int(r.lengths.shape[0])
+        parts = [self.ring["slots"][pos:pos + cnt].cpu().numpy()
+                 for pos, _, cnt in self.book.spans(r.first, m)]
+        return np.concatenate(parts) if parts else np.zeros((0, 32), np.uint8)
+
     def close(self):
-        for slot in self.slots:
-            slot.plan.close()
+        for s in self.slots:
+            s.round.close()
 
 
 # ---------------------------------------------------------------------------
@@ -358,21 +344,17 @@ class Server:
 
 def make_requests(count: int, rate_per_s: float, seed: int, pool_bytes: int,
                   max_msgs: int = 4096, min_len: int = 16, max_len: int = 1 << 20) -> list:
-    """Poisson request stream; each request's payload is a (wrapped) range of
-    the random-byte pool, chosen by its seed, starting 16-byte aligned."""
+    """Poisson request stream; each message's bytes are a range of the
+    random-byte pool starting at a 16-byte aligned offset chosen from the
+    request's seed."""
     from . import workloads
     out = []
     for k, r in enumerate(workloads.serve_requests(count, rate_per_s, seed, max_msgs, min_len, max_len)):
-        req = Req(k, r.arrival_s, r.alg, r.lengths, [])
         rng = np.random.Generator(np.random.PCG64(r.seed))
-        left = req.nbytes
-        off = int(rng.integers(0, max(pool_bytes - 16, 1))) // 16 * 16
-        while left > 0:
-            take = min(left, pool_bytes - off)
-            req.segments.append((off, take))
-            left -= take
-            off = 0
-        out.append(req)
+        lens = r.lengths.astype(np.uint64)
+        hi = (np.uint64(pool_bytes) - lens) // np.uint64(16)
+        src = (rng.random(lens.shape[0]) * (hi.astype(np.float64) + 1)).astype(np.uint64) * np.uint64(16)
+        out.append(Req(k, r.arrival_s, r.alg, r.lengths, src))
     return out
 
 
@@ -384,8 +366,16 @@ def latency_stats(requests: list) -> dict:
     nbytes = sum(r.nbytes for r in done)
     t_end = max(r.done for r in done)
     t_start = min(r.arrival for r in done)
+    # steady state: bytes of the requests finishing between the 10th and the
+    # 90th percentile of finishing times, over that interval (leaves out the
+    # ramp-up and the drain after the last arrival)
+    fin = np.array([r.done for r in done])
+    nb = np.array([r.nbytes for r in done], dtype=np.float64)
+    t10, t90 = np.percentile(fin, [10, 90])
+    mid = (fin > t10) & (fin <= t90)
+    steady = float(nb[mid].sum() / (t90 - t10) / 1e9) if t90 > t10 else 0.0
     return {"completed": len(done), "rejected": len(requests) - len(done),
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "mean_ms": float(lat.mean()), "max_ms": float(lat.max()),
-            "gbs": nbytes / max(t_end - t_start, 1e-9) / 1e9,
+            "gbs": nbytes / max(t_end - t_start, 1e-9) / 1e9, "steady_gbs": steady,
             "bytes": nbytes, "span_s": t_end - t_start}

@@ -43,7 +43,7 @@ def _rounds(batch, rng, max_pieces):
     return pieces, max(len(p) for p in pieces)
 
 
-def _run_segmented(hb, batch, pieces, nrounds, rng, call):
+def _run_segmented(hb, batch, pieces, nrounds, rng, call, indexed=False):
     """Feeds round r's piece of every unfinished message; returns the final
     slots in message order (host numpy)."""
     n = batch.n
@@ -62,13 +62,17 @@ def _run_segmented(hb, batch, pieces, nrounds, rng, call):
         more = np.array([len(pieces[i]) > r + 1 for i in active])
         offs = batch.offsets[active] + prior[active]
         idx = torch.from_numpy(active).cuda()
-        slots = slots_all[idx].contiguous()       # this call's slot order
         algs = torch.from_numpy(batch.algs[active]).cuda()
         off_t = torch.from_numpy(offs.astype(np.uint64).view(np.int64)).cuda()
         len_t = torch.from_numpy(sizes.astype(np.uint32).view(np.int32)).cuda()
         seg_t = torch.from_numpy(hb.seg_words(prior[active], more)).cuda()
-        call(algs, packed, off_t, len_t, seg_t, slots)
-        slots_all[idx] = slots
+        if indexed:
+            # each message keeps its slot; the call maps positions to slots
+            call(algs, packed, off_t, len_t, seg_t, slots_all, idx.to(torch.int32))
+        else:
+            slots = slots_all[idx].contiguous()       # this call's slot order
+            call(algs, packed, off_t, len_t, seg_t, slots, None)
+            slots_all[idx] = slots
         prior[active] += sizes
         done[active[~more]] = True
     torch.cuda.synchronize()
@@ -82,12 +86,14 @@ def _mixed_batch(n, seed, max_len):
     return b
 
 
-def test_segments_match_whole_message_digests(hb, oracle_mod):
+@pytest.mark.parametrize("indexed", [False, True])
+def test_segments_match_whole_message_digests(hb, oracle_mod, indexed):
     b = _mixed_batch(3000, seed=71, max_len=20000)
     rng = np.random.default_rng(5)
     pieces, nrounds = _rounds(b, rng, max_pieces=6)
     got = _run_segmented(hb, b, pieces, nrounds, rng,
-                         lambda a, p, o, l, s, out: hb.hash_batch_segments(a, p, o, l, s, out))
+                         lambda a, p, o, l, s, out, si: hb.hash_batch_segments(a, p, o, l, s, out, si),
+                         indexed=indexed)
     want = oracle_mod.hash_batch(None, b.packed, b.offsets, b.lengths, algs=b.algs)
     assert np.array_equal(got, want)
 
@@ -104,7 +110,8 @@ def test_segment_edge_cases(hb, oracle_mod):
         assert sum(c) == L
     rng = np.random.default_rng(6)
     got = _run_segmented(hb, b, pieces, max(len(p) for p in pieces), rng,
-                         lambda a, p, o, l, s, out: hb.hash_batch_segments(a, p, o, l, s, out))
+                         lambda a, p, o, l, s, out, si: hb.hash_batch_segments(a, p, o, l, s, out, si),
+                         indexed=True)
     want = oracle_mod.hash_batch(None, b.packed, b.offsets, b.lengths, algs=b.algs)
     assert np.array_equal(got, want)
 
@@ -126,7 +133,7 @@ def test_segments_through_captured_plans(hb, oracle_mod, shape):
     plan.set_segments(g_seg)
     plan.capture(g_algs, packed, g_off, g_len, g_out)
 
-    def call(a, p, o, l, s, out):
+    def call(a, p, o, l, s, out, si):
         m = a.numel()
         g_algs[:m] = a
         g_off[:m] = o

@@ -1,6 +1,12 @@
-"""The serving loop on the GPU: every request's digests are the same as when
-the request is hashed alone (and as the oracle's), whatever it was batched
-with, including under a budget tight enough that admission has to wait."""
+"""The streaming serving path on the GPU.
+
+A round claims ready messages of a ring, hashes their next segments and
+advances them; the server drives rounds on several streams.  Every message's
+final slot must equal the CPU oracle's digest of the whole message (and the
+plain single-algorithm path's), whatever segments, rounds and batch-mates it
+had, including when the ring is small enough that admission waits and
+entries are reused.
+"""
 import numpy as np
 import pytest
 
@@ -23,50 +29,123 @@ def env():
     return api, serve, pool_host, pool_dev, pool_bytes
 
 
-def _payload(req, pool_host):
-    return np.concatenate([pool_host[o:o + n] for o, n in req.segments]) if req.segments else \
-        np.zeros(0, dtype=np.uint8)
+def _ring(api, cap, req_cap):
+    dev = "cuda"
+    return {
+        "src": torch.zeros(cap, dtype=torch.int64, device=dev),
+        "prior": torch.zeros(cap, dtype=torch.int64, device=dev),
+        "len": torch.zeros(cap, dtype=torch.int32, device=dev),
+        "req": torch.zeros(cap, dtype=torch.int32, device=dev),
+        "alg": torch.zeros(cap, dtype=torch.uint8, device=dev),
+        "state": torch.zeros(cap, dtype=torch.int32, device=dev),
+        "slots": torch.zeros((cap, 32), dtype=torch.uint8, device=dev),
+        "req_remaining": torch.zeros(req_cap, dtype=torch.int32, device=dev),
+        "req_done": torch.zeros(req_cap, dtype=torch.int32).pin_memory(),
+    }
 
 
-def _check_alone(api, oracle_mod, reqs, pool_host, oracle_every=7):
+def test_rounds_hash_a_ring_segment_by_segment(env, oracle_mod):
+    api, serve, pool_host, pool_dev, pool_bytes = env
+    n, per_req = 700, 10
+    b = workloads.ragged(n, seed=81, max_len=9000, boundary_frac=0.05)
+    cap, nreq = 1024, (n + per_req - 1) // per_req
+    ring = _ring(api, cap, 128)
+    packed = torch.from_numpy(np.ascontiguousarray(b.packed)).cuda()
+    base = packed.data_ptr()
+    ring["src"][:n] = torch.from_numpy((b.offsets.astype(np.int64) + base)).cuda()
+    ring["len"][:n] = torch.from_numpy(b.lengths.view(np.int32)).cuda()
+    ring["alg"][:n] = torch.from_numpy(b.algs).cuda()
+    req = np.arange(n, dtype=np.int32) // per_req
+    ring["req"][:n] = torch.from_numpy(req).cuda()
+    ring["req_remaining"][:nreq] = torch.from_numpy(np.bincount(req).astype(np.int32)).cuda()
+    ring["state"][:n] = api.RING_READY
+    staging = torch.empty(64 << 10, dtype=torch.uint8, device="cuda")
+    seg = 512
+    rounds = [api.Round(ring, 300, staging[i * (32 << 10):], 32 << 10, seg, shape=16)
+              for i in range(2)]
+    streams = [torch.cuda.Stream() for _ in rounds]
+    torch.cuda.synchronize()
+    expect = int(sum(max(1, -(-int(L) // seg)) for L in b.lengths))
+    claimed = 0
+    for it in range(2000):
+        for r, s in zip(rounds, streams):
+            r.launch(0, n, stream=s)
+        torch.cuda.synchronize()
+        claimed += sum(r.report()[0] for r in rounds)
+        if (ring["req_done"].numpy()[:nreq] == 1).all():
+            break
+    assert (ring["req_done"].numpy()[:nreq] == 1).all()
+    assert claimed == expect                       # every segment exactly once
+    assert (ring["state"][:n] == api.RING_FREE).all()
+    assert (ring["req_remaining"][:nreq] == 0).all()
+    assert (ring["prior"][:n].cpu().numpy() == b.lengths.astype(np.int64)).all()
+    want = oracle_mod.hash_batch(None, b.packed, b.offsets, b.lengths, algs=b.algs)
+    assert np.array_equal(ring["slots"][:n].cpu().numpy(), want)
+    assert api.device_status() == 0
+    for r in rounds:
+        r.close()
+
+
+def test_round_arguments_are_checked(env):
+    api = env[0]
+    ring = _ring(api, 64, 4)
+    staging = torch.empty(4096, dtype=torch.uint8, device="cuda")
+    with pytest.raises(api.HashBatchError) as e:
+        api.Round(ring, 16, staging, 4096, 100)        # segment not a multiple of 64
+    assert e.value.code == -10
+    bad = dict(ring, state=torch.zeros(48, dtype=torch.int32, device="cuda"))
+    with pytest.raises(api.HashBatchError):
+        api.Round(bad, 16, staging, 4096, 128)          # capacity not a power of two
+    with pytest.raises(ValueError):                    # flags must be host memory
+        api.Round(dict(ring, req_done=torch.zeros(4, dtype=torch.int32, device="cuda")),
+                  16, staging, 4096, 128)
+    r = api.Round(ring, 16, staging, 4096, 128)
+    r.close()
+
+
+def _check_requests(api, oracle_mod, reqs, pool_host, oracle_every=3):
     for k, req in enumerate(reqs):
         assert req.done >= 0, req.rid
-        payload = _payload(req, pool_host)
-        buf = torch.from_numpy(np.concatenate([payload, np.zeros(16, np.uint8)])).cuda()
-        off = torch.from_numpy(req.local_offsets.view(np.int64)).cuda()
-        ln = torch.from_numpy(req.lengths.view(np.int32)).cuda()
-        alone = api.hash_batch(req.alg, buf, off, ln).cpu().numpy()
-        assert np.array_equal(req.digests, alone), req.rid
+        m = req.lengths.shape[0]
+        offs = req.src
         if k % oracle_every == 0:
-            want = oracle_mod.hash_batch(req.alg, payload, req.local_offsets, req.lengths)
+            want = oracle_mod.hash_batch(req.alg, pool_host, offs, req.lengths)
             assert np.array_equal(req.digests, want), req.rid
+        # the plain single-algorithm path on the same bytes
+        if k % (2 * oracle_every) == 1:
+            buf = torch.from_numpy(np.ascontiguousarray(pool_host)).cuda()
+            alone = api.hash_batch(req.alg, buf, torch.from_numpy(offs.view(np.int64)).cuda(),
+                                   torch.from_numpy(req.lengths.view(np.int32)).cuda())
+            assert np.array_equal(req.digests, alone[:m].cpu().numpy()), req.rid
 
 
-def test_served_digests_equal_alone_digests(env, oracle_mod):
+def test_served_digests_equal_oracle(env, oracle_mod):
     api, serve, pool_host, pool_dev, pool_bytes = env
-    reqs = serve.make_requests(150, 3000.0, seed=5, pool_bytes=pool_bytes, max_msgs=64,
+    reqs = serve.make_requests(120, 3000.0, seed=5, pool_bytes=pool_bytes, max_msgs=64,
                                max_len=1 << 16)
-    srv = serve.Server(pool_dev, budget=512 << 20, slots=3, max_msgs=8192, max_reqs=64)
+    srv = serve.Server(pool_dev, budget=256 << 20, rounds=3, segment_bytes=4096,
+                       max_msgs=4096, capacity=1 << 14, req_capacity=256, shape=16,
+                       warps_per_sm=8)
     srv.run(reqs, keep_digests=True)
     srv.close()
-    assert srv.batched_reqs == len(reqs) and srv.batches < len(reqs)   # requests shared batches
-    _check_alone(api, oracle_mod, reqs, pool_host)
+    assert srv.segments > sum(r.lengths.shape[0] for r in reqs)   # long messages were cut
+    _check_requests(api, oracle_mod, reqs, pool_host)
     stats = serve.latency_stats(reqs)
     assert stats["completed"] == len(reqs) and stats["p99_ms"] >= stats["p50_ms"] > 0
+    assert api.device_status() == 0
 
 
-def test_tight_budget_makes_admission_wait(env, oracle_mod):
+def test_small_ring_makes_admission_wait_and_reuses_entries(env, oracle_mod):
     api, serve, pool_host, pool_dev, pool_bytes = env
-    reqs = serve.make_requests(60, 20000.0, seed=6, pool_bytes=pool_bytes, max_msgs=32,
+    reqs = serve.make_requests(80, 50000.0, seed=6, pool_bytes=pool_bytes, max_msgs=32,
                                max_len=1 << 15)
-    biggest = max(r.nbytes for r in reqs)
-    budget = max(4 * biggest, 1 << 20)
-    srv = serve.Server(pool_dev, budget=budget, slots=2, max_msgs=4096, max_reqs=16)
+    srv = serve.Server(pool_dev, budget=64 << 20, rounds=2, segment_bytes=2048,
+                       max_msgs=512, capacity=128, req_capacity=8, shape=14, warps_per_sm=8)
     srv.run(reqs, keep_digests=True)
     srv.close()
-    assert srv.sched.arena.peak <= srv.sched.arena.capacity
-    assert any(r.admitted > r.arrival + 1e-4 for r in reqs)   # someone had to wait for space
-    _check_alone(api, oracle_mod, reqs, pool_host, oracle_every=5)
+    assert srv.book.tail > srv.book.capacity                      # the ring wrapped
+    assert any(r.admitted > r.arrival + 1e-4 for r in reqs)       # someone had to wait
+    _check_requests(api, oracle_mod, reqs, pool_host, oracle_every=2)
 
 
 def test_completion_flags_must_be_mapped_host_memory(env):
