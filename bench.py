@@ -699,7 +699,8 @@ def run_int_peak(args, dist):
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     names = ["LOP3", "IADD3", "SHF", "PRMT", "LOP3/IADD3/SHF", "IMAD", "LOP3/IMAD", "IADD3/IMAD",
              "SHF/IMAD", "LOP3/FFMA", "IMAD-add", "LOP3/IMAD-add", "LOP3/SHF/IADD3/IMAD-add",
-             "IMAD.HI", "LOP3/IMAD.HI", "LOP3/rotation-as-IMAD-pair"]
+             "IMAD.HI", "LOP3/IMAD.HI", "LOP3/rotation-as-IMAD-pair", "rotation-as-IMAD.WIDE+IMAD",
+             "LOP3/rotation-as-IMAD.WIDE+IMAD", "SHF/rotation-as-IMAD.WIDE+IMAD"]
     threads, iters = 512, 4000
     blocks = sms * 4
     res = {}

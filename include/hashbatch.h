@@ -421,7 +421,10 @@ int hash_batch_mixed_shape(const uint8_t *algs, const uint8_t *packed_bytes,
  * 6 LOP3/IMAD, 7 IADD3/IMAD, 8 SHF/IMAD, 9 LOP3/FFMA, 10 IMAD x*1+y (an add
  * on the multiply-add pipe), 11 LOP3/(x*1+y), 12 LOP3/SHF/IADD3/(x*1+y),
  * 13 IMAD.HI, 14 LOP3/IMAD.HI, 15 LOP3 + a rotation done as IMAD.HI of an
- * IMAD (three operations per pair of steps) --
+ * IMAD (three operations per pair of steps), 16 a rotation done on the
+ * multiply-add pipe as the two halves of a widening multiply by 2^s added
+ * together (two instructions per step), 17 LOP3 / that rotation,
+ * 18 SHF / that rotation --
  * and writes the SM cycles each block took to cycles_out_dev[blocks]
  * (device) and a sink word to sink_dev.  The number of 32-bit operations
  * executed is blocks * threads * iters * hash_int_peak_ops_per_iter().

@@ -27,6 +27,15 @@ constexpr bool kMd5Fma = false;
 constexpr bool kSha1Fma = true;
 constexpr bool kSm3Fma = true;
 
+// SM3 rotations that run on the FMA pipe (rotl_fma), one bit per site:
+//   1 C <- B<<<9   2 G <- F<<<19   4 A<<<12   8 (A<<<12 + E + T)<<<7
+//   16 both rotations of P0   32 W<<<15 in the expansion   64 W<<<7 in the
+//   expansion   128 both rotations of P1   256 A<<<12 + E + T as two IMADs
+#ifndef HB_SM3_FMA_ROT
+#define HB_SM3_FMA_ROT 0
+#endif
+constexpr unsigned kSm3Rot = HB_SM3_FMA_ROT;
+
 template <int ALG>
 struct AlgTraits;
 
@@ -247,11 +256,13 @@ __device__ __forceinline__ constexpr uint32_t sm3_tj_rot() {
   return s == 0 ? t : (uint32_t)((t << s) | (t >> (32 - s)));
 }
 
-__device__ __forceinline__ uint32_t sm3_p0(uint32_t x) {
-  return lop3<LUT_XOR3>(x, rotl<9>(x), rotl<17>(x));
+__device__ __forceinline__ uint32_t sm3_p0(uint32_t x, const MulConsts& mc) {
+  constexpr bool F = (kSm3Rot & 16u) != 0;
+  return lop3<LUT_XOR3>(x, rotl_f<9, F>(x, mc), rotl_f<17, F>(x, mc));
 }
-__device__ __forceinline__ uint32_t sm3_p1(uint32_t x) {
-  return lop3<LUT_XOR3>(x, rotl<15>(x), rotl<23>(x));
+__device__ __forceinline__ uint32_t sm3_p1(uint32_t x, const MulConsts& mc) {
+  constexpr bool F = (kSm3Rot & 128u) != 0;
+  return lop3<LUT_XOR3>(x, rotl_f<15, F>(x, mc), rotl_f<23, F>(x, mc));
 }
 
 // Rounds J .. 63.  W is a 16-word ring holding W_{J} .. W_{J+3} (and older
@@ -264,8 +275,10 @@ __device__ __forceinline__ void sm3_rounds(uint32_t (&v)[8], uint32_t (&W)[16], 
   if constexpr (J < 64) {
     constexpr int M = J + 4;  // index of the word produced this round
     if constexpr (M >= 16 && M < 68) {
-      const uint32_t x = lop3<LUT_XOR3>(W[(M - 16) & 15], W[(M - 9) & 15], rotl<15>(W[(M - 3) & 15]));
-      W[M & 15] = lop3<LUT_XOR3>(sm3_p1(x), rotl<7>(W[(M - 13) & 15]), W[(M - 6) & 15]);
+      const uint32_t x = lop3<LUT_XOR3>(W[(M - 16) & 15], W[(M - 9) & 15],
+                                        rotl_f<15, (kSm3Rot & 32u) != 0>(W[(M - 3) & 15], mc));
+      W[M & 15] = lop3<LUT_XOR3>(sm3_p1(x, mc), rotl_f<7, (kSm3Rot & 64u) != 0>(W[(M - 13) & 15], mc),
+                                 W[(M - 6) & 15]);
     }
     uint32_t& A = v[0];
     uint32_t& B = v[1];
@@ -277,8 +290,13 @@ __device__ __forceinline__ void sm3_rounds(uint32_t (&v)[8], uint32_t (&W)[16], 
     uint32_t& H = v[7];
     const uint32_t wj = W[J & 15];
     const uint32_t wpj = wj ^ W[M & 15];
-    const uint32_t a12 = rotl<12>(A);
-    const uint32_t ss1 = rotl<7>(a12 + E + sm3_tj_rot<J>());
+    const uint32_t a12 = rotl_f<12, (kSm3Rot & 4u) != 0>(A, mc);
+    uint32_t s0;
+    if constexpr ((kSm3Rot & 256u) != 0)
+      s0 = add_f<true>(a12, add_f<true>(E, sm3_tj_rot<J>(), mc), mc);
+    else
+      s0 = a12 + E + sm3_tj_rot<J>();
+    const uint32_t ss1 = rotl_f<7, (kSm3Rot & 8u) != 0>(s0, mc);
     const uint32_t ss2 = ss1 ^ a12;
     uint32_t ff, gg;
     if constexpr (J < 16) {
@@ -291,13 +309,13 @@ __device__ __forceinline__ void sm3_rounds(uint32_t (&v)[8], uint32_t (&W)[16], 
     const uint32_t tt1 = add_f<kSm3Fma>(ss2, add_f<kSm3Fma>(ff, add_f<kSm3Fma>(D, wpj, mc), mc), mc);
     const uint32_t tt2 = add_f<kSm3Fma>(ss1, add_f<kSm3Fma>(gg, add_f<kSm3Fma>(H, wj, mc), mc), mc);
     D = C;
-    C = rotl<9>(B);
+    C = rotl_f<9, (kSm3Rot & 1u) != 0>(B, mc);
     B = A;
     A = tt1;
     H = G;
-    G = rotl<19>(F);
+    G = rotl_f<19, (kSm3Rot & 2u) != 0>(F, mc);
     F = E;
-    E = sm3_p0(tt2);
+    E = sm3_p0(tt2, mc);
     sm3_rounds<J + 1>(v, W, mc);
   }
 }

@@ -75,6 +75,23 @@ __device__ __forceinline__ uint32_t rotl_add_f(uint32_t x, uint32_t y, const Mul
   else return __funnelshift_l(x, x, S) + y;
 }
 
+// rotl(x, S) entirely on the FMA pipe: the 64-bit product x * 2^S holds
+// x << S in its low word and x >> (32 - S) in its high word; their bits do not
+// overlap, so their sum is the rotation (one IMAD.WIDE, one IMAD).
+template <int S>
+__device__ __forceinline__ uint32_t rotl_fma(uint32_t x, const MulConsts& m) {
+  uint64_t w;
+  asm("mul.wide.u32 %0, %1, %2;" : "=l"(w) : "r"(x), "r"(m.pow2[S]));
+  return mad_lo((uint32_t)w, m.one, (uint32_t)(w >> 32));
+}
+
+// rotl(x, S) on the ALU pipe (one SHF) or, when F, on the FMA pipe.
+template <int S, bool F>
+__device__ __forceinline__ uint32_t rotl_f(uint32_t x, const MulConsts& m) {
+  if constexpr (F && HB_FMA_OFFLOAD) return rotl_fma<S>(x, m);
+  else return __funnelshift_l(x, x, S);
+}
+
 // Byte permute (PRMT): bytes of the 64-bit value {hi:lo} picked by `sel`.
 __device__ __forceinline__ uint32_t prmt(uint32_t lo, uint32_t hi, uint32_t sel) {
   return __byte_perm(lo, hi, sel);

@@ -170,6 +170,9 @@ __global__ void hb_bounds_kernel(const uint64_t* offsets, const uint32_t* length
 //   6 LOP3/IMAD   7 IADD3/IMAD   8 SHF/IMAD   9 LOP3/FFMA   10 IMAD x*1+y
 //   11 LOP3/(x*1+y)   12 LOP3/SHF/IADD3/(x*1+y)   13 IMAD.HI x*2^7+y
 //   14 LOP3/IMAD.HI   15 LOP3 + rotation as IMAD.HI(x, 2^7, IMAD(x, 2^7, 0))
+//   16 rotation on the multiply-add pipe: {lo, hi} = x*2^7 (IMAD.WIDE),
+//      then lo*1 + hi (IMAD): two instructions per counted step
+//   17 LOP3 / rotation as in 16   18 SHF / rotation as in 16
 
 template <int OP>
 __device__ __forceinline__ uint32_t peak_step(int u, uint32_t x, uint32_t y, uint32_t z, uint32_t one) {
@@ -204,6 +207,15 @@ __device__ __forceinline__ uint32_t peak_step(int u, uint32_t x, uint32_t y, uin
     uint32_t lo, d;
     asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(lo) : "r"(x), "r"(one << 7), "r"(0u));
     asm("mad.hi.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(x), "r"(one << 7), "r"(lo));
+    return d;
+  }
+  else if constexpr (OP >= 16 && OP <= 18) {
+    if (OP == 17 && !(u & 1)) return lop3<0x96>(x, y, z);
+    if (OP == 18 && !(u & 1)) return __funnelshift_l(x, y, 7);
+    uint64_t w;
+    asm("mul.wide.u32 %0, %1, %2;" : "=l"(w) : "r"(x), "r"(one << 7));
+    uint32_t d;
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"((uint32_t)w), "r"(one), "r"((uint32_t)(w >> 32)));
     return d;
   }
   else {
@@ -399,7 +411,8 @@ cudaError_t launch_int_peak(int op, int blocks, int threads, int iters, unsigned
                              int_peak_launch<6>, int_peak_launch<7>, int_peak_launch<8>,
                              int_peak_launch<9>, int_peak_launch<10>, int_peak_launch<11>,
                              int_peak_launch<12>, int_peak_launch<13>, int_peak_launch<14>,
-                             int_peak_launch<15>};
+                             int_peak_launch<15>, int_peak_launch<16>, int_peak_launch<17>,
+                             int_peak_launch<18>};
   if (op < 0 || op >= (int)(sizeof(table) / sizeof(table[0]))) return cudaErrorInvalidValue;
   table[op](blocks, threads, iters, cycles, sink, stream);
   return cudaGetLastError();

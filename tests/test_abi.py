@@ -80,7 +80,7 @@ def test_int_peak_argument_checks(lib):
     assert lib.hash_int_peak(0, 0, 32, 1, p, p, None) == -10
     assert lib.hash_int_peak(0, 1, 2048, 1, p, p, None) == -10
     assert lib.hash_int_peak_ops_per_iter() == 32
-    assert lib.hash_int_peak(16, 1, 32, 1, p, p, None) == -10
+    assert lib.hash_int_peak(19, 1, 32, 1, p, p, None) == -10
 
 
 def test_product_path_does_not_import_oracle():
