@@ -332,7 +332,12 @@ int hash_batch_check_bounds(const uint64_t *offsets, const uint32_t *lengths, ui
  * hash_batch_host -- the same computation from HOST buffers: copies the packed
  * bytes, offsets and lengths to device memory owned by the library, hashes
  * them, copies the digest slots back to digests_host, and waits for the
- * stream.  Host buffers should be pinned (cudaHostAlloc / cudaHostRegister)
+ * stream.  The packed bytes go over in chunks; the messages whose last byte
+ * is in a chunk are hashed, and their slots copied back, while later chunks
+ * are still coming in (two library streams besides `stream`).  This assumes
+ * message ends (offset + length) do not decrease with the index, as in any
+ * back-to-back layout; a device check confirms it, and otherwise every
+ * message is hashed again once all bytes are in (same result, slower).  Host buffers should be pinned (cudaHostAlloc / cudaHostRegister)
  * for full copy speed; pageable memory works but is slower.  algs_host may be
  * NULL (single `alg`) or a host array of per-message codes (mixed path).
  * After the copies, every message is checked against packed_len on the

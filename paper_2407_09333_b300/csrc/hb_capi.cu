@@ -21,6 +21,10 @@ constexpr int kMaxDevices = 64;
 constexpr int kMaxShapes = 64;  // capacity of the per-shape occupancy cache
 constexpr uint64_t kMaxPlainN = 1ull << 40;
 constexpr uint64_t kMaxMixedN = 1ull << 31;
+// Host path: the packed bytes go over in up to kHostChunks pieces of at least
+// kHostChunkMin bytes, so hashing and the copy-out overlap the copy-in.
+constexpr int kHostChunks = 16;
+constexpr uint64_t kHostChunkMin = 8ull << 20;
 
 struct DeviceBuf {
   void* p = nullptr;
@@ -66,7 +70,11 @@ struct Ctx {
   bool ws_used = false;
   // host-buffer path
   DeviceBuf h_packed, h_off, h_len, h_algs, h_dig, h_flag;
-  int* flag_host = nullptr;              // pinned
+  int* flag_host = nullptr;              // pinned: [0] bounds, [1] ends not monotone
+  // pipelined host path: hashing and copy-out streams, per-chunk events
+  cudaStream_t host_hash = nullptr, host_out = nullptr;
+  cudaEvent_t ev_meta = nullptr, ev_end = nullptr;
+  cudaEvent_t ev_in[kHostChunks] = {}, ev_hashed[kHostChunks] = {};
 };
 
 std::mutex g_mu;
@@ -93,7 +101,7 @@ int get_ctx(Ctx** out) {
         cudaMalloc(&c->status, sizeof(int)) != cudaSuccess ||
         cudaMemset(c->status, 0, sizeof(int)) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ws_event, cudaEventDisableTiming) != cudaSuccess ||
-        cudaHostAlloc(&c->flag_host, sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
+        cudaHostAlloc(&c->flag_host, 2 * sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
       delete c;
       return cuda_fail(cudaGetLastError());
     }
@@ -354,6 +362,57 @@ int hash_batch_check_bounds(const uint64_t* offsets, const uint32_t* lengths, ui
   return e == cudaSuccess ? HB_OK : cuda_fail(e);
 }
 
+}  // extern "C"
+
+namespace {
+
+int host_streams(Ctx* c) {
+  if (c->host_hash) return HB_OK;
+  cudaError_t e = cudaStreamCreateWithFlags(&c->host_hash, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->host_out, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_meta, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_end, cudaEventDisableTiming);
+  for (int k = 0; e == cudaSuccess && k < kHostChunks; ++k) {
+    e = cudaEventCreateWithFlags(&c->ev_in[k], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_hashed[k], cudaEventDisableTiming);
+  }
+  return e == cudaSuccess ? HB_OK : cuda_fail(e);
+}
+
+// Hashes messages [first, first + count) of the device copies on stream s.
+int host_hash_range(Ctx* c, int alg, const uint8_t* d_algs, const uint8_t* d_packed,
+                    const uint64_t* d_off, const uint32_t* d_len, uint64_t first, uint64_t count,
+                    uint8_t* d_dig, const int* abort_flag, cudaStream_t s) {
+  if (count == 0) return HB_OK;
+  if (d_algs)
+    return launch_mixed(c, c->tune_mixed, 0, d_algs + first, d_packed, d_off + first,
+                        d_len + first, count, d_dig + first * HB_SLOT_BYTES, c->ws.p, abort_flag, s);
+  KernelArgs a{};
+  a.packed = d_packed;
+  a.offsets = d_off + first;
+  a.lengths = d_len + first;
+  a.n = count;
+  a.digests = d_dig + first * HB_SLOT_BYTES;
+  a.status = c->status;
+  a.abort_flag = abort_flag;
+  a.wait_limit_ns = g_wait_limit_ns;
+  a.mc = hb::make_mul_consts();
+  return launch_plain(c, alg, c->tune_plain[alg], 0, a, s);
+}
+
+}  // namespace
+
+extern "C" {
+
+// Pipeline: the caller's stream copies the metadata, then the packed bytes in
+// chunks [b_k, b_k+1); the hashing stream, after the bounds check, hashes the
+// messages whose last byte lies in chunk k as soon as chunk k has arrived;
+// the copy-out stream brings their digest slots back while later chunks are
+// still coming in.  Which messages end in which chunk is found on the host by
+// binary search, assuming message ends (offset + length) never decrease with
+// the index -- true of any back-to-back layout.  A device check confirms
+// that; when it fails, every message is hashed again once all bytes are in,
+// so the result never depends on the layout.
 int hash_batch_host(int alg, const uint8_t* algs_host, const uint8_t* packed_host,
                     uint64_t packed_len, const uint64_t* offsets_host,
                     const uint32_t* lengths_host, uint64_t n, uint8_t* digests_host,
@@ -366,6 +425,7 @@ int hash_batch_host(int alg, const uint8_t* algs_host, const uint8_t* packed_hos
   Ctx* c = nullptr;
   int rc = get_ctx(&c);
   if (rc) return rc;
+  if ((rc = host_streams(c))) return rc;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   // Make sure no earlier call on another stream still uses the buffers.
   if (cudaDeviceSynchronize() != cudaSuccess) return cuda_fail(cudaGetLastError());
@@ -375,52 +435,81 @@ int hash_batch_host(int alg, const uint8_t* algs_host, const uint8_t* packed_hos
       (e = c->h_off.reserve(n * sizeof(uint64_t))) != cudaSuccess ||
       (e = c->h_len.reserve(n * sizeof(uint32_t))) != cudaSuccess ||
       (e = c->h_dig.reserve(n * (size_t)HB_SLOT_BYTES)) != cudaSuccess ||
-      (e = c->h_flag.reserve(sizeof(int))) != cudaSuccess ||
+      (e = c->h_flag.reserve(2 * sizeof(int))) != cudaSuccess ||
       (algs_host && (e = c->h_algs.reserve(n)) != cudaSuccess))
     return cuda_fail(e);
+  if (algs_host && (rc = reserve_ws(c, n))) return rc;
   uint8_t* d_packed = static_cast<uint8_t*>(c->h_packed.p);
   uint64_t* d_off = static_cast<uint64_t*>(c->h_off.p);
   uint32_t* d_len = static_cast<uint32_t*>(c->h_len.p);
   uint8_t* d_dig = static_cast<uint8_t*>(c->h_dig.p);
   int* d_flag = static_cast<int*>(c->h_flag.p);
-  uint8_t* d_algs = static_cast<uint8_t*>(c->h_algs.p);
-  if (packed_len && cudaMemcpyAsync(d_packed, packed_host, packed_len, cudaMemcpyHostToDevice, s))
-    return cuda_fail(cudaGetLastError());
+  uint8_t* d_algs = algs_host ? static_cast<uint8_t*>(c->h_algs.p) : nullptr;
+  cudaStream_t sh = c->host_hash, so = c->host_out;
+  auto fail = [&]() { return cuda_fail(cudaGetLastError()); };
+
+  // metadata, then the checks on the hashing stream
   if (cudaMemcpyAsync(d_off, offsets_host, n * sizeof(uint64_t), cudaMemcpyHostToDevice, s) ||
-      cudaMemcpyAsync(d_len, lengths_host, n * sizeof(uint32_t), cudaMemcpyHostToDevice, s))
-    return cuda_fail(cudaGetLastError());
-  if (algs_host && cudaMemcpyAsync(d_algs, algs_host, n, cudaMemcpyHostToDevice, s))
-    return cuda_fail(cudaGetLastError());
-  // Bounds are checked on the device before any message byte is read; the
-  // hashing kernels skip all work when the check failed.
-  if (cudaMemsetAsync(d_flag, 0, sizeof(int), s)) return cuda_fail(cudaGetLastError());
-  e = hb::launch_bounds(d_off, d_len, n, packed_len, d_flag, nullptr, grid_for_elementwise(c, n), s);
+      cudaMemcpyAsync(d_len, lengths_host, n * sizeof(uint32_t), cudaMemcpyHostToDevice, s) ||
+      (algs_host && cudaMemcpyAsync(d_algs, algs_host, n, cudaMemcpyHostToDevice, s)) ||
+      cudaEventRecord(c->ev_meta, s) || cudaStreamWaitEvent(sh, c->ev_meta, 0) ||
+      cudaMemsetAsync(d_flag, 0, 2 * sizeof(int), sh))
+    return fail();
+  // bounds first: the hashing kernels skip all work when it failed
+  e = hb::launch_bounds(d_off, d_len, n, packed_len, d_flag, nullptr, grid_for_elementwise(c, n), sh);
+  if (e == cudaSuccess) e = hb::launch_monotone(d_off, d_len, n, d_flag + 1, grid_for_elementwise(c, n), sh);
   if (e != cudaSuccess) return cuda_fail(e);
-  if (algs_host) {
-    if ((rc = reserve_ws(c, n))) return rc;
-    rc = launch_mixed(c, c->tune_mixed, 0, d_algs, d_packed, d_off, d_len, n, d_dig, c->ws.p,
-                      d_flag, s);
-    if (rc) return rc;
-    if (cudaEventRecord(c->ws_event, s) != cudaSuccess) return cuda_fail(cudaGetLastError());
-    c->ws_used = true;
-  } else {
-    KernelArgs a{};
-    a.packed = d_packed;
-    a.offsets = d_off;
-    a.lengths = d_len;
-    a.n = n;
-    a.digests = d_dig;
-    a.status = c->status;
-    a.abort_flag = d_flag;
-    a.wait_limit_ns = g_wait_limit_ns;
-  a.mc = hb::make_mul_consts();
-    if ((rc = launch_plain(c, alg, c->tune_plain[alg], 0, a, s))) return rc;
+
+  // chunks of the packed bytes and the messages ending in each
+  int K = (int)std::min<uint64_t>(kHostChunks, std::max<uint64_t>(1, packed_len / kHostChunkMin));
+  uint64_t prev_b = 0, prev_m = 0;
+  for (int k = 0; k < K; ++k) {
+    const uint64_t b = (k == K - 1) ? packed_len : packed_len / K * (k + 1);
+    // first message whose end lies past b (ends assumed non-decreasing)
+    uint64_t lo = prev_m, hi = n;
+    if (k == K - 1) {
+      lo = n;
+    } else {
+      while (lo < hi) {
+        const uint64_t mid = lo + (hi - lo) / 2;
+        if (offsets_host[mid] + lengths_host[mid] <= b) lo = mid + 1; else hi = mid;
+      }
+    }
+    if (b > prev_b && cudaMemcpyAsync(d_packed + prev_b, packed_host + prev_b, b - prev_b,
+                                      cudaMemcpyHostToDevice, s))
+      return fail();
+    if (cudaEventRecord(c->ev_in[k], s) || cudaStreamWaitEvent(sh, c->ev_in[k], 0)) return fail();
+    if ((rc = host_hash_range(c, alg, d_algs, d_packed, d_off, d_len, prev_m, lo - prev_m, d_dig,
+                              d_flag, sh)))
+      return rc;
+    if (cudaEventRecord(c->ev_hashed[k], sh) || cudaStreamWaitEvent(so, c->ev_hashed[k], 0))
+      return fail();
+    if (lo > prev_m && cudaMemcpyAsync(digests_host + prev_m * HB_SLOT_BYTES,
+                                       d_dig + prev_m * HB_SLOT_BYTES,
+                                       (lo - prev_m) * (size_t)HB_SLOT_BYTES,
+                                       cudaMemcpyDeviceToHost, so))
+      return fail();
+    prev_b = b;
+    prev_m = lo;
   }
-  if (cudaMemcpyAsync(digests_host, d_dig, n * (size_t)HB_SLOT_BYTES, cudaMemcpyDeviceToHost, s) ||
-      cudaMemcpyAsync(c->flag_host, d_flag, sizeof(int), cudaMemcpyDeviceToHost, s))
-    return cuda_fail(cudaGetLastError());
-  if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_fail(cudaGetLastError());
-  return *c->flag_host ? HB_ERR_BOUNDS : HB_OK;
+  if (cudaMemcpyAsync(c->flag_host, d_flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, so) ||
+      cudaEventRecord(c->ev_end, so) || cudaStreamWaitEvent(s, c->ev_end, 0))
+    return fail();
+  if (algs_host) {
+    if (cudaEventRecord(c->ws_event, sh) != cudaSuccess) return fail();
+    c->ws_used = true;
+  }
+  if (cudaStreamSynchronize(s) != cudaSuccess) return fail();
+  if (c->flag_host[0]) return HB_ERR_BOUNDS;
+  if (c->flag_host[1]) {
+    // ends decrease somewhere: every byte is in now, hash everything again
+    if ((rc = host_hash_range(c, alg, d_algs, d_packed, d_off, d_len, 0, n, d_dig, d_flag, s)))
+      return rc;
+    if (cudaMemcpyAsync(digests_host, d_dig, n * (size_t)HB_SLOT_BYTES, cudaMemcpyDeviceToHost, s) ||
+        cudaStreamSynchronize(s))
+      return fail();
+  }
+  return HB_OK;
 }
 
 int hash_device_status(void* stream, int* status_out) {
@@ -454,6 +543,14 @@ int hash_release_device(void) {
   if (c->status) cudaFree(c->status);
   if (c->ws_event) cudaEventDestroy(c->ws_event);
   if (c->flag_host) cudaFreeHost(c->flag_host);
+  if (c->host_hash) cudaStreamDestroy(c->host_hash);
+  if (c->host_out) cudaStreamDestroy(c->host_out);
+  for (cudaEvent_t ev : {c->ev_meta, c->ev_end})
+    if (ev) cudaEventDestroy(ev);
+  for (int k = 0; k < kHostChunks; ++k) {
+    if (c->ev_in[k]) cudaEventDestroy(c->ev_in[k]);
+    if (c->ev_hashed[k]) cudaEventDestroy(c->ev_hashed[k]);
+  }
   delete c;
   g_ctx[dev] = nullptr;
   return HB_OK;

@@ -161,6 +161,18 @@ __global__ void hb_bounds_kernel(const uint64_t* offsets, const uint32_t* length
   }
 }
 
+// Whether message ends (offset + length) are non-decreasing in index order;
+// sets *flag = 1 when they are not.  The pipelined host path relies on it to
+// hash a message once the packed bytes up to its end have arrived.
+__global__ void hb_monotone_kernel(const uint64_t* offsets, const uint32_t* lengths, uint64_t n,
+                                   int* flag) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  bool bad = false;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i + 1 < n; i += stride)
+    bad |= offsets[i] + lengths[i] > offsets[i + 1] + lengths[i + 1];
+  if (bad) atomicExch(flag, 1);
+}
+
 // ---------------------------------------------------------------------------
 // Integer issue microbenchmark: eight independent chains per thread, four
 // unrolled steps per iteration, one 32-bit operation per chain per step.
@@ -394,6 +406,12 @@ cudaError_t launch_bounds(const uint64_t* offsets, const uint32_t* lengths, uint
                           cudaStream_t stream) {
   hb_bounds_kernel<<<grid, 256, 0, stream>>>(offsets, lengths, n, packed_len, status_dev,
                                              ctx_status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_monotone(const uint64_t* offsets, const uint32_t* lengths, uint64_t n, int* flag,
+                            int grid, cudaStream_t stream) {
+  hb_monotone_kernel<<<grid, 256, 0, stream>>>(offsets, lengths, n, flag);
   return cudaGetLastError();
 }
 

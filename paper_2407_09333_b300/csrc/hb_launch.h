@@ -121,6 +121,9 @@ cudaError_t launch_bucketing(const MixedArgs& m, int grid, cudaStream_t stream);
 cudaError_t launch_bounds(const uint64_t* offsets, const uint32_t* lengths, uint64_t n,
                           uint64_t packed_len, int* status_dev, int* ctx_status, int grid,
                           cudaStream_t stream);
+// flag = 1 when offsets[i] + lengths[i] decreases anywhere in index order.
+cudaError_t launch_monotone(const uint64_t* offsets, const uint32_t* lengths, uint64_t n, int* flag,
+                            int grid, cudaStream_t stream);
 cudaError_t launch_int_peak(int op, int blocks, int threads, int iters, unsigned long long* cycles,
                             uint32_t* sink, cudaStream_t stream);
 cudaError_t launch_selftest_wait(uint64_t limit_ns, int* status, cudaStream_t stream);

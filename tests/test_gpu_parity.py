@@ -161,6 +161,33 @@ def test_host_path_plain_and_mixed(hb, oracle_mod):
     _assert_slots_equal(out, _oracle_slots(oracle_mod, plain, 1), "host plain")
 
 
+@pytest.mark.parametrize("layout", ["packed", "shuffled"])
+def test_host_path_pipelined_chunks(hb, oracle_mod, layout):
+    # ~40 MB of packed bytes: the host path copies it in several chunks and
+    # hashes each chunk's messages while later chunks are in flight.  In the
+    # shuffled layout message ends are not in index order, so the chunk
+    # assignment is wrong and the library must notice and hash again.
+    rng = np.random.default_rng(21)
+    lens = rng.integers(0, 9000, size=9000).astype(np.uint32)
+    lens[:7] = workloads.BOUNDARY_LENGTHS
+    b = workloads.scattered(lens, seed=22, overlap=False, mixed=True)
+    offsets = b.offsets.copy()
+    if layout == "shuffled":
+        perm = rng.permutation(b.n)
+        offsets, lens_p, algs_p = offsets[perm], b.lengths[perm], b.algs[perm]
+        b = workloads.Batch(b.packed, offsets, lens_p, algs_p)
+    for alg in (0, 2, None):
+        out = np.zeros((b.n, 32), dtype=np.uint8)
+        if alg is None:
+            hb.hash_batch_host(None, b.packed, b.offsets, b.lengths, out, algs=b.algs)
+        else:
+            hb.hash_batch_host(alg, b.packed, b.offsets, b.lengths, out)
+        sel = np.arange(0, b.n, 7)
+        ref = b if alg is None else workloads.Batch(b.packed, b.offsets, b.lengths, None)
+        want = _oracle_slots(oracle_mod, ref, alg, sel)
+        _assert_slots_equal(out[sel], want, "host %s %s" % (layout, alg))
+
+
 def test_host_path_rejects_out_of_bounds(hb):
     b = workloads.fixed(100, 40, seed=2)
     offs = b.offsets.copy()
