@@ -424,13 +424,22 @@ __device__ __forceinline__ void warp_pipeline(Source& src, uint8_t* wsm, const K
       if (act) {
         const uint32_t dst = slots + (is * 32 + lane) * kSlotBytes;
         const bool extra = (t.addr & 15u) != 0u;  // unaligned window needs one more granule
+        if (avail == kSlotBytes) {
+          // the whole slot lies inside the message (the usual case in a long
+          // message): every granule is a full one
 #pragma unroll
-        for (int g = 0; g < kGranules; ++g) {
-          const int32_t v = avail - 16 * g;
-          const uint32_t nbytes = v <= 0 ? 0u : (v >= 16 ? 16u : (uint32_t)v);
-          const uint64_t from = nbytes ? g0 + 16ull * g : safe_src;
-          if (g < kGranules - 1 || extra)
-            cp_async16_zfill(dst + 16 * g, reinterpret_cast<const void*>(from), nbytes);
+          for (int g = 0; g < kGranules; ++g)
+            if (g < kGranules - 1 || extra)
+              cp_async16_zfill(dst + 16 * g, reinterpret_cast<const void*>(g0 + 16ull * g), 16u);
+        } else {
+#pragma unroll
+          for (int g = 0; g < kGranules; ++g) {
+            const int32_t v = avail - 16 * g;
+            const uint32_t nbytes = v <= 0 ? 0u : (v >= 16 ? 16u : (uint32_t)v);
+            const uint64_t from = nbytes ? g0 + 16ull * g : safe_src;
+            if (g < kGranules - 1 || extra)
+              cp_async16_zfill(dst + 16 * g, reinterpret_cast<const void*>(from), nbytes);
+          }
         }
       }
     } else {
