@@ -637,30 +637,45 @@ def run_serve(args, dist):
     pool_bytes = args.pool_mib << 20
     pool_host = workloads.fixed(1, pool_bytes, shard_seed(4, dist.rank)).packed
     pool = torch.from_numpy(np.ascontiguousarray(pool_host)).cuda()
-    srv = serve.Server(pool, budget=args.budget_gib << 30, rounds=args.rounds,
-                       segment_bytes=(3 * args.segment_kib << 10, 2 * args.segment_kib << 10,
-                                      args.segment_kib << 10), shape=args.serve_shape,
-                       warps_per_sm=args.serve_warps)
+    in_place = not args.staged
+
+    def make_server(place):
+        return serve.Server(pool, budget=args.budget_gib << 30, rounds=args.rounds,
+                            segment_bytes=(3 * args.segment_kib << 10, 2 * args.segment_kib << 10,
+                                           args.segment_kib << 10), shape=args.serve_shape,
+                            warps_per_sm=args.serve_warps, in_place=place)
+
+    def serve_point(srv, load, seed):
+        rate = load * ref_gbs * 1e9 / mean_req
+        reqs = serve.make_requests(args.requests, rate, seed, pool_bytes)
+        r0, s0 = srv.rounds_launched, srv.segments
+        srv.run(reqs)
+        st = serve.latency_stats(reqs)
+        st.update({"offered_load": load, "offered_gbs": rate * mean_req / 1e9,
+                   "requests": len(reqs), "rounds": srv.rounds_launched - r0,
+                   "segments": srv.segments - s0})
+        return st
+
     probe = serve.make_requests(args.requests, 1.0, shard_seed(4, dist.rank), pool_bytes)
     mean_req = float(np.mean([r.nbytes for r in probe]))
     all_lengths = np.concatenate([r.lengths for r in probe])
     all_algs = np.concatenate([np.full(r.lengths.shape[0], r.alg, np.uint8) for r in probe])
     points = []
+    srv = make_server(in_place)
     with ClockSampler(torch.cuda.current_device()) as clocks:
         for k, load in enumerate(args.loads):
-            rate = load * ref_gbs * 1e9 / mean_req
-            reqs = serve.make_requests(args.requests, rate, shard_seed(4, dist.rank) + 17 * k, pool_bytes)
-            r0, s0 = srv.rounds_launched, srv.segments
-            srv.run(reqs)
-            st = serve.latency_stats(reqs)
-            st.update({"offered_load": load, "offered_gbs": rate * mean_req / 1e9,
-                       "requests": len(reqs), "rounds": srv.rounds_launched - r0,
-                       "segments": srv.segments - s0})
-            points.append(st)
+            points.append(serve_point(srv, load, shard_seed(4, dist.rank) + 17 * k))
     budget_used = {"ring_and_rounds": serve.device_bytes(srv.book.capacity, srv.book.req_capacity,
                                                          len(srv.slots), srv.max_msgs),
-                   "staging": srv.staging_per_round * len(srv.slots)}
+                   "staging": 0 if srv.in_place else srv.staging_per_round * len(srv.slots)}
     srv.close()
+    del srv
+    # the other mode at the highest offered load, for comparison
+    other = make_server(not in_place)
+    other_point = serve_point(other, max(args.loads), shard_seed(4, dist.rank) + 17 * len(args.loads))
+    other.close()
+    del other
+    torch.cuda.empty_cache()
     plain_gbs, plain_L = plain_equal_bytes_gbs(api, torch, all_lengths, all_algs, pool)
     top = max(points, key=lambda p: p["offered_load"])
     # sustained rate: requests finishing between the 10th and 90th percentile
@@ -674,14 +689,18 @@ def run_serve(args, dist):
                 "lengths log-uniform in [16 B, 1 MiB], random algorithm; bytes from a %d MiB "
                 "random pool (numpy PCG64)" % args.pool_mib,
         "config": {"workload": "serving: continuous batching under a %d GiB device budget, "
-                               "%d streaming rounds, %d KiB segments, %d requests per load point"
-                               % (args.budget_gib, args.rounds, args.segment_kib, args.requests),
+                               "%d streaming rounds (%s), %d KiB SM3 segments, %d requests per load point"
+                               % (args.budget_gib, args.rounds,
+                                  "in place" if in_place else "staging copy",
+                                  args.segment_kib, args.requests),
                    "reference_ragged_gbs": ref_gbs, "mean_request_bytes": mean_req,
                    "parallelism": "dp%d: independent servers, no collective" % dist.world},
         "serve": points,
         "served_vs_plain_equal_bytes": top["gbs"] / plain_gbs,
         "steady_vs_plain_equal_bytes": top["steady_gbs"] / plain_gbs,
         "device_budget_bytes": budget_used,
+        "other_mode": dict(other_point, mode="staging copy" if in_place else "in place",
+                           steady_vs_plain_equal_bytes=other_point["steady_gbs"] / plain_gbs),
         "plain_equal_bytes_gbs": plain_gbs, "plain_mean_length": plain_L,
         "p50_ms_at_top_load": top["p50_ms"], "p99_ms_at_top_load": top["p99_ms"],
         "clocks": clocks.summary(),
@@ -731,11 +750,14 @@ def main(argv=None):
     p.add_argument("--loads", type=float, nargs="+", default=[0.1, 0.3, 0.5, 0.7, 0.9, 1.1],
                    help="offered loads as fractions of the ragged path's throughput (c5)")
     p.add_argument("--budget-gib", type=int, default=8, help="device-memory budget (c5)")
-    p.add_argument("--rounds", type=int, default=8, help="streaming rounds in flight (c5)")
-    p.add_argument("--segment-kib", type=int, default=64,
+    p.add_argument("--rounds", type=int, default=2, help="streaming rounds in flight (c5)")
+    p.add_argument("--segment-kib", type=int, default=32,
                    help="SM3 segment of long messages; SHA-1 2x, MD5 3x (c5)")
     p.add_argument("--serve-shape", type=int, default=11, help="launch shape of the rounds (c5)")
     p.add_argument("--serve-warps", type=int, default=8, help="resident warps per SM per round (c5)")
+    p.add_argument("--staged", action="store_true",
+                   help="serve through the staging copy instead of hashing segments where the "
+                        "client's bytes are (c5)")
     p.add_argument("--pool-mib", type=int, default=2048, help="random-byte pool for requests (c5)")
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--e2e-steps", type=int, default=10)

@@ -262,7 +262,9 @@ int hash_plan_destroy(hb_plan *plan);
  *      while its next segment fits the round's limits (max_msgs segments,
  *      staging_bytes of staging, each segment starting 16-byte aligned).
  *      A segment is the next min(len - prior, segment_bytes[alg]) bytes;
- *   2. copy: the segments' bytes go from src + prior to the staging area;
+ *   2. copy: the segments' bytes go from src + prior to the staging area
+ *      (with staging NULL, none: step 3 reads them where they are, and
+ *      staging_bytes only caps the bytes one round claims);
  *   3. hash: the ragged path over the segments (hash_batch_segments with
  *      slot_index = the entry), so each entry's 32-byte slot carries its
  *      chaining value between rounds and finally its digest;
@@ -284,8 +286,8 @@ int hash_plan_destroy(hb_plan *plan);
  *   (cudaMalloc) and captures its launch sequence as a CUDA graph.
  *   segment_bytes[3]: per algorithm code, multiples of 64 (a cheaper
  *   algorithm can take longer segments for the same chain time);
- *   max_msgs < 2^23; staging must be
- *   16-byte aligned.  Sets up every kernel first: call it outside any capture.
+ *   max_msgs < 2^23; staging must be 16-byte aligned, or NULL for the
+ *   in-place mode.  Sets up every kernel first: call it outside any capture.
  * hash_round_launch -- runs one round for the window [head, tail)
  *   (tail - head <= capacity) on `stream`.  Do not launch a round again until
  *   its previous launch has finished.

@@ -389,7 +389,8 @@ class Round:
     int32), alg (CUDA uint8), slots (CUDA uint8, capacity x 32),
     req_remaining (CUDA int32) and req_done (pinned CPU int32); `staging` a
     CUDA uint8 tensor (16-byte aligned) of which the round uses
-    staging_bytes from the start.
+    staging_bytes from the start, or None to hash segments in place (then
+    staging_bytes only caps the bytes a round claims).
     """
 
     def __init__(self, ring: dict, max_msgs: int, staging, staging_bytes: int,
@@ -398,7 +399,7 @@ class Round:
         cap = int(ring["state"].numel())
         if ring["req_done"].is_cuda or not ring["req_done"].is_pinned():
             raise ValueError("req_done must be pinned host memory")
-        if int(staging_bytes) > staging.numel():
+        if staging is not None and int(staging_bytes) > staging.numel():
             raise ValueError("staging_bytes exceeds the staging tensor")
         self._ring = HbRing(
             cap, _dev_ptr(ring["src"], 8, "src"), _dev_ptr(ring["prior"], 8, "prior"),
@@ -411,7 +412,8 @@ class Round:
         seg = (_c_u32 * 3)(*[int(x) for x in segment_bytes])
         h = ctypes.c_void_p()
         _check(lib().hash_round_create(ctypes.byref(self._ring), int(max_msgs),
-                                       _dev_ptr(staging, 1, "staging"), int(staging_bytes),
+                                       None if staging is None else _dev_ptr(staging, 1, "staging"),
+                                       int(staging_bytes),
                                        seg, int(shape), int(warps_per_sm),
                                        ctypes.byref(h)), "hash_round_create")
         self._h = h

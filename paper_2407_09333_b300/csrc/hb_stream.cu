@@ -51,7 +51,8 @@ struct RoundArgs {
   // round
   RoundCtl* ctl;
   uint32_t max_msgs;
-  uint8_t* staging;
+  uint8_t* staging;              // nullptr: hash in place from the sources
+  uint64_t in_place_base;        // in place: offsets are relative to this address
   uint64_t staging_bytes;
   uint32_t segment_bytes[4];     // per algorithm code (index 3: unknown codes)
   uint8_t* b_algs;
@@ -131,7 +132,8 @@ __global__ void __launch_bounds__(kClaimThreads) hb_round_claim_kernel(RoundArgs
       const uint64_t i = old_cnt + __popc(mask & ((1u << lane) - 1u));
       const uint64_t off = old_bytes + incl - b16;
       r.b_algs[i] = r.alg[k];
-      r.b_offsets[i] = off;
+      // staged: offset into the staging area; in place: the source itself
+      r.b_offsets[i] = r.staging ? off : ld_cg_u64(r.src + k) + prior - r.in_place_base;
       r.b_lengths[i] = (uint32_t)seg;
       r.b_seg[i] = prior | (more ? HB_SEG_MORE : 0ull);
       r.b_slot[i] = (uint32_t)k;
@@ -255,7 +257,7 @@ int hash_round_create(const hb_ring* ring, uint32_t max_msgs, uint8_t* staging,
                       uint64_t staging_bytes, const uint32_t* segment_bytes, int shape_index,
                       int warps_per_sm, hb_round** round_out) {
   using namespace hb;
-  if (!ring || !staging || !round_out || !segment_bytes) return HB_ERR_NULL;
+  if (!ring || !round_out || !segment_bytes) return HB_ERR_NULL;
   *round_out = nullptr;
   if (!ring->src || !ring->prior || !ring->len || !ring->req || !ring->alg || !ring->state ||
       !ring->slots || !ring->req_remaining || !ring->req_done)
@@ -305,6 +307,7 @@ int hash_round_create(const hb_ring* ring, uint32_t max_msgs, uint8_t* staging,
   a.status = status;
   a.max_msgs = max_msgs;
   a.staging = staging;
+  a.in_place_base = reinterpret_cast<uint64_t>(ring->slots);
   a.staging_bytes = staging_bytes;
   for (int i = 0; i < 3; ++i) a.segment_bytes[i] = segment_bytes[i];
   a.segment_bytes[3] = *std::max_element(segment_bytes, segment_bytes + 3);
@@ -343,7 +346,9 @@ int hash_round_create(const hb_ring* ring, uint32_t max_msgs, uint8_t* staging,
   m.perm = reinterpret_cast<uint32_t*>(static_cast<char*>(p->ws) + sizeof(MixedWorkspace));
   m.slot_index = a.b_slot;
   KernelArgs k{};
-  k.packed = staging;
+  // in place, any valid device address serves as the base (message
+  // addresses are base + offset; the base also feeds zero-byte copies)
+  k.packed = staging ? staging : ring->slots;
   k.offsets = a.b_offsets;
   k.lengths = a.b_lengths;
   k.algs = a.b_algs;
@@ -368,7 +373,7 @@ int hash_round_create(const hb_ring* ring, uint32_t max_msgs, uint8_t* staging,
   if (e == cudaSuccess) e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
     hb_round_claim_kernel<<<elem_grid, kClaimThreads, 0, s>>>(a);
-    hb_round_copy_kernel<<<elem_grid, 256, 0, s>>>(a.b_copies, p->ctl);
+    if (staging) hb_round_copy_kernel<<<elem_grid, 256, 0, s>>>(a.b_copies, p->ctl);
     cudaError_t e1 = launch_bucketing(m, elem_grid, s);
     if (e1 == cudaSuccess) e1 = launch_hash(true, 0, shape_index, hash_grid, k, s);
     hb_round_advance_kernel<<<elem_grid, 256, 0, s>>>(a);

@@ -23,6 +23,10 @@ Rounds run concurrently on their streams, so the copies and the hashing of
 different rounds overlap, and a message's next segment goes to whichever
 round is free next.
 
+With `in_place=True` a round skips the copy and hashes each segment where
+the client's bytes are; the staging budget then only caps the bytes the
+rounds have claimed at a time (the server owns no copy of the payload).
+
 Host side (this module, plain Python): admission in arrival order while the
 ring and the request table have room (`RingBook`), one batch of metadata
 copies per loop for the newly admitted requests, round launches, and the
@@ -140,12 +144,13 @@ class Server:
 
     # Segments per algorithm (MD5, SHA-1, SM3): about the same chain time each
     # (an SM3 block costs about three MD5 blocks and two SHA-1 blocks).
-    DEFAULT_SEGMENTS = (192 << 10, 128 << 10, 64 << 10)
+    DEFAULT_SEGMENTS = (96 << 10, 64 << 10, 32 << 10)
 
-    def __init__(self, pool, budget: int = 8 << 30, rounds: int = 8,
+    def __init__(self, pool, budget: int = 8 << 30, rounds: int = 2,
                  segment_bytes=DEFAULT_SEGMENTS, max_msgs: int = 1 << 17,
                  capacity: int = 1 << 21, req_capacity: int = 1 << 14,
-                 shape: int = 11, warps_per_sm: int = 8, device="cuda"):
+                 shape: int = 11, warps_per_sm: int = 8, in_place: bool = True,
+                 device="cuda"):
         import torch
         from . import api
         self.torch, self.api, self.device = torch, api, device
@@ -177,8 +182,11 @@ class Server:
             "req_done": torch.zeros(req_capacity, dtype=torch.int32).pin_memory(),
         }
         self.done_np = self.ring["req_done"].numpy()
-        self.staging = torch.empty(staging_total, dtype=torch.uint8, device=dev)
-        self.slots = [_RoundSlot(self, self.staging[i * self.staging_per_round:],
+        # in place: segments are hashed where the client's bytes are, and the
+        # same byte budget only caps what the rounds claim at a time
+        self.in_place = in_place
+        self.staging = None if in_place else torch.empty(staging_total, dtype=torch.uint8, device=dev)
+        self.slots = [_RoundSlot(self, None if in_place else self.staging[i * self.staging_per_round:],
                                  self.staging_per_round) for i in range(rounds)]
         # host staging of admissions (pinned; reused once the last admission's
         # copies have finished)

@@ -44,7 +44,8 @@ def _ring(api, cap, req_cap):
     }
 
 
-def test_rounds_hash_a_ring_segment_by_segment(env, oracle_mod):
+@pytest.mark.parametrize("in_place", [False, True])
+def test_rounds_hash_a_ring_segment_by_segment(env, oracle_mod, in_place):
     api, serve, pool_host, pool_dev, pool_bytes = env
     n, per_req = 700, 10
     b = workloads.ragged(n, seed=81, max_len=9000, boundary_frac=0.05)
@@ -61,8 +62,8 @@ def test_rounds_hash_a_ring_segment_by_segment(env, oracle_mod):
     ring["state"][:n] = api.RING_READY
     staging = torch.empty(64 << 10, dtype=torch.uint8, device="cuda")
     seg = 512
-    rounds = [api.Round(ring, 300, staging[i * (32 << 10):], 32 << 10, seg, shape=16)
-              for i in range(2)]
+    rounds = [api.Round(ring, 300, None if in_place else staging[i * (32 << 10):], 32 << 10, seg,
+                        shape=16) for i in range(2)]
     streams = [torch.cuda.Stream() for _ in rounds]
     torch.cuda.synchronize()
     expect = int(sum(max(1, -(-int(L) // seg)) for L in b.lengths))
@@ -119,20 +120,33 @@ def _check_requests(api, oracle_mod, reqs, pool_host, oracle_every=3):
             assert np.array_equal(req.digests, alone[:m].cpu().numpy()), req.rid
 
 
-def test_served_digests_equal_oracle(env, oracle_mod):
+def test_served_through_staging_digests_equal_oracle(env, oracle_mod):
     api, serve, pool_host, pool_dev, pool_bytes = env
     reqs = serve.make_requests(120, 3000.0, seed=5, pool_bytes=pool_bytes, max_msgs=64,
                                max_len=1 << 16)
     srv = serve.Server(pool_dev, budget=256 << 20, rounds=3, segment_bytes=4096,
                        max_msgs=4096, capacity=1 << 14, req_capacity=256, shape=16,
-                       warps_per_sm=8)
+                       warps_per_sm=8, in_place=False)
     srv.run(reqs, keep_digests=True)
     srv.close()
+    assert srv.staging is not None
     assert srv.segments > sum(r.lengths.shape[0] for r in reqs)   # long messages were cut
     _check_requests(api, oracle_mod, reqs, pool_host)
     stats = serve.latency_stats(reqs)
     assert stats["completed"] == len(reqs) and stats["p99_ms"] >= stats["p50_ms"] > 0
     assert api.device_status() == 0
+
+
+def test_served_in_place_digests_equal_oracle(env, oracle_mod):
+    api, serve, pool_host, pool_dev, pool_bytes = env
+    reqs = serve.make_requests(60, 3000.0, seed=9, pool_bytes=pool_bytes, max_msgs=64,
+                               max_len=1 << 16)
+    srv = serve.Server(pool_dev, budget=128 << 20, rounds=2, segment_bytes=(12288, 8192, 4096),
+                       max_msgs=4096, capacity=1 << 14, req_capacity=256, in_place=True)
+    srv.run(reqs, keep_digests=True)
+    srv.close()
+    assert srv.staging is None
+    _check_requests(api, oracle_mod, reqs, pool_host, oracle_every=2)
 
 
 def test_small_ring_makes_admission_wait_and_reuses_entries(env, oracle_mod):
