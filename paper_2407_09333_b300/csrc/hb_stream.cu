@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(kClaimThreads) hb_round_claim_kernel(RoundArgs
     bool more = false;
     if (claimed) {
       prior = ld_cg_u64(r.prior + k);
-      const uint32_t code = r.alg[k];
+      const uint32_t code = __ldcg(r.alg + k);
       const uint64_t S = r.segment_bytes[code < 3u ? code : 3u];
       const uint64_t rem = (uint64_t)ld_cg_u32(r.len + k) - prior;
       more = rem > S;
@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(kClaimThreads) hb_round_claim_kernel(RoundArgs
     if (claimed) {
       const uint64_t i = old_cnt + __popc(mask & ((1u << lane) - 1u));
       const uint64_t off = old_bytes + incl - b16;
-      r.b_algs[i] = r.alg[k];
+      r.b_algs[i] = (uint8_t)__ldcg(r.alg + k);
       // staged: offset into the staging area; in place: the source itself
       r.b_offsets[i] = r.staging ? off : ld_cg_u64(r.src + k) + prior - r.in_place_base;
       r.b_lengths[i] = (uint32_t)seg;
@@ -200,7 +200,7 @@ __global__ void hb_round_advance_kernel(RoundArgs r) {
       atomicExch(r.state + k, HB_RING_READY);
     } else {
       atomicExch(r.state + k, HB_RING_FREE);
-      const uint32_t q = r.req[k];
+      const uint32_t q = ld_cg_u32(r.req + k);
       if (q >= r.req_capacity) {  // a request index outside the table: report, skip
         atomicOr(r.status, HB_DEV_BOUNDS);
       } else if (atomicSub(r.req_remaining + q, 1u) == 1u) {

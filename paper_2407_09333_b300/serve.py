@@ -274,6 +274,12 @@ class Server:
                     pending.popleft()
                     rejected += 1
                     continue
+                if m == 0:                      # nothing to hash: done on arrival
+                    pending.popleft()
+                    r.admitted = r.done = now
+                    r.digests = np.zeros((0, 32), np.uint8) if keep_digests else None
+                    finished += 1
+                    continue
                 if not book.fits(m):
                     break
                 pending.popleft()
