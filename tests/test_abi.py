@@ -93,3 +93,34 @@ def test_product_path_does_not_import_oracle():
                 text = open(os.path.join(root, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "hash_oracle" not in text and "liboracle" not in text, f
+
+
+def test_segment_and_round_argument_checks(lib):
+    buf = ctypes.create_string_buffer(256)
+    p = ctypes.c_void_p((ctypes.addressof(buf) + 15) & ~15)
+    # segments: empty batch, missing descriptors, missing buffers
+    assert lib.hash_batch_segments(None, None, None, None, None, None, 0, None, None) == 0
+    assert lib.hash_batch_segments(p, p, p, p, None, None, 1, p, None) == -2
+    assert lib.hash_batch_segments(p, None, p, p, p, None, 1, p, None) == -2
+    assert lib.hash_batch_segments(p, p, p, p, p, None, 1 << 31, p, None) == -3
+    assert lib.hash_plan_set_segments(None, p, None) == -2
+    # rounds: every check below returns before any CUDA call
+    seg = (ctypes.c_uint32 * 3)(64, 64, 64)
+    h = ctypes.c_void_p()
+    assert lib.hash_round_create(None, 16, p, 4096, seg, -1, 0, ctypes.byref(h)) == -2
+    ring = api.HbRing(64, p, p, p, p, p, p, p, p, p, 4)
+    assert lib.hash_round_create(ctypes.byref(ring), 16, p, 4096, None, -1, 0, ctypes.byref(h)) == -2
+    bad = api.HbRing(48, p, p, p, p, p, p, p, p, p, 4)           # not a power of two
+    assert lib.hash_round_create(ctypes.byref(bad), 16, p, 4096, seg, -1, 0, ctypes.byref(h)) == -10
+    nul = api.HbRing(64, p, p, p, p, p, None, p, p, p, 4)        # no state array
+    assert lib.hash_round_create(ctypes.byref(nul), 16, p, 4096, seg, -1, 0, ctypes.byref(h)) == -2
+    assert lib.hash_round_create(ctypes.byref(ring), 1 << 23, p, 4096, seg, -1, 0,
+                                 ctypes.byref(h)) == -3
+    odd = (ctypes.c_uint32 * 3)(64, 100, 64)                     # not a multiple of 64
+    assert lib.hash_round_create(ctypes.byref(ring), 16, p, 4096, odd, -1, 0, ctypes.byref(h)) == -10
+    mis = ctypes.c_void_p(p.value + 4)                           # staging not 16-byte aligned
+    assert lib.hash_round_create(ctypes.byref(ring), 16, mis, 4096, seg, -1, 0, ctypes.byref(h)) == -7
+    assert lib.hash_round_create(ctypes.byref(ring), 16, p, 4096, seg, 999, 0, ctypes.byref(h)) == -10
+    assert lib.hash_round_launch(None, 0, 0, None) == -2
+    assert lib.hash_round_report(None, None, None) == -2
+    assert lib.hash_round_destroy(None) == 0
