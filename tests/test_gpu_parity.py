@@ -150,6 +150,23 @@ def test_mixed_matches_single_algorithm_path(hb):
 # ---------------------------------------------------------------------------
 # host-buffer path, bounds, failure detection
 
+def test_standard_example_inputs(hb, oracle_mod):
+    # ASCII inputs of the kind the standards' worked examples use, packed
+    # back to back at odd offsets (expected slots from the oracle)
+    alpha = "abcdefghijklmnopqrstuvwxyz"
+    msgs = [b"", b"a", b"abc", b"message digest", alpha.encode(),
+            (alpha.upper() + alpha + "0123456789").encode(),
+            "".join(alpha[i:i + 4] for i in range(14)).encode(),
+            "".join(alpha[i:i + 8] for i in range(14)).encode(),
+            b"abcd" * 16, b"1234567890" * 8, b"a" * 1_000_000]
+    packed = np.frombuffer(b"x" + b"".join(msgs) + b"x" * 16, dtype=np.uint8).copy()
+    lengths = np.array([len(m) for m in msgs], dtype=np.uint32)
+    offsets = (1 + np.concatenate([[0], np.cumsum(lengths)[:-1]])).astype(np.uint64)
+    b = workloads.Batch(packed, offsets, lengths, None)
+    for alg in ALGS:
+        _assert_slots_equal(_gpu_slots(hb, b, alg), _oracle_slots(oracle_mod, b, alg), "examples")
+
+
 def test_host_path_plain_and_mixed(hb, oracle_mod):
     b = workloads.scattered(np.arange(0, 400), seed=4, overlap=True, mixed=True)
     out = np.zeros((b.n, 32), dtype=np.uint8)

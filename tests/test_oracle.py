@@ -57,6 +57,23 @@ def test_constant_bytes_match_hashlib(oracle_mod, alg):
 
 
 @pytest.mark.parametrize("alg", [0, 1, 2])
+def test_standard_example_inputs_match_hashlib(oracle_mod, alg):
+    # the kinds of input the standards' worked examples use: short ASCII
+    # strings, the 56- and 112-byte alphabet runs that end exactly where
+    # padding needs a second block, a 64-byte repeated pattern and a million
+    # repeated bytes; expected digests come from hashlib, not from a table
+    alpha = "abcdefghijklmnopqrstuvwxyz"
+    msgs = [b"", b"a", b"abc", b"message digest", alpha.encode(),
+            (alpha.upper() + alpha + "0123456789").encode(),
+            "".join(alpha[i:i + 4] for i in range(14)).encode(),
+            "".join(alpha[i:i + 8] for i in range(14)).encode(),
+            b"abcd" * 16, b"1234567890" * 8, b"a" * 1_000_000]
+    assert len(msgs[6]) == 56 and len(msgs[7]) == 112
+    for m in msgs:
+        assert oracle_mod.digest(alg, m) == hashlib.new(NAMES[alg], m).digest(), m[:16]
+
+
+@pytest.mark.parametrize("alg", [0, 1, 2])
 def test_paper_nine_digit_messages_match_hashlib(oracle_mod, alg):
     # the paper's message shape (Sec. V-A.2): 9 characters over {0-9}
     b = workloads.digits9(200, first=123_456_700)
