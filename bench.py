@@ -381,7 +381,18 @@ def run_ours(args, dist):
         torch.cuda.set_device(dist.local_rank)
     build.build()
     api.lib()
-    desc, batch, mixed = make_workload(args.workload, dist.rank, args.messages)
+    if args.scaling == "strong":
+        # one batch for the whole job; each rank hashes its range, split by
+        # estimated work (padded blocks x ops per block)
+        from paper_2407_09333_b300 import shard
+        desc, full, mixed = make_workload(args.workload, 0, args.messages)
+        lo, hi = shard.rank_range(full.lengths, full.algs, alg=None if mixed else 2,
+                                  rank=dist.rank, world=dist.world)
+        batch = workloads.Batch(full.packed, full.offsets[lo:hi], full.lengths[lo:hi],
+                                full.algs[lo:hi] if full.algs is not None else None)
+        desc += "; strong scaling: rank %d hashes messages [%d, %d) of %d" % (dist.rank, lo, hi, full.n)
+    else:
+        desc, batch, mixed = make_workload(args.workload, dist.rank, args.messages)
     packed, off, ln, algs = api.to_device(batch)
     n = batch.n
     out = torch.empty((n, 32), dtype=torch.uint8, device="cuda")
@@ -505,7 +516,7 @@ def run_ours(args, dist):
     line = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": dist.world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "higher_is_better": True, "scaling": args.scaling, "vs_baseline": None, "dtype": "u32",
         "data": "synthetic: uniform random bytes (numpy PCG64), shard seed per rank",
         "config": {"workload": desc, "messages_per_gpu": n, "bytes_per_gpu": batch.total_bytes,
                    "l2": "no flush: inputs larger than the 126 MB L2",
@@ -767,6 +778,9 @@ def main(argv=None):
                    help="fixed ragged bucketing 'sub_log2,alg_major' (with --shape)")
     p.add_argument("--messages", type=int, default=0,
                    help="message count of the ragged workload (default 2^20); smaller for profiling")
+    p.add_argument("--scaling", default="weak", choices=["weak", "strong"],
+                   help="weak: every rank hashes its own batch; strong: the ranks split one batch "
+                        "by estimated work")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--int-peak", action="store_true",
