@@ -237,6 +237,11 @@ def job_rate(dist, local_units: float, local_seconds: float) -> float:
 # workloads
 
 def make_workload(name: str, rank: int, messages: int = 0):
+    if name == "paper":
+        # the strings the device generates, laid out in memory (CPU reference arm)
+        n = messages or (1 << 22)
+        return ("paper: nine-digit decimal strings %d .. %d, MD5 + SHA-1 + SM3" % (0, n - 1),
+                workloads.digits9(n), False)
     if name == "c3" and messages:
         return ("ragged mixed-algorithm batch: %d messages, log-uniform lengths in [0, 64 KiB], "
                 "1%% at padding boundaries, algorithm per message" % messages,
@@ -720,6 +725,80 @@ def run_serve(args, dist):
         print(json.dumps(line), flush=True)
 
 
+def run_paper(args, dist):
+    """The paper's workload (Sec. V-A.2) generated on the device: every
+    9-character decimal string "000000000" .. "999999999" hashed with each of
+    MD5, SHA-1 and SM3 per step, the 10^9 strings split evenly across ranks."""
+    import torch
+    from paper_2407_09333_b300 import api, build
+
+    if torch.cuda.is_available():
+        torch.cuda.set_device(dist.local_rank)
+    build.build()
+    total = api.DIGITS_COUNT
+    per = (total + dist.world - 1) // dist.world
+    first = dist.rank * per
+    count = max(0, min(per, total - first))
+    out = torch.empty((max(count, 1), 32), dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    launches = [(a, (lambda a=a: api.hash_digits(a, first, count, out=out))) for a in (0, 1, 2)]
+    for _ in range(args.warmup):
+        for _, fn in launches:
+            fn()
+    torch.cuda.synchronize()
+    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in launches] for _ in range(args.steps)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clocks:
+        t0.record(stream)
+        for k in range(args.steps):
+            for j, (_, fn) in enumerate(launches):
+                ev[k][j][0].record(stream)
+                fn()
+                ev[k][j][1].record(stream)
+        t1.record(stream)
+        torch.cuda.synchronize()
+    dist.barrier()
+    ms = dist.max(t0.elapsed_time(t1))
+    job_msgs = dist.sum(float(3 * count * args.steps))
+    peaks = load_peaks()
+    clk = clocks.summary()
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    peak = alu_peak_tops(sms, peaks["sm_max_mhz"])
+    per_alg = {}
+    for j, (a, _) in enumerate(launches):
+        t = statistics.median([ev[k][j][0].elapsed_time(ev[k][j][1]) for k in range(args.steps)]) * 1e-3
+        ops = float(count) * OPS_PER_BLOCK[a]
+        per_alg[ALG_NAMES[a]] = {"Mhash/s": count / t / 1e6, "GB/s": 9 * count / t / 1e9, "ms": t * 1e3,
+                                 "s_for_1e9": t * total / max(count, 1), "alu_Tops": ops / t / 1e12,
+                                 "alu_frac": ops / t / 1e12 / peak}
+    dom = max(per_alg, key=lambda k: per_alg[k]["ms"])
+    line = {
+        "metric": METRIC, "value": job_msgs * 9 / (ms * 1e-3) / 1e9, "unit": "GB/s",
+        "n_gpus": dist.world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "strong",
+        "vs_baseline": None, "dtype": "u32",
+        "data": "generated on the device: the 10^9 nine-character decimal strings (no input bytes)",
+        "config": {"workload": "paper: all 10^9 nine-digit decimal strings, MD5 + SHA-1 + SM3 per step",
+                   "messages_per_gpu": count, "l2": "no inputs; 32 GB of digest slots per launch"},
+        "mhash_per_s": job_msgs / (ms * 1e-3) / 1e6,
+        "per_alg": per_alg,
+        "roofline": {"bound": "alu", "kernel": "hb_digits_kernel<%s>" % dom,
+                     "achieved": per_alg[dom]["alu_Tops"], "peak": peak, "unit": "Tops/s",
+                     "frac": per_alg[dom]["alu_frac"],
+                     "peak_source": "derived: %d SMs x 4 sub-partitions x 32 lanes x %.0f MHz max SM clock"
+                                    % (sms, peaks["sm_max_mhz"]),
+                     "traffic": None},
+        "e2e": None, "e2e_note": "no input bytes: the strings are generated on the device",
+        "gpu_launches": 3 * args.steps,
+        "clocks": clk,
+    }
+    if dist.rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_int_peak(args, dist):
     """K5: sustained 32-bit operations per clock per SM for each op class."""
     import torch
@@ -756,7 +835,7 @@ def main(argv=None):
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=2000)
     p.add_argument("--warmup", type=int, default=5)
-    p.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5"])
+    p.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "paper"])
     p.add_argument("--requests", type=int, default=20000, help="requests per load point (c5)")
     p.add_argument("--loads", type=float, nargs="+", default=[0.1, 0.3, 0.5, 0.7, 0.9, 1.1],
                    help="offered loads as fractions of the ragged path's throughput (c5)")
@@ -794,6 +873,8 @@ def main(argv=None):
             run_int_peak(args, dist)
         elif args.workload == "c5" and args.impl == "ours":
             run_serve(args, dist)
+        elif args.workload == "paper" and args.impl == "ours":
+            run_paper(args, dist)
         elif args.impl == "reference":
             run_reference(args, dist)
         else:

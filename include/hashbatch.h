@@ -321,6 +321,19 @@ int hash_round_report(hb_round *round, uint64_t *segments, uint64_t *bytes);
 int hash_round_destroy(hb_round *round);
 
 /*
+ * hash_digits -- the paper's workload generated on the device (Sec. V-A.2):
+ * message i is the 9-character decimal string of i with leading zeros
+ * ("000000000" .. "999999999"); digests_out[k] (32-byte slot) receives the
+ * digest of message first + k, for k < count.  No input bytes are read: the
+ * strings are built in registers.  first + count <= HB_DIGITS_COUNT (10^9);
+ * digests_out is a device array of count slots, 16-byte aligned.
+ * Returns HB_OK, HB_ERR_INVALID_ALG, HB_ERR_TOO_LARGE, HB_ERR_NULL,
+ * HB_ERR_ALIGN or HB_ERR_CUDA.
+ */
+#define HB_DIGITS_COUNT 1000000000ull
+int hash_digits(int alg, uint64_t first, uint64_t count, uint8_t *digests_out, void *stream);
+
+/*
  * hash_batch_check_bounds -- checks on the device that every message lies in
  * [0, packed_len): offsets[i] + lengths[i] <= packed_len, computed without
  * overflow.  Writes 0 to *status_dev when all messages are in bounds, else

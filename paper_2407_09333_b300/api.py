@@ -65,6 +65,7 @@ _SIGNATURES = {
     "hash_plan_set_completion": (_c_int, [_vp, _vp, _vp, _vp]),
     "hash_plan_set_segments": (_c_int, [_vp, _vp, _vp]),
     "hash_gather": (_c_int, [_vp, _c_u32, _vp]),
+    "hash_digits": (_c_int, [_c_int, _c_u64, _c_u64, _vp, _vp]),
     "hash_round_create": (_c_int, [_vp, _c_u32, _vp, _c_u64, ctypes.POINTER(_c_u32), _c_int,
                                    _c_int, ctypes.POINTER(_vp)]),
     "hash_round_launch": (_c_int, [_vp, _c_u64, _c_u64, _vp]),
@@ -251,6 +252,19 @@ def hash_batch_mixed_noalloc(algs, packed, offsets, lengths, out, stream=None):
         _dev_ptr(offsets, 8, "offsets"), _dev_ptr(lengths, 4, "lengths"), n,
         _dev_ptr(out, 1, "out"), _stream_handle(stream))
     _check(rc, "hash_batch_mixed_noalloc")
+    return out
+
+
+DIGITS_COUNT = 10 ** 9
+
+
+def hash_digits(alg: int, first: int, count: int, out=None, stream=None):
+    """Digest slots (count, 32) of the 9-character decimal strings of
+    first .. first + count - 1, generated on the device."""
+    torch = _torch()
+    out = _out_tensor(out, int(count), "cuda")
+    _check(lib().hash_digits(int(alg), int(first), int(count), _dev_ptr(out, 1, "out"),
+                             _stream_handle(stream)), "hash_digits")
     return out
 
 

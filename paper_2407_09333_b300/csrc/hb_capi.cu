@@ -512,6 +512,23 @@ int hash_batch_host(int alg, const uint8_t* algs_host, const uint8_t* packed_hos
   return HB_OK;
 }
 
+int hash_digits(int alg, uint64_t first, uint64_t count, uint8_t* digests_out, void* stream) {
+  if (hash_digest_size(alg) == 0) return HB_ERR_INVALID_ALG;
+  if (count == 0) return HB_OK;
+  if (first >= HB_DIGITS_COUNT || count > HB_DIGITS_COUNT - first) return HB_ERR_TOO_LARGE;
+  if (!digests_out) return HB_ERR_NULL;
+  if (reinterpret_cast<uintptr_t>(digests_out) & 15u) return HB_ERR_ALIGN;
+  Ctx* c = nullptr;
+  int rc = get_ctx(&c);
+  if (rc) return rc;
+  const uint64_t runs = (first + count + 9) / 10 - first / 10;
+  const uint64_t need = (runs + 255) / 256;
+  const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(need, (uint64_t)c->sms * 8));
+  cudaError_t e = hb::launch_digits(alg, first, count, digests_out, grid,
+                                    static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? HB_OK : cuda_fail(e);
+}
+
 int hash_device_status(void* stream, int* status_out) {
   if (!status_out) return HB_ERR_NULL;
   Ctx* c = nullptr;

@@ -144,6 +144,72 @@ __global__ void __launch_bounds__(WARPS * 32) hb_mixed_kernel(KernelArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// The paper's workload, generated on the device (Sec. V-A.2): message i is
+// the 9-character decimal string of i with leading zeros, "000000000" ..
+// "999999999", built in registers -- no input bytes are read.  Each string
+// is one padded block: 9 characters, 0x80, zeros, the bit length 72.  A
+// thread hashes the ten strings 10q .. 10q+9, which share their first eight
+// characters, so the digits of q are worked out once per ten messages.
+
+template <int ALG>
+__global__ void __launch_bounds__(256) hb_digits_kernel(uint64_t first, uint64_t count,
+                                                        uint8_t* digests, MulConsts mc) {
+  constexpr bool BE = AlgTraits<ALG>::kBigEndian;
+  const uint64_t end = first + count;
+  const uint64_t q_end = (end + 9) / 10;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t q = first / 10 + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < q_end;
+       q += stride) {
+    uint32_t c[8];  // characters of q, most significant first
+    uint32_t v = (uint32_t)q;
+#pragma unroll
+    for (int k = 7; k >= 0; --k) {
+      c[k] = '0' + v % 10u;
+      v /= 10u;
+    }
+    uint32_t w[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) w[k] = 0u;
+    if (BE) {
+      w[0] = (c[0] << 24) | (c[1] << 16) | (c[2] << 8) | c[3];
+      w[1] = (c[4] << 24) | (c[5] << 16) | (c[6] << 8) | c[7];
+      w[15] = 72u;
+    } else {
+      w[0] = c[0] | (c[1] << 8) | (c[2] << 16) | (c[3] << 24);
+      w[1] = c[4] | (c[5] << 8) | (c[6] << 16) | (c[7] << 24);
+      w[14] = 72u;
+    }
+#pragma unroll 1
+    for (uint32_t d = 0; d < 10; ++d) {
+      const uint64_t i = q * 10 + d;
+      if (i < first || i >= end) continue;
+      const uint32_t ch = '0' + d;
+      w[2] = BE ? ((ch << 24) | (0x80u << 16)) : (ch | (0x80u << 8));
+      uint32_t st[8];
+      alg_init<ALG>(st);
+      alg_compress<ALG>(st, w, mc);
+      uint32_t o[8];
+      alg_digest_words<ALG>(st, o);
+      uint8_t* dst = digests + (i - first) * HB_SLOT_BYTES;
+      stg128_cs(dst, o[0], o[1], o[2], o[3]);
+      stg128_cs(dst + 16, o[4], o[5], o[6], o[7]);
+    }
+  }
+}
+
+cudaError_t launch_digits(int alg, uint64_t first, uint64_t count, uint8_t* digests, int grid,
+                          cudaStream_t stream) {
+  const MulConsts mc = make_mul_consts();
+  switch (alg) {
+    case HB_MD5: hb_digits_kernel<HB_MD5><<<grid, 256, 0, stream>>>(first, count, digests, mc); break;
+    case HB_SHA1: hb_digits_kernel<HB_SHA1><<<grid, 256, 0, stream>>>(first, count, digests, mc); break;
+    case HB_SM3: hb_digits_kernel<HB_SM3><<<grid, 256, 0, stream>>>(first, count, digests, mc); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // Bounds check (never traps; reports through status words).
 
 __global__ void hb_bounds_kernel(const uint64_t* offsets, const uint32_t* lengths, uint64_t n,

@@ -121,6 +121,9 @@ cudaError_t launch_bucketing(const MixedArgs& m, int grid, cudaStream_t stream);
 cudaError_t launch_bounds(const uint64_t* offsets, const uint32_t* lengths, uint64_t n,
                           uint64_t packed_len, int* status_dev, int* ctx_status, int grid,
                           cudaStream_t stream);
+// Digests of the 9-character decimal strings of first .. first + count - 1.
+cudaError_t launch_digits(int alg, uint64_t first, uint64_t count, uint8_t* digests, int grid,
+                          cudaStream_t stream);
 // flag = 1 when offsets[i] + lengths[i] decreases anywhere in index order.
 cudaError_t launch_monotone(const uint64_t* offsets, const uint32_t* lengths, uint64_t n, int* flag,
                             int grid, cudaStream_t stream);

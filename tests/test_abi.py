@@ -124,3 +124,14 @@ def test_segment_and_round_argument_checks(lib):
     assert lib.hash_round_launch(None, 0, 0, None) == -2
     assert lib.hash_round_report(None, None, None) == -2
     assert lib.hash_round_destroy(None) == 0
+
+
+def test_digits_argument_checks(lib):
+    buf = ctypes.create_string_buffer(64)
+    p = ctypes.c_void_p((ctypes.addressof(buf) + 15) & ~15)
+    assert lib.hash_digits(3, 0, 1, p, None) == -1
+    assert lib.hash_digits(0, 0, 0, None, None) == 0
+    assert lib.hash_digits(0, 10 ** 9, 1, p, None) == -3
+    assert lib.hash_digits(0, 10 ** 9 - 1, 2, p, None) == -3
+    assert lib.hash_digits(0, 0, 1, None, None) == -2
+    assert lib.hash_digits(0, 0, 1, ctypes.c_void_p(p.value + 4), None) == -7

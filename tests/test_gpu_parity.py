@@ -167,6 +167,26 @@ def test_standard_example_inputs(hb, oracle_mod):
         _assert_slots_equal(_gpu_slots(hb, b, alg), _oracle_slots(oracle_mod, b, alg), "examples")
 
 
+@pytest.mark.parametrize("first,count", [(0, 1000), (77, 33), (123_456_703, 4_999),
+                                         (999_999_000, 1000), (5, 1)])
+def test_on_device_nine_digit_strings(hb, oracle_mod, first, count):
+    # the paper's workload generated on the device, against the oracle over
+    # the same strings laid out in memory
+    b = workloads.digits9(count, first=first)
+    for alg in ALGS:
+        got = hb.hash_digits(alg, first, count).cpu().numpy()
+        _assert_slots_equal(got, _oracle_slots(oracle_mod, b, alg), "digits %d+%d" % (first, count))
+
+
+def test_on_device_nine_digit_limits(hb):
+    with pytest.raises(hb.HashBatchError) as e:
+        hb.hash_digits(0, hb.DIGITS_COUNT - 5, 6)
+    assert e.value.code == -3
+    with pytest.raises(hb.HashBatchError) as e:
+        hb.hash_digits(3, 0, 10)
+    assert e.value.code == -1
+
+
 def test_host_path_plain_and_mixed(hb, oracle_mod):
     b = workloads.scattered(np.arange(0, 400), seed=4, overlap=True, mixed=True)
     out = np.zeros((b.n, 32), dtype=np.uint8)
