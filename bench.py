@@ -567,6 +567,16 @@ def e2e_measure(args, batch, mixed, api, torch, dist):
         for a in calls:
             api.hash_batch_host(a, packed_h, off_h, len_h, out_h, algs=algs_h)
 
+    if args.host_limit_mib:
+        api.set_host_memory_limit(args.host_limit_mib << 20)
+        try:
+            step()
+        except api.HashBatchError as e:
+            api.set_host_memory_limit(0)
+            return {"value": None, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
+                    "device_memory_limit_bytes": args.host_limit_mib << 20,
+                    "error": "%s (windows need messages in memory order)" % e}
+
     steps = max(1, min(args.steps, args.e2e_steps))
     for _ in range(max(1, min(args.warmup, 3))):
         step()
@@ -579,7 +589,10 @@ def e2e_measure(args, batch, mixed, api, torch, dist):
     dt = time.perf_counter() - t0
     dist.barrier()
     per_call_in = batch.packed.nbytes + 12 * n + (n if mixed else 0)
+    if args.host_limit_mib:
+        api.set_host_memory_limit(0)
     return {"value": job_rate(dist, len(calls) * batch.total_bytes * steps, dt) / 1e9, "unit": "GB/s",
+            "device_memory_limit_bytes": args.host_limit_mib << 20,
             "h2d_bytes_per_step": len(calls) * per_call_in,
             "d2h_bytes_per_step": len(calls) * 32 * n, "steps": steps,
             "api": "hash_batch_host (pinned host buffers)"}
@@ -860,6 +873,8 @@ def main(argv=None):
     p.add_argument("--scaling", default="weak", choices=["weak", "strong"],
                    help="weak: every rank hashes its own batch; strong: the ranks split one batch "
                         "by estimated work")
+    p.add_argument("--host-limit-mib", type=int, default=0,
+                   help="device memory the e2e host path may use (0 = whole batch on the device)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--int-peak", action="store_true",

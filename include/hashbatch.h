@@ -352,7 +352,19 @@ int hash_batch_check_bounds(const uint64_t *offsets, const uint32_t *lengths, ui
  * are still coming in (two library streams besides `stream`).  This assumes
  * message ends (offset + length) do not decrease with the index, as in any
  * back-to-back layout; a device check confirms it, and otherwise every
- * message is hashed again once all bytes are in (same result, slower).  Host buffers should be pinned (cudaHostAlloc / cudaHostRegister)
+ * message is hashed again once all bytes are in (same result, slower).
+ *
+ * Device memory: by default the call keeps the whole batch on the device.
+ * After hash_set_host_memory_limit(bytes) (0 = no limit, the default),
+ * batches whose device footprint would exceed the limit stream through two
+ * device windows of at most bytes/2 each: consecutive messages whose bytes
+ * and metadata fit a window are copied in, checked, hashed and copied out
+ * while the other window is in flight, so batches larger than the device
+ * (or than a budget) hash at copy speed.  This needs message ends in
+ * non-decreasing index order and no message starting before the end of an
+ * earlier window's last message (back-to-back, gaps allowed); otherwise the
+ * call returns HB_ERR_ARG (HB_ERR_BOUNDS for a message outside packed_len,
+ * HB_ERR_TOO_LARGE for a message that does not fit a window).  Host buffers should be pinned (cudaHostAlloc / cudaHostRegister)
  * for full copy speed; pageable memory works but is slower.  algs_host may be
  * NULL (single `alg`) or a host array of per-message codes (mixed path).
  * After the copies, every message is checked against packed_len on the
@@ -362,6 +374,7 @@ int hash_batch_check_bounds(const uint64_t *offsets, const uint32_t *lengths, ui
  * before reusing them.  Returns as hash_batch / hash_batch_mixed, plus
  * HB_ERR_BOUNDS.
  */
+uint64_t hash_set_host_memory_limit(uint64_t bytes);
 int hash_batch_host(int alg, const uint8_t *algs_host, const uint8_t *packed_host,
                     uint64_t packed_len, const uint64_t *offsets_host,
                     const uint32_t *lengths_host, uint64_t n, uint8_t *digests_host,

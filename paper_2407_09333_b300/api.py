@@ -66,6 +66,7 @@ _SIGNATURES = {
     "hash_plan_set_segments": (_c_int, [_vp, _vp, _vp]),
     "hash_gather": (_c_int, [_vp, _c_u32, _vp]),
     "hash_digits": (_c_int, [_c_int, _c_u64, _c_u64, _vp, _vp]),
+    "hash_set_host_memory_limit": (_c_u64, [_c_u64]),
     "hash_round_create": (_c_int, [_vp, _c_u32, _vp, _c_u64, ctypes.POINTER(_c_u32), _c_int,
                                    _c_int, ctypes.POINTER(_vp)]),
     "hash_round_launch": (_c_int, [_vp, _c_u64, _c_u64, _vp]),
@@ -302,6 +303,12 @@ def hash_batch_host(alg, packed, offsets, lengths, out, algs=None, stream=None):
         _host_ptr(out, "out"), _stream_handle(stream))
     _check(rc, "hash_batch_host")
     return out
+
+
+def set_host_memory_limit(nbytes: int) -> int:
+    """Device bytes hash_batch_host may use (0 = no limit); returns the old
+    value.  Larger batches stream through two windows of nbytes/2."""
+    return int(lib().hash_set_host_memory_limit(int(nbytes)))
 
 
 def device_status(stream=None) -> int:

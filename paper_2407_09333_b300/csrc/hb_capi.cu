@@ -75,11 +75,15 @@ struct Ctx {
   cudaStream_t host_hash = nullptr, host_out = nullptr;
   cudaEvent_t ev_meta = nullptr, ev_end = nullptr;
   cudaEvent_t ev_in[kHostChunks] = {}, ev_hashed[kHostChunks] = {};
+  // windowed host path: two windows, each one device buffer
+  DeviceBuf win[2];
+  cudaEvent_t ev_win_out[2] = {};
 };
 
 std::mutex g_mu;
 Ctx* g_ctx[kMaxDevices] = {};
 uint64_t g_wait_limit_ns = 2000000000ull;
+uint64_t g_host_limit = 0;  // device bytes the host path may use; 0 = no limit
 
 thread_local cudaError_t g_last_cuda_error = cudaSuccess;
 
@@ -376,6 +380,8 @@ int host_streams(Ctx* c) {
     e = cudaEventCreateWithFlags(&c->ev_in[k], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_hashed[k], cudaEventDisableTiming);
   }
+  for (int j = 0; e == cudaSuccess && j < 2; ++j)
+    e = cudaEventCreateWithFlags(&c->ev_win_out[j], cudaEventDisableTiming);
   return e == cudaSuccess ? HB_OK : cuda_fail(e);
 }
 
@@ -400,9 +406,132 @@ int host_hash_range(Ctx* c, int alg, const uint8_t* d_algs, const uint8_t* d_pac
   return launch_plain(c, alg, c->tune_plain[alg], 0, a, s);
 }
 
+// Device bytes a window needs per message: offset, length, algorithm code,
+// digest slot.
+constexpr uint64_t kWinMsgBytes = 8 + 4 + 1 + HB_SLOT_BYTES;
+
+uint64_t align_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
+
+// Batches larger than the host-path limit: windows of consecutive messages
+// whose bytes (from the previous window's last message end to their own last
+// end) and metadata fit half the limit go through two alternating device
+// buffers; copy-in, hashing and copy-out of different windows overlap.
+// Needs message ends in non-decreasing index order with no message starting
+// before the previous window's last end (a back-to-back layout, gaps
+// allowed); each window is checked on the device.
+int host_windowed(Ctx* c, int alg, const uint8_t* algs_host, const uint8_t* packed_host,
+                  uint64_t packed_len, const uint64_t* offsets_host,
+                  const uint32_t* lengths_host, uint64_t n, uint8_t* digests_host,
+                  cudaStream_t s, bool* layout_failed) {
+  *layout_failed = false;
+  const uint64_t B = g_host_limit / 2;  // bytes per window buffer
+  const uint64_t max_msgs = B / (2 * kWinMsgBytes);
+  if (max_msgs == 0) return HB_ERR_TOO_LARGE;
+  auto end_of = [&](uint64_t i) { return offsets_host[i] + lengths_host[i]; };
+  cudaError_t e;
+  for (int j = 0; j < 2; ++j)
+    if ((e = c->win[j].reserve(B)) != cudaSuccess) return cuda_fail(e);
+  if (algs_host) {
+    int rc = reserve_ws(c, max_msgs);
+    if (rc) return rc;
+  }
+  if ((e = c->h_flag.reserve(2 * sizeof(int))) != cudaSuccess) return cuda_fail(e);
+  int* d_flag = static_cast<int*>(c->h_flag.p);
+  cudaStream_t sh = c->host_hash, so = c->host_out;
+  auto fail = [&]() { return cuda_fail(cudaGetLastError()); };
+  if (cudaMemsetAsync(d_flag, 0, 2 * sizeof(int), s) || cudaEventRecord(c->ev_meta, s) ||
+      cudaStreamWaitEvent(sh, c->ev_meta, 0))
+    return fail();
+  uint64_t m = 0, rs = 0;
+  int k = 0;
+  while (m < n) {
+    // largest window [m, m2) whose bytes [rs, end(m2-1)) plus metadata fit B
+    uint64_t lo = m + 1, hi = std::min<uint64_t>(n, m + max_msgs);
+    auto fits = [&](uint64_t x) {
+      const uint64_t re = std::max<uint64_t>(end_of(x - 1), rs);
+      return align_up(re - rs, 256) + kWinMsgBytes * (x - m) + 1024 <= B;
+    };
+    if (!fits(lo)) {
+      // nothing may still be writing the caller's buffers when we return
+      cudaStreamSynchronize(s);
+      cudaStreamSynchronize(sh);
+      cudaStreamSynchronize(so);
+      if (offsets_host[m] > packed_len || lengths_host[m] > packed_len - offsets_host[m])
+        return HB_ERR_BOUNDS;
+      if (align_up(lengths_host[m], 256) + kWinMsgBytes + 1024 > B)
+        return HB_ERR_TOO_LARGE;  // one message larger than a window
+      *layout_failed = true;
+      return HB_ERR_ARG;          // the message lies too far past the previous window
+    }
+    while (lo < hi) {
+      const uint64_t mid = lo + (hi - lo + 1) / 2;
+      if (fits(mid)) lo = mid; else hi = mid - 1;
+    }
+    const uint64_t m2 = lo, cnt = m2 - m;
+    const uint64_t re = std::min<uint64_t>(std::max<uint64_t>(end_of(m2 - 1), rs), packed_len);
+    const int j = k & 1;
+    uint8_t* base = static_cast<uint8_t*>(c->win[j].p);
+    uint8_t* d_packed = base;
+    uint64_t* d_off = reinterpret_cast<uint64_t*>(base + align_up(re - rs + 16, 256));
+    uint32_t* d_len = reinterpret_cast<uint32_t*>(d_off + cnt);
+    uint8_t* d_dig = reinterpret_cast<uint8_t*>(align_up(reinterpret_cast<uint64_t>(d_len + cnt), 256));
+    uint8_t* d_algs = d_dig + cnt * HB_SLOT_BYTES;
+    // this window's buffer is free once the window two back has been copied out
+    if (k >= 2 && cudaStreamWaitEvent(s, c->ev_win_out[j], 0)) return fail();
+    if ((re > rs && cudaMemcpyAsync(d_packed, packed_host + rs, re - rs, cudaMemcpyHostToDevice, s)) ||
+        cudaMemcpyAsync(d_off, offsets_host + m, cnt * sizeof(uint64_t), cudaMemcpyHostToDevice, s) ||
+        cudaMemcpyAsync(d_len, lengths_host + m, cnt * sizeof(uint32_t), cudaMemcpyHostToDevice, s) ||
+        (algs_host && cudaMemcpyAsync(d_algs, algs_host + m, cnt, cudaMemcpyHostToDevice, s)) ||
+        cudaEventRecord(c->ev_in[k % kHostChunks], s) ||
+        cudaStreamWaitEvent(sh, c->ev_in[k % kHostChunks], 0))
+      return fail();
+    const int g = grid_for_elementwise(c, cnt);
+    e = hb::launch_rebase(d_off, cnt, rs, g, sh);
+    if (e == cudaSuccess) e = hb::launch_bounds(d_off, d_len, cnt, re - rs, d_flag, nullptr, g, sh);
+    if (e != cudaSuccess) return cuda_fail(e);
+    int rc = host_hash_range(c, alg, algs_host ? d_algs : nullptr, d_packed, d_off, d_len, 0, cnt,
+                             d_dig, d_flag, sh);
+    if (rc) return rc;
+    if (cudaEventRecord(c->ev_hashed[k % kHostChunks], sh) ||
+        cudaStreamWaitEvent(so, c->ev_hashed[k % kHostChunks], 0) ||
+        cudaMemcpyAsync(digests_host + m * HB_SLOT_BYTES, d_dig, cnt * (size_t)HB_SLOT_BYTES,
+                        cudaMemcpyDeviceToHost, so) ||
+        cudaEventRecord(c->ev_win_out[j], so))
+      return fail();
+    m = m2;
+    rs = re;
+    ++k;
+  }
+  if (cudaMemcpyAsync(c->flag_host, d_flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, so) ||
+      cudaEventRecord(c->ev_end, so) || cudaStreamWaitEvent(s, c->ev_end, 0))
+    return fail();
+  if (algs_host) {
+    if (cudaEventRecord(c->ws_event, sh) != cudaSuccess) return fail();
+    c->ws_used = true;
+  }
+  if (cudaStreamSynchronize(s) != cudaSuccess) return fail();
+  if (c->flag_host[0]) {
+    // a window saw a message outside its bytes: either the message is out of
+    // the buffer (a caller error) or the layout does not stream
+    for (uint64_t i = 0; i < n; ++i)
+      if (offsets_host[i] > packed_len || lengths_host[i] > packed_len - offsets_host[i])
+        return HB_ERR_BOUNDS;
+    *layout_failed = true;
+    return HB_ERR_ARG;
+  }
+  return HB_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
+uint64_t hash_set_host_memory_limit(uint64_t bytes) {
+  std::lock_guard<std::mutex> lock(g_mu);
+  const uint64_t old = g_host_limit;
+  g_host_limit = bytes;
+  return old;
+}
 
 // Pipeline: the caller's stream copies the metadata, then the packed bytes in
 // chunks [b_k, b_k+1); the hashing stream, after the bounds check, hashes the
@@ -430,6 +559,12 @@ int hash_batch_host(int alg, const uint8_t* algs_host, const uint8_t* packed_hos
   // Make sure no earlier call on another stream still uses the buffers.
   if (cudaDeviceSynchronize() != cudaSuccess) return cuda_fail(cudaGetLastError());
   const size_t pbytes = ((size_t)packed_len + 15) / 16 * 16 + 16;
+  const uint64_t footprint = pbytes + n * (kWinMsgBytes + 4);
+  if (g_host_limit && footprint > g_host_limit) {
+    bool layout_failed = false;
+    return host_windowed(c, alg, algs_host, packed_host, packed_len, offsets_host, lengths_host,
+                         n, digests_host, s, &layout_failed);
+  }
   cudaError_t e;
   if ((e = c->h_packed.reserve(pbytes)) != cudaSuccess ||
       (e = c->h_off.reserve(n * sizeof(uint64_t))) != cudaSuccess ||
@@ -567,6 +702,10 @@ int hash_release_device(void) {
   for (int k = 0; k < kHostChunks; ++k) {
     if (c->ev_in[k]) cudaEventDestroy(c->ev_in[k]);
     if (c->ev_hashed[k]) cudaEventDestroy(c->ev_hashed[k]);
+  }
+  for (int j = 0; j < 2; ++j) {
+    c->win[j].release();
+    if (c->ev_win_out[j]) cudaEventDestroy(c->ev_win_out[j]);
   }
   delete c;
   g_ctx[dev] = nullptr;

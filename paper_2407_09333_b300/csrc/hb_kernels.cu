@@ -475,6 +475,20 @@ cudaError_t launch_bounds(const uint64_t* offsets, const uint32_t* lengths, uint
   return cudaGetLastError();
 }
 
+// offsets[i] -= base (a window's messages, relative to the window's bytes;
+// an offset below base wraps to a huge value that the bounds check rejects).
+__global__ void hb_rebase_kernel(uint64_t* offsets, uint64_t n, uint64_t base) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    offsets[i] -= base;
+}
+
+cudaError_t launch_rebase(uint64_t* offsets, uint64_t n, uint64_t base, int grid,
+                          cudaStream_t stream) {
+  hb_rebase_kernel<<<grid, 256, 0, stream>>>(offsets, n, base);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_monotone(const uint64_t* offsets, const uint32_t* lengths, uint64_t n, int* flag,
                             int grid, cudaStream_t stream) {
   hb_monotone_kernel<<<grid, 256, 0, stream>>>(offsets, lengths, n, flag);

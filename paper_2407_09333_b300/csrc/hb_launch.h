@@ -124,6 +124,9 @@ cudaError_t launch_bounds(const uint64_t* offsets, const uint32_t* lengths, uint
 // Digests of the 9-character decimal strings of first .. first + count - 1.
 cudaError_t launch_digits(int alg, uint64_t first, uint64_t count, uint8_t* digests, int grid,
                           cudaStream_t stream);
+// offsets[i] -= base for i < n.
+cudaError_t launch_rebase(uint64_t* offsets, uint64_t n, uint64_t base, int grid,
+                          cudaStream_t stream);
 // flag = 1 when offsets[i] + lengths[i] decreases anywhere in index order.
 cudaError_t launch_monotone(const uint64_t* offsets, const uint32_t* lengths, uint64_t n, int* flag,
                             int grid, cudaStream_t stream);

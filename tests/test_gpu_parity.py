@@ -225,6 +225,50 @@ def test_host_path_pipelined_chunks(hb, oracle_mod, layout):
         _assert_slots_equal(out[sel], want, "host %s %s" % (layout, alg))
 
 
+def test_host_path_streams_batches_over_the_memory_limit(hb, oracle_mod):
+    # a 40 MB batch through two 2 MB device windows
+    rng = np.random.default_rng(31)
+    lens = rng.integers(0, 9000, size=9000).astype(np.uint32)
+    lens[:7] = workloads.BOUNDARY_LENGTHS
+    b = workloads.scattered(lens, seed=32, overlap=False, mixed=True)
+    old = hb.set_host_memory_limit(4 << 20)
+    try:
+        sel = np.arange(0, b.n, 5)
+        for alg in (1, None):
+            out = np.zeros((b.n, 32), dtype=np.uint8)
+            if alg is None:
+                hb.hash_batch_host(None, b.packed, b.offsets, b.lengths, out, algs=b.algs)
+                ref = b
+            else:
+                hb.hash_batch_host(alg, b.packed, b.offsets, b.lengths, out)
+                ref = workloads.Batch(b.packed, b.offsets, b.lengths, None)
+            _assert_slots_equal(out[sel], _oracle_slots(oracle_mod, ref, alg, sel), "windows %s" % alg)
+        out = np.zeros((b.n, 32), dtype=np.uint8)
+        # a layout that does not stream (ends out of order)
+        perm = rng.permutation(b.n)
+        with pytest.raises(hb.HashBatchError) as e:
+            hb.hash_batch_host(2, b.packed, b.offsets[perm], b.lengths[perm], out)
+        assert e.value.code == -10
+        # a message outside the buffer
+        offs = b.offsets.copy()
+        offs[-1] = b.packed.size - 1
+        with pytest.raises(hb.HashBatchError) as e:
+            hb.hash_batch_host(2, b.packed, offs, b.lengths, out)
+        assert e.value.code == -8
+        # a message larger than a window
+        big = workloads.fixed(3, 3 << 20, seed=33)
+        with pytest.raises(hb.HashBatchError) as e:
+            hb.hash_batch_host(0, big.packed, big.offsets, big.lengths, np.zeros((3, 32), np.uint8))
+        assert e.value.code == -3
+    finally:
+        hb.set_host_memory_limit(old)
+    # the library is still usable without the limit
+    out = np.zeros((b.n, 32), dtype=np.uint8)
+    hb.hash_batch_host(2, b.packed, b.offsets, b.lengths, out)
+    ref = workloads.Batch(b.packed, b.offsets, b.lengths, None)
+    _assert_slots_equal(out[:50], _oracle_slots(oracle_mod, ref, 2, np.arange(50)), "after")
+
+
 def test_host_path_rejects_out_of_bounds(hb):
     b = workloads.fixed(100, 40, seed=2)
     offs = b.offsets.copy()
