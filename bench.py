@@ -542,6 +542,8 @@ def run_ours(args, dist):
         line["plain_equal_bytes_gbs"] = pg
         line["plain_mean_length"] = pl
         line["ragged_vs_plain_equal_bytes"] = per_alg["mixed"]["GB/s"] / pg
+        line["cost_model"] = cost_model_report(api, torch, batch.lengths, batch.algs, packed,
+                                               per_alg["mixed"]["ms"])
     if not args.no_e2e:
         line["e2e"] = e2e_measure(args, batch, mixed, api, torch, dist)
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
@@ -633,6 +635,49 @@ def plain_equal_bytes_gbs(api, torch, lengths, algs, pool, reps=3, max_msgs=1 <<
         b_total += nbytes
         del o, l, out
     return b_total / t_total / 1e9, L
+
+
+def cost_model_report(api, torch, lengths, algs, pool, measured_ms, reps=3):
+    """Fits the linear launch-cost model on fixed-length launches (each
+    algorithm, three batch sizes, the set's mean length, messages read from
+    `pool`) and predicts the measured ragged launch from its lengths and
+    algorithms alone."""
+    from paper_2407_09333_b300 import costmodel
+    L = max(1, int(round(float(lengths.astype(np.float64).mean()))))
+    span = max(1, (pool.numel() - L) // 16)
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        best = float("inf")
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(); fn(); e1.record(); e1.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        return best * 1e-3
+
+    samples = []
+    sizes = (1 << 18, 3 << 18, 1 << 20)
+    for a in (0, 1, 2):
+        batches = []
+        for n in sizes:
+            i = torch.arange(n, dtype=torch.int64, device=pool.device)
+            o = ((i * 2654435761) % span) * 16
+            l = torch.full((n,), L, dtype=torch.int32, device=pool.device)
+            batches.append((n, o, l, torch.empty((n, 32), dtype=torch.uint8, device=pool.device)))
+        # the algorithm's best launch shape on the largest batch, used for all sizes
+        n, o, l, out = batches[-1]
+        shape = min(range(len(api.shapes())),
+                    key=lambda sh: timed(lambda: api.hash_batch(a, pool, o, l, out=out, shape=sh)))
+        for n, o, l, out in batches:
+            t = timed(lambda: api.hash_batch(a, pool, o, l, out=out, shape=shape))
+            samples.append((costmodel.work_by_alg(np.full(n, L), alg=a), t))
+        del batches
+    m = costmodel.fit(samples)
+    pred = m.predict_batch(lengths, algs=algs) * 1e3
+    return {"form": "T = sum over algorithms of rate x (padded blocks x ops per block) + T0",
+            "rate_ps_per_op": [r * 1e12 for r in m.rate], "overhead_us": m.overhead * 1e6,
+            "r2": m.r2, "predicted_ms": pred, "measured_ms": measured_ms,
+            "measured_over_predicted": measured_ms / pred}
 
 
 def run_serve(args, dist):
