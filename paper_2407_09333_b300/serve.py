@@ -37,6 +37,7 @@ from __future__ import annotations
 
 import collections
 import dataclasses
+import gc
 import time
 
 import numpy as np
@@ -249,6 +250,17 @@ class Server:
     def run(self, requests: list, keep_digests: bool = False, time_limit_s: float = 600.0):
         """Serve `requests` (sorted by arrival) in real time; returns them,
         finished (done >= 0) or rejected (done < 0)."""
+        # the loop allocates no reference cycles; a collector pause would
+        # stall round launches, so the cyclic collector waits until the end
+        gc_was_on = gc.isenabled()
+        gc.disable()
+        try:
+            return self._run(requests, keep_digests, time_limit_s)
+        finally:
+            if gc_was_on:
+                gc.enable()
+
+    def _run(self, requests: list, keep_digests: bool, time_limit_s: float):
         torch, book = self.torch, self.book
         torch.cuda.synchronize()
         nreq = len(requests)
