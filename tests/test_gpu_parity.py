@@ -187,6 +187,15 @@ def test_on_device_nine_digit_limits(hb):
     assert e.value.code == -1
 
 
+@pytest.mark.parametrize("alg", [0, 1])
+def test_bit_length_needs_the_high_word(hb, oracle_mod, alg):
+    # 2^29 + 37 bytes: 8L no longer fits 32 bits, so the length block carries
+    # a nonzero high word (little-endian for MD5, big-endian for SHA-1/SM3)
+    L = (1 << 29) + 37
+    b = workloads.fixed(1, L, seed=61)
+    _assert_slots_equal(_gpu_slots(hb, b, alg), _oracle_slots(oracle_mod, b, alg), "2^29+37")
+
+
 def test_host_path_plain_and_mixed(hb, oracle_mod):
     b = workloads.scattered(np.arange(0, 400), seed=4, overlap=True, mixed=True)
     out = np.zeros((b.n, 32), dtype=np.uint8)
