@@ -1,10 +1,13 @@
 """Autotuner for the launch shape of the hashing kernels.
 
-A shape is (warps per block, cp.async stages per warp), i.e. the threads per
-block and the bytes staged per warp (stages x 32 lanes x 80-byte windows).
-For a given algorithm and a representative batch, every shape is timed with
-CUDA events on the caller's stream and the fastest is installed in the
-library (hash_tune_set).  Results are cached in JSON keyed by device name,
+A shape is (warps per block, stages in flight per warp, 64-byte blocks per
+stage, cooperative copies): the threads per block, how far ahead each warp
+stages its messages (stages x blocks per stage x 32 lanes x 64 bytes, plus
+alignment slack) and whether a warp copies message by message (cooperative)
+or lane by lane.  For a given algorithm and a representative batch, every
+shape is timed with CUDA events on the caller's stream and the fastest is
+installed in the library (hash_tune_set); the ragged path also tunes its
+bucketing and its resident warps per SM.  Results are cached in JSON keyed by device name,
 SM count, algorithm (or "mixed") and a length class (floor(log2(mean
 message length + 1))), so a later process with the same device and workload
 shape reuses them without timing.

@@ -1,7 +1,8 @@
-// hb_device.cuh -- sm_103a device primitives used by every hashing kernel:
-// integer ops pinned to single instructions (LOP3, SHF, PRMT), the per-warp
-// bulk-copy (TMA, no multicast) staging pipeline built on mbarriers, and the
-// bounded waits that report a timeout instead of hanging.
+// hb_device.cuh -- sm_103a device primitives used by the hashing kernels:
+// integer ops pinned to single instructions (LOP3, SHF, PRMT), moves of adds
+// and rotations to the multiply-add pipe, shared-memory and cp.async staging
+// primitives, and the bounded mbarrier wait that reports a timeout instead of
+// hanging.
 #pragma once
 
 #include <cstdint>
@@ -111,26 +112,9 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
 }
 
-__device__ __forceinline__ void mbar_inval(uint32_t bar) {
-  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
-}
-
-// Make mbarrier initialisation (and earlier generic shared-memory writes)
-// visible to the async proxy that performs bulk-copy completion.
+// Make an mbarrier's initialisation visible before it is waited on.
 __device__ __forceinline__ void fence_barrier_init() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void fence_proxy_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-// One arrival that also raises the expected transaction byte count.
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile(
-      "{\n\t.reg .b64 st;\n\t"
-      "mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(bar),
-      "r"(bytes)
-      : "memory");
 }
 
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
@@ -167,20 +151,8 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
   }
 }
 
-// 1-D bulk copy global -> shared (TMA engine, no multicast).  dst, src and
-// bytes must be multiples of 16; completion is signalled on `bar` as
-// transaction bytes.
-__device__ __forceinline__ void bulk_copy_g2s(uint32_t dst, const void* src, uint32_t bytes,
-                                              uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          dst),
-      "l"(src), "r"(bytes), "r"(bar)
-      : "memory");
-}
-
 // Shared-memory accesses by 32-bit shared-window address.  They are
-// `volatile` so they keep their order relative to the mbarrier waits and to
+// `volatile` so they keep their order relative to the cp.async waits and to
 // each other at the source level, but carry no memory clobber, so the
 // compiler still schedules the surrounding arithmetic freely.
 __device__ __forceinline__ uint32_t lds32(uint32_t addr) {
@@ -195,10 +167,6 @@ __device__ __forceinline__ uint4 lds128(uint32_t addr) {
                : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
                : "r"(addr));
   return v;
-}
-
-__device__ __forceinline__ void sts32(uint32_t addr, uint32_t v) {
-  asm volatile("st.shared.u32 [%0], %1;" ::"r"(addr), "r"(v));
 }
 
 __device__ __forceinline__ void sts128(uint32_t addr, uint4 v) {
