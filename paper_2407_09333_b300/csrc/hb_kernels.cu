@@ -7,9 +7,15 @@
 //   hb_scatter_kernel  ragged path, step 3: message ids into their group
 //   hb_mixed_kernel    ragged path, step 4: persistent, chunks popped from a
 //                      counter longest-first (hash_batch_mixed)
+//   hb_digits_kernel   the paper's nine-digit workload generated in registers
 //   hb_bounds_kernel   offsets/lengths against the packed buffer size
+//   hb_monotone_kernel, hb_rebase_kernel   host-path helpers (chunk check,
+//                      window-relative offsets)
+//   hb_set_count_kernel, hb_gather_kernel  batch size for captured graphs,
+//                      byte-range packing
 //   hb_int_peak_kernel integer-issue microbenchmark (measurement only)
 //   hb_selftest_wait_kernel  bounded-wait failure test
+// (The streaming-round kernels live in hb_stream.cu.)
 #include <cuda_runtime.h>
 
 #include <cstdint>
