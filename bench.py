@@ -39,7 +39,7 @@ if ROOT not in sys.path:
 from paper_2407_09333_b300 import workloads  # noqa: E402
 
 METRIC = "hashed GB/s and Mhash/s per alg (plain vs ragged batch); serve p50/p99 latency"
-ALG_NAMES = ("md5", "sha1", "sm3")
+ALG_NAMES = ("md5", "sha1", "sm3", None, "all")   # index 4: the fused kernel
 
 # Algorithmic 32-bit operations per 64-byte block (3-input ALU ops: LOP3 for
 # each Boolean function or 3-way XOR, IADD3 for up to three addends, SHF for
@@ -409,7 +409,9 @@ def run_ours(args, dist):
     from paper_2407_09333_b300 import autotune
     tuned = {}
     mean_len = batch.total_bytes / max(n, 1)
-    for a in ([None] if mixed else [0, 1, 2]):
+    fused = not mixed and not args.separate
+    rec = torch.empty((n, 96), dtype=torch.uint8, device="cuda") if fused else None
+    for a in ([None] if mixed else [0, 1, 2] + ([api.ALL] if fused else [])):
         if args.shape is not None:
             # fixed launch configuration (reproducible profiler captures)
             api.tune_set(api.TUNE_MIXED if a is None else a, args.shape)
@@ -420,7 +422,8 @@ def run_ours(args, dist):
                                                               "blocks_per_stage": kb,
                                                               "cooperative": bool(co), "fixed": True}
             continue
-        r = autotune.tune(a, packed, off, ln, out, algs=algs, mean_len=mean_len)
+        r = autotune.tune(a, packed, off, ln, rec if a == api.ALL else out, algs=algs,
+                          mean_len=mean_len)
         tuned["mixed" if a is None else ALG_NAMES[a]] = {"warps": r["warps"], "stages": r["stages"],
                                                           "blocks_per_stage": r.get("blocks_per_stage", 1),
                                                           "cooperative": r.get("cooperative", False),
@@ -439,6 +442,11 @@ def run_ours(args, dist):
         launches = [(None, lambda: plan.replay(n))]
         bytes_per_step = batch.total_bytes
         msgs_per_step = n
+    elif fused:
+        # every message with all three algorithms in one pass (hash_batch_all)
+        launches = [(api.ALL, lambda: api.hash_batch_all(packed, off, ln, out=rec))]
+        bytes_per_step = 3 * batch.total_bytes
+        msgs_per_step = 3 * n
     else:
         launches = [(a, (lambda a=a: api.hash_batch(a, packed, off, ln, out=out))) for a in (0, 1, 2)]
         bytes_per_step = 3 * batch.total_bytes
@@ -481,26 +489,48 @@ def run_ours(args, dist):
     clk = clocks.summary()
     sm_mhz = clk["sm_mhz"] or peaks["sm_max_mhz"]
 
-    per_alg = {}
-    hbm_bytes_per_launch = (batch.total_bytes + 12 * n + (1 * n if mixed else 0) + 32 * n)
-    for j, (a, _) in enumerate(launches):
-        t = per_launch_ms[j] * 1e-3
-        name = ALG_NAMES[a] if a is not None else "mixed"
-        if a is not None:
+    def launch_figures(a, t):
+        """GB/s, Mhash/s and roofline fractions of one launch of `a`."""
+        copies = 3 if a == api.ALL else 1
+        if a == api.ALL:
+            ops = float(nblocks.sum()) * sum(OPS_PER_BLOCK.values())
+        elif a is not None:
             ops = float(nblocks.sum()) * OPS_PER_BLOCK[a]
         else:
             ops = float(sum(float(nblocks[batch.algs == x].sum()) * OPS_PER_BLOCK[x] for x in (0, 1, 2)))
-        per_alg[name] = {
-            "GB/s": batch.total_bytes / t / 1e9, "Mhash/s": n / t / 1e6, "ms": per_launch_ms[j],
+        hbm = batch.total_bytes + 12 * n + (1 * n if mixed else 0) + 32 * copies * n
+        return {
+            "GB/s": copies * batch.total_bytes / t / 1e9, "Mhash/s": copies * n / t / 1e6, "ms": t * 1e3,
             "alu_Tops": ops / t / 1e12,
             "alu_frac_at_clock": ops / t / 1e12 / alu_peak_tops(sms, sm_mhz),
-            "hbm_frac": hbm_bytes_per_launch / t / 1e9 / peaks["hbm_gbs"],
-        }
+            "hbm_frac": hbm / t / 1e9 / peaks["hbm_gbs"],
+        }, ops, hbm
+
+    per_alg = {}
+    hbm_of = {}
+    for j, (a, _) in enumerate(launches):
+        name = ALG_NAMES[a] if a is not None else "mixed"
+        per_alg[name], _, hbm_of[name] = launch_figures(a, per_launch_ms[j] * 1e-3)
+    per_alg_separate = None
+    if fused:
+        # the three single-algorithm kernels, for the per-algorithm figures
+        per_alg_separate = {}
+        for a in (0, 1, 2):
+            fn = lambda: api.hash_batch(a, packed, off, ln, out=out)
+            fn()
+            torch.cuda.synchronize()
+            ts = []
+            for _ in range(20):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream); fn(); e1.record(stream); e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            per_alg_separate[ALG_NAMES[a]] = launch_figures(a, statistics.median(ts) * 1e-3)[0]
     dom = max(range(nl), key=lambda j: per_launch_ms[j])
     dom_alg = launches[dom][0]
     dom_name = ALG_NAMES[dom_alg] if dom_alg is not None else "mixed"
     t_dom = per_launch_ms[dom] * 1e-3
     dom_ops = per_alg[dom_name]["alu_Tops"] * 1e12 * t_dom
+    hbm_bytes_per_launch = hbm_of[dom_name]
     peak_alu = alu_peak_tops(sms, peaks["sm_max_mhz"])
     kernel_key = "%s:%s" % (args.workload, dom_name)
     roofline = {
@@ -528,10 +558,12 @@ def run_ours(args, dist):
                    "parallelism": "dp%d: disjoint message shards, no collective on the data path" % dist.world},
         "mhash_per_s": job_msgs / (ms * 1e-3) / 1e6,
         "per_alg": per_alg,
+        "per_alg_separate_kernels": per_alg_separate,
         "tuned_shapes": tuned,
         "roofline": roofline,
-        # plain: one kernel per algorithm; ragged graph: count-setter, group
-        # histogram, scan, scatter and the persistent hashing kernel
+        # plain: one fused kernel (or one per algorithm with --separate);
+        # ragged graph: count-setter, group histogram, scan, scatter and the
+        # persistent hashing kernel
         "gpu_launches": args.steps * nl * (5 if mixed else 1),
         "clocks": clk,
     }
@@ -562,8 +594,9 @@ def e2e_measure(args, batch, mixed, api, torch, dist):
     off_h = torch.from_numpy(batch.offsets.view(np.int64)).pin_memory()
     len_h = torch.from_numpy(batch.lengths.view(np.int32)).pin_memory()
     algs_h = torch.from_numpy(batch.algs).pin_memory() if mixed else None
-    out_h = torch.empty((n, 32), dtype=torch.uint8).pin_memory()
-    calls = [None] if mixed else [0, 1, 2]
+    fused = not mixed and not args.separate
+    out_h = torch.empty((n, 96 if fused else 32), dtype=torch.uint8).pin_memory()
+    calls = [None] if mixed else [api.ALL] if fused else [0, 1, 2]
 
     def step():
         for a in calls:
@@ -593,10 +626,11 @@ def e2e_measure(args, batch, mixed, api, torch, dist):
     per_call_in = batch.packed.nbytes + 12 * n + (n if mixed else 0)
     if args.host_limit_mib:
         api.set_host_memory_limit(0)
-    return {"value": job_rate(dist, len(calls) * batch.total_bytes * steps, dt) / 1e9, "unit": "GB/s",
+    hashed = (3 if fused else len(calls)) * batch.total_bytes
+    return {"value": job_rate(dist, hashed * steps, dt) / 1e9, "unit": "GB/s",
             "device_memory_limit_bytes": args.host_limit_mib << 20,
             "h2d_bytes_per_step": len(calls) * per_call_in,
-            "d2h_bytes_per_step": len(calls) * 32 * n, "steps": steps,
+            "d2h_bytes_per_step": out_h.numel() * len(calls), "steps": steps,
             "api": "hash_batch_host (pinned host buffers)"}
 
 
@@ -920,6 +954,8 @@ def main(argv=None):
                         "by estimated work")
     p.add_argument("--host-limit-mib", type=int, default=0,
                    help="device memory the e2e host path may use (0 = whole batch on the device)")
+    p.add_argument("--separate", action="store_true",
+                   help="plain workloads: one kernel per algorithm instead of the fused kernel")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--int-peak", action="store_true",

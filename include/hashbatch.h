@@ -59,6 +59,11 @@ extern "C" {
 #define HB_SM3 2
 
 #define HB_SLOT_BYTES 32
+/* All three algorithms on every message (hash_batch_all): one 96-byte record
+ * per message holding the MD5, SHA-1 and SM3 slots in that order.  Also the
+ * tuning code of the fused kernel (hash_tune_set / get / occupancy). */
+#define HB_ALL 4
+#define HB_ALL_RECORD_BYTES 96
 
 /* Return codes. */
 #define HB_OK 0
@@ -104,6 +109,18 @@ const char *hash_last_cuda_error(void);
 int hash_batch(int alg, const uint8_t *packed_bytes, const uint64_t *offsets,
                const uint32_t *lengths, uint64_t n, uint8_t *digests_out,
                void *stream);
+
+/*
+ * hash_batch_all -- MD5, SHA-1 and SM3 of every message in one pass: each
+ * message's bytes are staged once and every staged block feeds the three
+ * compression functions (little-endian words for MD5, byte-swapped words for
+ * SHA-1 and SM3).  records_out is a device array of n 96-byte records
+ * (16-byte aligned): record i holds message i's MD5, SHA-1 and SM3 slots, each
+ * laid out as hash_batch writes it.  Same results as three hash_batch calls,
+ * one read of the input instead of three.  Returns as hash_batch.
+ */
+int hash_batch_all(const uint8_t *packed_bytes, const uint64_t *offsets,
+                   const uint32_t *lengths, uint64_t n, uint8_t *records_out, void *stream);
 
 /*
  * hash_batch_mixed -- per-message algorithm, for ragged batches: messages are
@@ -366,7 +383,8 @@ int hash_batch_check_bounds(const uint64_t *offsets, const uint32_t *lengths, ui
  * call returns HB_ERR_ARG (HB_ERR_BOUNDS for a message outside packed_len,
  * HB_ERR_TOO_LARGE for a message that does not fit a window).  Host buffers should be pinned (cudaHostAlloc / cudaHostRegister)
  * for full copy speed; pageable memory works but is slower.  algs_host may be
- * NULL (single `alg`) or a host array of per-message codes (mixed path).
+ * NULL (single `alg`, or HB_ALL for hash_batch_all's 96-byte records) or a
+ * host array of per-message codes (mixed path).
  * After the copies, every message is checked against packed_len on the
  * device before any message byte is read; when one is out of bounds the
  * hashing kernels skip all work and the call returns HB_ERR_BOUNDS.  The
@@ -438,6 +456,9 @@ int hash_tune_mixed_warps(int warps_per_sm);
  * library's choice: enough blocks for the work, at most one full wave of
  * resident blocks); used by the autotuner and the benchmarks.
  */
+int hash_batch_all_shape(const uint8_t *packed_bytes, const uint64_t *offsets,
+                         const uint32_t *lengths, uint64_t n, uint8_t *records_out,
+                         int shape_index, int grid_blocks, void *stream);
 int hash_batch_shape(int alg, const uint8_t *packed_bytes, const uint64_t *offsets,
                      const uint32_t *lengths, uint64_t n, uint8_t *digests_out,
                      int shape_index, int grid_blocks, void *stream);

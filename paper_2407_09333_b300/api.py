@@ -15,6 +15,8 @@ import numpy as np
 
 MD5, SHA1, SM3 = 0, 1, 2
 TUNE_MIXED = 3
+ALL = 4                 # all three algorithms per message (hash_batch_all)
+ALL_RECORD_BYTES = 96
 SLOT_BYTES = 32
 ALG_NAMES = {MD5: "md5", SHA1: "sha1", SM3: "sm3"}
 ALG_CODES = {v: k for k, v in ALG_NAMES.items()}
@@ -36,6 +38,8 @@ _SIGNATURES = {
     "hash_last_cuda_error": (ctypes.c_char_p, []),
     "hash_batch": (_c_int, [_c_int, _vp, _vp, _vp, _c_u64, _vp, _vp]),
     "hash_batch_mixed": (_c_int, [_vp, _vp, _vp, _vp, _c_u64, _vp, _vp]),
+    "hash_batch_all": (_c_int, [_vp, _vp, _vp, _c_u64, _vp, _vp]),
+    "hash_batch_all_shape": (_c_int, [_vp, _vp, _vp, _c_u64, _vp, _c_int, _c_int, _vp]),
     "hash_batch_mixed_noalloc": (_c_int, [_vp, _vp, _vp, _vp, _c_u64, _vp, _vp]),
     "hash_batch_segments": (_c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _c_u64, _vp, _vp]),
     "hash_batch_check_bounds": (_c_int, [_vp, _vp, _c_u64, _c_u64, _vp, _vp]),
@@ -181,6 +185,26 @@ def hash_batch(alg: int, packed, offsets, lengths, out=None, stream=None,
     return out
 
 
+def hash_batch_all(packed, offsets, lengths, out=None, stream=None, shape: int = -1,
+                   grid: int = 0):
+    """Records (n, 96) uint8: MD5, SHA-1 and SM3 slots of every message,
+    computed in one pass over the input."""
+    torch = _torch()
+    n = int(offsets.numel())
+    if lengths.numel() != n:
+        raise ValueError("offsets and lengths differ in length")
+    if out is None:
+        out = torch.empty((n, ALL_RECORD_BYTES), dtype=torch.uint8, device=offsets.device)
+    elif out.dtype != torch.uint8 or out.numel() < n * ALL_RECORD_BYTES or not out.is_contiguous():
+        raise ValueError("out must be a contiguous uint8 tensor of n*96 bytes")
+    rc = lib().hash_batch_all_shape(
+        _dev_ptr(packed, 1, "packed"), _dev_ptr(offsets, 8, "offsets"),
+        _dev_ptr(lengths, 4, "lengths"), n, _dev_ptr(out, 1, "out"), int(shape), int(grid),
+        _stream_handle(stream))
+    _check(rc, "hash_batch_all")
+    return out
+
+
 def hash_batch_mixed(algs, packed, offsets, lengths, out=None, stream=None,
                      shape: int = -1, grid: int = 0):
     """Digest slots (n, 32) uint8, per-message algorithm (ragged path)."""
@@ -293,9 +317,15 @@ def _host_ptr(a, name):
 
 
 def hash_batch_host(alg, packed, offsets, lengths, out, algs=None, stream=None):
-    """End-to-end call from host buffers (pinned for full speed)."""
+    """End-to-end call from host buffers (pinned for full speed).  `out`
+    holds n 32-byte slots, or n 96-byte records for alg == ALL."""
     n = int(len(offsets))
     packed_len = int(packed.numel() if hasattr(packed, "numel") else packed.size)
+    rec = ALL_RECORD_BYTES if alg == ALL else SLOT_BYTES
+    out_bytes = int(out.numel() * out.element_size()) if hasattr(out, "numel") else int(out.nbytes)
+    if out_bytes < n * rec or len(lengths) != n or (algs is not None and len(algs) != n):
+        raise ValueError("out must hold %d bytes per message; offsets, lengths (and algs) "
+                         "one entry per message" % rec)
     rc = lib().hash_batch_host(
         -1 if alg is None else int(alg), _host_ptr(algs, "algs"),
         _host_ptr(packed, "packed") if packed_len else None, packed_len,

@@ -32,7 +32,7 @@ def length_class(mean_len: float) -> int:
 
 
 def cache_key(device_name: str, sms: int, alg, mean_len: float) -> str:
-    name = "mixed" if alg is None else api.ALG_NAMES[alg]
+    name = "mixed" if alg is None else "all" if alg == api.ALL else api.ALG_NAMES[alg]
     return "%s|%d|%s|L%d" % (device_name, sms, name, length_class(mean_len))
 
 
@@ -71,7 +71,9 @@ def _time_ms(torch, fn, reps: int) -> float:
 
 def tune(alg, packed, offsets, lengths, out, algs=None, mean_len: float | None = None,
          reps: int = 3, use_cache: bool = True, path: str | None = None) -> dict:
-    """Pick and install the fastest shape for `alg` (None = the mixed path).
+    """Pick and install the fastest shape for `alg` (None = the mixed path,
+    api.ALL = the fused three-algorithm kernel; `out` then holds 96-byte
+    records).
 
     Returns {"shape": index, "warps": w, "stages": s, "ms": {index: ms},
     "cached": bool}.
@@ -96,6 +98,8 @@ def tune(alg, packed, offsets, lengths, out, algs=None, mean_len: float | None =
     def run(idx):
         if alg is None:
             return lambda: api.hash_batch_mixed(algs, packed, offsets, lengths, out=out, shape=idx)
+        if alg == api.ALL:
+            return lambda: api.hash_batch_all(packed, offsets, lengths, out=out, shape=idx)
         return lambda: api.hash_batch(alg, packed, offsets, lengths, out=out, shape=idx)
 
     result = {"key": key}

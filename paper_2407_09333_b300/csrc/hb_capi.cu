@@ -58,10 +58,10 @@ struct Ctx {
   int device = -1;
   int sms = 0;
   int* status = nullptr;                 // device word of HB_DEV_* bits
-  int occ_plain[3][kMaxShapes] = {};     // resident blocks per SM, 0 = not prepared
+  int occ_plain[HB_ALL + 1][kMaxShapes] = {};  // resident blocks per SM, 0 = not prepared
   int occ_mixed[kMaxShapes] = {};
   int occ_mixed_seg[kMaxShapes] = {};    // segment-aware variant
-  int tune_plain[3] = {0, 0, 0};
+  int tune_plain[HB_ALL + 1] = {0, 0, 0, 0, 0};  // index HB_ALL: the fused kernel
   int tune_mixed = hb::kDefaultMixedShape;
   int mixed_warps_per_sm = hb::kDefaultMixedWarpsPerSm;  // 0 = full occupancy
   hb::BucketCfg buckets = hb::kDefaultBuckets;
@@ -259,9 +259,16 @@ const char* hash_strerror(int code) {
   }
 }
 
+int hash_batch_all_shape(const uint8_t* packed_bytes, const uint64_t* offsets,
+                         const uint32_t* lengths, uint64_t n, uint8_t* records_out,
+                         int shape_index, int grid_blocks, void* stream);
+
 int hash_batch_shape(int alg, const uint8_t* packed_bytes, const uint64_t* offsets,
                      const uint32_t* lengths, uint64_t n, uint8_t* digests_out, int shape_index,
                      int grid_blocks, void* stream) {
+  if (alg == HB_ALL)
+    return hash_batch_all_shape(packed_bytes, offsets, lengths, n, digests_out, shape_index,
+                                grid_blocks, stream);
   if (hash_digest_size(alg) == 0) return HB_ERR_INVALID_ALG;
   if (n == 0) return HB_OK;
   if (n >= kMaxPlainN) return HB_ERR_TOO_LARGE;
@@ -280,6 +287,33 @@ int hash_batch_shape(int alg, const uint8_t* packed_bytes, const uint64_t* offse
   a.wait_limit_ns = g_wait_limit_ns;
   a.mc = hb::make_mul_consts();
   return launch_plain(c, alg, shape_index, grid_blocks, a, static_cast<cudaStream_t>(stream));
+}
+
+int hash_batch_all_shape(const uint8_t* packed_bytes, const uint64_t* offsets,
+                         const uint32_t* lengths, uint64_t n, uint8_t* records_out,
+                         int shape_index, int grid_blocks, void* stream) {
+  if (n == 0) return HB_OK;
+  if (n >= kMaxPlainN) return HB_ERR_TOO_LARGE;
+  int rc = check_common(packed_bytes, offsets, lengths, n, records_out);
+  if (rc) return rc;
+  Ctx* c = nullptr;
+  if ((rc = get_ctx(&c))) return rc;
+  if (shape_index < 0) shape_index = c->tune_plain[HB_ALL];
+  KernelArgs a{};
+  a.packed = packed_bytes;
+  a.offsets = offsets;
+  a.lengths = lengths;
+  a.n = n;
+  a.digests = records_out;
+  a.status = c->status;
+  a.wait_limit_ns = g_wait_limit_ns;
+  a.mc = hb::make_mul_consts();
+  return launch_plain(c, HB_ALL, shape_index, grid_blocks, a, static_cast<cudaStream_t>(stream));
+}
+
+int hash_batch_all(const uint8_t* packed_bytes, const uint64_t* offsets, const uint32_t* lengths,
+                   uint64_t n, uint8_t* records_out, void* stream) {
+  return hash_batch_all_shape(packed_bytes, offsets, lengths, n, records_out, -1, 0, stream);
 }
 
 int hash_batch(int alg, const uint8_t* packed_bytes, const uint64_t* offsets,
@@ -390,6 +424,7 @@ int host_hash_range(Ctx* c, int alg, const uint8_t* d_algs, const uint8_t* d_pac
                     const uint64_t* d_off, const uint32_t* d_len, uint64_t first, uint64_t count,
                     uint8_t* d_dig, const int* abort_flag, cudaStream_t s) {
   if (count == 0) return HB_OK;
+  const uint64_t rec = alg == HB_ALL ? HB_ALL_RECORD_BYTES : HB_SLOT_BYTES;
   if (d_algs)
     return launch_mixed(c, c->tune_mixed, 0, d_algs + first, d_packed, d_off + first,
                         d_len + first, count, d_dig + first * HB_SLOT_BYTES, c->ws.p, abort_flag, s);
@@ -398,7 +433,7 @@ int host_hash_range(Ctx* c, int alg, const uint8_t* d_algs, const uint8_t* d_pac
   a.offsets = d_off + first;
   a.lengths = d_len + first;
   a.n = count;
-  a.digests = d_dig + first * HB_SLOT_BYTES;
+  a.digests = d_dig + first * rec;
   a.status = c->status;
   a.abort_flag = abort_flag;
   a.wait_limit_ns = g_wait_limit_ns;
@@ -408,7 +443,7 @@ int host_hash_range(Ctx* c, int alg, const uint8_t* d_algs, const uint8_t* d_pac
 
 // Device bytes a window needs per message: offset, length, algorithm code,
 // digest slot.
-constexpr uint64_t kWinMsgBytes = 8 + 4 + 1 + HB_SLOT_BYTES;
+constexpr uint64_t kWinMsgBytes = 8 + 4 + 1 + HB_ALL_RECORD_BYTES;  // largest record
 
 uint64_t align_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
 
@@ -424,6 +459,7 @@ int host_windowed(Ctx* c, int alg, const uint8_t* algs_host, const uint8_t* pack
                   const uint32_t* lengths_host, uint64_t n, uint8_t* digests_host,
                   cudaStream_t s, bool* layout_failed) {
   *layout_failed = false;
+  const uint64_t rec = (alg == HB_ALL && !algs_host) ? HB_ALL_RECORD_BYTES : HB_SLOT_BYTES;
   const uint64_t B = g_host_limit / 2;  // bytes per window buffer
   const uint64_t max_msgs = B / (2 * kWinMsgBytes);
   if (max_msgs == 0) return HB_ERR_TOO_LARGE;
@@ -475,7 +511,7 @@ int host_windowed(Ctx* c, int alg, const uint8_t* algs_host, const uint8_t* pack
     uint64_t* d_off = reinterpret_cast<uint64_t*>(base + align_up(re - rs + 16, 256));
     uint32_t* d_len = reinterpret_cast<uint32_t*>(d_off + cnt);
     uint8_t* d_dig = reinterpret_cast<uint8_t*>(align_up(reinterpret_cast<uint64_t>(d_len + cnt), 256));
-    uint8_t* d_algs = d_dig + cnt * HB_SLOT_BYTES;
+    uint8_t* d_algs = d_dig + cnt * rec;
     // this window's buffer is free once the window two back has been copied out
     if (k >= 2 && cudaStreamWaitEvent(s, c->ev_win_out[j], 0)) return fail();
     if ((re > rs && cudaMemcpyAsync(d_packed, packed_host + rs, re - rs, cudaMemcpyHostToDevice, s)) ||
@@ -494,7 +530,7 @@ int host_windowed(Ctx* c, int alg, const uint8_t* algs_host, const uint8_t* pack
     if (rc) return rc;
     if (cudaEventRecord(c->ev_hashed[k % kHostChunks], sh) ||
         cudaStreamWaitEvent(so, c->ev_hashed[k % kHostChunks], 0) ||
-        cudaMemcpyAsync(digests_host + m * HB_SLOT_BYTES, d_dig, cnt * (size_t)HB_SLOT_BYTES,
+        cudaMemcpyAsync(digests_host + m * rec, d_dig, cnt * (size_t)rec,
                         cudaMemcpyDeviceToHost, so) ||
         cudaEventRecord(c->ev_win_out[j], so))
       return fail();
@@ -546,9 +582,11 @@ int hash_batch_host(int alg, const uint8_t* algs_host, const uint8_t* packed_hos
                     uint64_t packed_len, const uint64_t* offsets_host,
                     const uint32_t* lengths_host, uint64_t n, uint8_t* digests_host,
                     void* stream) {
-  if (!algs_host && hash_digest_size(alg) == 0) return HB_ERR_INVALID_ALG;
+  if (!algs_host && alg != HB_ALL && hash_digest_size(alg) == 0) return HB_ERR_INVALID_ALG;
   if (n == 0) return HB_OK;
   if (n >= (algs_host ? kMaxMixedN : kMaxPlainN)) return HB_ERR_TOO_LARGE;
+  // digest bytes per message: one slot, or (HB_ALL) a three-slot record
+  const uint64_t rec = (alg == HB_ALL && !algs_host) ? HB_ALL_RECORD_BYTES : HB_SLOT_BYTES;
   if (!offsets_host || !lengths_host || !digests_host || (!packed_host && packed_len))
     return HB_ERR_NULL;
   Ctx* c = nullptr;
@@ -569,7 +607,7 @@ int hash_batch_host(int alg, const uint8_t* algs_host, const uint8_t* packed_hos
   if ((e = c->h_packed.reserve(pbytes)) != cudaSuccess ||
       (e = c->h_off.reserve(n * sizeof(uint64_t))) != cudaSuccess ||
       (e = c->h_len.reserve(n * sizeof(uint32_t))) != cudaSuccess ||
-      (e = c->h_dig.reserve(n * (size_t)HB_SLOT_BYTES)) != cudaSuccess ||
+      (e = c->h_dig.reserve(n * (size_t)rec)) != cudaSuccess ||
       (e = c->h_flag.reserve(2 * sizeof(int))) != cudaSuccess ||
       (algs_host && (e = c->h_algs.reserve(n)) != cudaSuccess))
     return cuda_fail(e);
@@ -619,9 +657,8 @@ int hash_batch_host(int alg, const uint8_t* algs_host, const uint8_t* packed_hos
       return rc;
     if (cudaEventRecord(c->ev_hashed[k], sh) || cudaStreamWaitEvent(so, c->ev_hashed[k], 0))
       return fail();
-    if (lo > prev_m && cudaMemcpyAsync(digests_host + prev_m * HB_SLOT_BYTES,
-                                       d_dig + prev_m * HB_SLOT_BYTES,
-                                       (lo - prev_m) * (size_t)HB_SLOT_BYTES,
+    if (lo > prev_m && cudaMemcpyAsync(digests_host + prev_m * rec, d_dig + prev_m * rec,
+                                       (lo - prev_m) * (size_t)rec,
                                        cudaMemcpyDeviceToHost, so))
       return fail();
     prev_b = b;
@@ -640,7 +677,7 @@ int hash_batch_host(int alg, const uint8_t* algs_host, const uint8_t* packed_hos
     // ends decrease somewhere: every byte is in now, hash everything again
     if ((rc = host_hash_range(c, alg, d_algs, d_packed, d_off, d_len, 0, n, d_dig, d_flag, s)))
       return rc;
-    if (cudaMemcpyAsync(digests_host, d_dig, n * (size_t)HB_SLOT_BYTES, cudaMemcpyDeviceToHost, s) ||
+    if (cudaMemcpyAsync(digests_host, d_dig, n * (size_t)rec, cudaMemcpyDeviceToHost, s) ||
         cudaStreamSynchronize(s))
       return fail();
   }
@@ -727,7 +764,7 @@ int hash_tune_shape(int index, int* warps_per_block, int* stages, int* blocks_pe
 
 int hash_tune_set(int alg, int shape_index) {
   if (shape_index < 0 || shape_index >= hb::num_shapes()) return HB_ERR_ARG;
-  if (alg != HB_TUNE_MIXED && hash_digest_size(alg) == 0) return HB_ERR_INVALID_ALG;
+  if (alg != HB_TUNE_MIXED && alg != HB_ALL && hash_digest_size(alg) == 0) return HB_ERR_INVALID_ALG;
   Ctx* c = nullptr;
   int rc = get_ctx(&c);
   if (rc) return rc;
@@ -742,7 +779,7 @@ int hash_tune_get(int alg) {
   Ctx* c = nullptr;
   if (get_ctx(&c)) return cuda_fail(cudaGetLastError());
   if (alg == HB_TUNE_MIXED) return c->tune_mixed;
-  if (hash_digest_size(alg) == 0) return HB_ERR_INVALID_ALG;
+  if (alg != HB_ALL && hash_digest_size(alg) == 0) return HB_ERR_INVALID_ALG;
   return c->tune_plain[alg];
 }
 
@@ -768,7 +805,7 @@ int hash_tune_buckets(int sub_log2, int alg_major) {
 int hash_tune_occupancy(int alg, int shape_index) {
   if (shape_index < 0 || shape_index >= hb::num_shapes()) return HB_ERR_ARG;
   const bool mixed = alg == HB_TUNE_MIXED;
-  if (!mixed && hash_digest_size(alg) == 0) return HB_ERR_INVALID_ALG;
+  if (!mixed && alg != HB_ALL && hash_digest_size(alg) == 0) return HB_ERR_INVALID_ALG;
   Ctx* c = nullptr;
   int rc = get_ctx(&c);
   if (rc) return rc;

@@ -1,7 +1,8 @@
 // hb_kernels.cu -- every kernel of the library and its host-side launcher.
 //
-//   hb_plain_kernel    one algorithm, one message per thread, static
-//                      grid-stride over 32-message tasks (hash_batch)
+//   hb_plain_kernel    one algorithm (or all three, HB_ALL), one message per
+//                      thread, static grid-stride over 32-message tasks
+//                      (hash_batch, hash_batch_all)
 //   hb_hist_kernel     ragged path, step 1: histogram of (cost bucket, alg)
 //   hb_scan_kernel     ragged path, step 2: group starts, padding, counters
 //   hb_scatter_kernel  ragged path, step 3: message ids into their group
@@ -441,6 +442,7 @@ static KernelFn pick(bool mixed, int alg, int shape, bool seg) {
     case HB_MD5: return plain_fn<HB_MD5>(shape);
     case HB_SHA1: return plain_fn<HB_SHA1>(shape);
     case HB_SM3: return plain_fn<HB_SM3>(shape);
+    case HB_ALL: return plain_fn<HB_ALL>(shape);
     default: return nullptr;
   }
 }

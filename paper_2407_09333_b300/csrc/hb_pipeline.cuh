@@ -73,6 +73,20 @@ __device__ __forceinline__ uint32_t padded_blocks(uint32_t len) {
   return (uint32_t)(((uint64_t)len + 72u) >> 6);
 }
 
+// Chaining state a lane carries across the blocks of its message: one
+// algorithm's words, or (HB_ALL) all three algorithms' side by side.
+struct AllState {
+  uint32_t md5[8], sha1[8], sm3[8];
+};
+template <int ALG>
+struct StateFor {
+  using type = uint32_t[8];
+};
+template <>
+struct StateFor<HB_ALL> {
+  using type = AllState;
+};
+
 // Per-lane description of the task the issuing side is walking.
 struct LaneTask {
   uint64_t msg;    // message index (digest slot); meaningful when nb > 0
@@ -294,6 +308,49 @@ struct SegCtx {
   uint32_t slot;   // the message's 32-byte slot
 };
 
+// One block of a message for all three algorithms (HB_ALL): the staged
+// words feed MD5 as loaded and SHA-1 / SM3 byte-swapped; the final block
+// writes the message's 96-byte record.
+__device__ __forceinline__ void process_block_all(AllState& st, uint32_t slot, uint32_t s,
+                                                  uint32_t len, uint32_t b, uint64_t msg,
+                                                  uint8_t* records, const MulConsts& mc) {
+  const int64_t rem = (int64_t)len - 64 * (int64_t)b;  // message bytes from this block on
+  if (rem >= 0 && rem < 64) sts8(slot + s + (uint32_t)rem, 0x80u);
+  uint32_t w[16], wb[16];
+  read_block_words<false>(slot, s, w);
+#pragma unroll
+  for (int i = 0; i < 16; ++i) wb[i] = bswap32(w[i]);
+  const bool final_block = rem <= 55;
+  if (final_block) {
+    const uint32_t lo = len << 3, hi = len >> 29;  // bit length mod 2^64
+    w[14] = lo;
+    w[15] = hi;
+    wb[14] = hi;
+    wb[15] = lo;
+  }
+  if (b == 0) {
+    md5_init(st.md5);
+    sha1_init(st.sha1);
+    sm3_init(st.sm3);
+  }
+  md5_compress(st.md5, w, mc);
+  sha1_compress(st.sha1, wb, mc);
+  sm3_compress(st.sm3, wb, mc);
+  if (final_block) {
+    uint8_t* dst = records + msg * HB_ALL_RECORD_BYTES;
+    uint32_t o[8];
+    alg_digest_words<HB_MD5>(st.md5, o);
+    stg128_cs(dst, o[0], o[1], o[2], o[3]);
+    stg128_cs(dst + 16, o[4], o[5], o[6], o[7]);
+    alg_digest_words<HB_SHA1>(st.sha1, o);
+    stg128_cs(dst + 32, o[0], o[1], o[2], o[3]);
+    stg128_cs(dst + 48, o[4], o[5], o[6], o[7]);
+    alg_digest_words<HB_SM3>(st.sm3, o);
+    stg128_cs(dst + 64, o[0], o[1], o[2], o[3]);
+    stg128_cs(dst + 80, o[4], o[5], o[6], o[7]);
+  }
+}
+
 template <int ALG, bool SEG = false>
 __device__ __forceinline__ void process_block(uint32_t (&st)[8], uint32_t slot, uint32_t s,
                                               uint32_t len, uint32_t b, uint64_t msg,
@@ -348,14 +405,17 @@ __device__ __forceinline__ void process_block(uint32_t (&st)[8], uint32_t slot, 
 // Consumes the KB blocks of one stage for one lane (blocks past the
 // message's padded length are skipped).
 template <int ALG, int KB, bool SEG = false>
-__device__ __forceinline__ void process_stage(uint32_t (&st)[8], uint32_t slot, uint32_t s,
-                                              uint32_t len, uint32_t b0, uint64_t msg,
+__device__ __forceinline__ void process_stage(typename StateFor<ALG>::type& st, uint32_t slot,
+                                              uint32_t s, uint32_t len, uint32_t b0, uint64_t msg,
                                               const KernelArgs& a, const SegCtx& sc = SegCtx{}) {
   const uint32_t nb = (SEG && sc.more) ? (len >> 6) : padded_blocks(len);
 #pragma unroll 1
   for (int j = 0; j < KB; ++j) {
     if (b0 + j >= nb) break;
-    process_block<ALG, SEG>(st, slot + 64 * j, s, len, b0 + j, msg, a.digests, a.mc, a, sc);
+    if constexpr (ALG == HB_ALL)
+      process_block_all(st, slot + 64 * j, s, len, b0 + j, msg, a.digests, a.mc);
+    else
+      process_block<ALG, SEG>(st, slot + 64 * j, s, len, b0 + j, msg, a.digests, a.mc, a, sc);
   }
 }
 
@@ -388,7 +448,7 @@ __device__ __forceinline__ void warp_pipeline(Source& src, uint8_t* wsm, const K
 
   // Consuming side state.
   int cs = 0;
-  uint32_t st[8];
+  typename StateFor<MIXED ? HB_MD5 : ALG>::type st;
   int inflight = 0;
 
   auto issue = [&]() {

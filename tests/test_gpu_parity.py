@@ -196,6 +196,39 @@ def test_bit_length_needs_the_high_word(hb, oracle_mod, alg):
     _assert_slots_equal(_gpu_slots(hb, b, alg), _oracle_slots(oracle_mod, b, alg), "2^29+37")
 
 
+@pytest.mark.parametrize("shape", [0, 5, 10, 11, 14, 19])
+def test_all_three_in_one_pass(hb, oracle_mod, shape):
+    # every length 0..300 plus long ones, unaligned and overlapping: the
+    # fused kernel's three slots equal the oracle's per-algorithm slots
+    lens = list(range(0, 301)) + [511, 512, 513, 4095, 4096, 4097, 65537]
+    b = workloads.scattered(lens, seed=41 + shape, overlap=True)
+    packed, off, ln, _ = hb.to_device(b)
+    rec = hb.hash_batch_all(packed, off, ln, shape=shape).cpu().numpy()
+    assert rec.shape == (b.n, 96)
+    for alg in ALGS:
+        _assert_slots_equal(rec[:, 32 * alg:32 * alg + 32], _oracle_slots(oracle_mod, b, alg),
+                            "all shape %d alg %d" % (shape, alg))
+
+
+def test_all_three_host_path(hb, oracle_mod):
+    b = workloads.fixed(20000, 55, seed=42)
+    out = np.zeros((b.n, 96), dtype=np.uint8)
+    hb.hash_batch_host(hb.ALL, b.packed, b.offsets, b.lengths, out)
+    for alg in ALGS:
+        _assert_slots_equal(out[:, 32 * alg:32 * alg + 32], _oracle_slots(oracle_mod, b, alg),
+                            "all host alg %d" % alg)
+    # through the device-memory windows as well
+    old = hb.set_host_memory_limit(1 << 20)
+    try:
+        out2 = np.zeros_like(out)
+        hb.hash_batch_host(hb.ALL, b.packed, b.offsets, b.lengths, out2)
+    finally:
+        hb.set_host_memory_limit(old)
+    assert np.array_equal(out, out2)
+    with pytest.raises(ValueError):
+        hb.hash_batch_host(hb.ALL, b.packed, b.offsets, b.lengths, np.zeros((b.n, 32), np.uint8))
+
+
 def test_host_path_plain_and_mixed(hb, oracle_mod):
     b = workloads.scattered(np.arange(0, 400), seed=4, overlap=True, mixed=True)
     out = np.zeros((b.n, 32), dtype=np.uint8)
