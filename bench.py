@@ -514,17 +514,25 @@ def run_ours(args, dist):
     per_alg_separate = None
     if fused:
         # the three single-algorithm kernels, for the per-algorithm figures
+        # (timed like a step of the --separate mode: back to back on the
+        # stream, an event pair around each launch)
         per_alg_separate = {}
-        for a in (0, 1, 2):
-            fn = lambda: api.hash_batch(a, packed, off, ln, out=out)
+        sep = [(a, (lambda a=a: api.hash_batch(a, packed, off, ln, out=out))) for a in (0, 1, 2)]
+        for _, fn in sep:
             fn()
-            torch.cuda.synchronize()
-            ts = []
-            for _ in range(20):
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream); fn(); e1.record(stream); e1.synchronize()
-                ts.append(e0.elapsed_time(e1))
-            per_alg_separate[ALG_NAMES[a]] = launch_figures(a, statistics.median(ts) * 1e-3)[0]
+        torch.cuda.synchronize()
+        reps = 20
+        sev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                for _ in sep] for _ in range(reps)]
+        for k in range(reps):
+            for j, (_, fn) in enumerate(sep):
+                sev[k][j][0].record(stream)
+                fn()
+                sev[k][j][1].record(stream)
+        torch.cuda.synchronize()
+        for j, (a, _) in enumerate(sep):
+            t = statistics.median([sev[k][j][0].elapsed_time(sev[k][j][1]) for k in range(reps)])
+            per_alg_separate[ALG_NAMES[a]] = launch_figures(a, t * 1e-3)[0]
     dom = max(range(nl), key=lambda j: per_launch_ms[j])
     dom_alg = launches[dom][0]
     dom_name = ALG_NAMES[dom_alg] if dom_alg is not None else "mixed"

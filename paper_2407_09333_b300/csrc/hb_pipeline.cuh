@@ -316,17 +316,15 @@ __device__ __forceinline__ void process_block_all(AllState& st, uint32_t slot, u
                                                   uint8_t* records, const MulConsts& mc) {
   const int64_t rem = (int64_t)len - 64 * (int64_t)b;  // message bytes from this block on
   if (rem >= 0 && rem < 64) sts8(slot + s + (uint32_t)rem, 0x80u);
-  uint32_t w[16], wb[16];
+  // One copy of the words is live at a time: MD5 takes them as loaded, then
+  // they are byte-swapped in place for SHA-1 and SM3.
+  uint32_t w[16];
   read_block_words<false>(slot, s, w);
-#pragma unroll
-  for (int i = 0; i < 16; ++i) wb[i] = bswap32(w[i]);
   const bool final_block = rem <= 55;
+  const uint32_t lo = len << 3, hi = len >> 29;  // bit length mod 2^64
   if (final_block) {
-    const uint32_t lo = len << 3, hi = len >> 29;  // bit length mod 2^64
     w[14] = lo;
     w[15] = hi;
-    wb[14] = hi;
-    wb[15] = lo;
   }
   if (b == 0) {
     md5_init(st.md5);
@@ -334,8 +332,14 @@ __device__ __forceinline__ void process_block_all(AllState& st, uint32_t slot, u
     sm3_init(st.sm3);
   }
   md5_compress(st.md5, w, mc);
-  sha1_compress(st.sha1, wb, mc);
-  sm3_compress(st.sm3, wb, mc);
+#pragma unroll
+  for (int i = 0; i < 16; ++i) w[i] = bswap32(w[i]);
+  if (final_block) {
+    w[14] = hi;
+    w[15] = lo;
+  }
+  sha1_compress(st.sha1, w, mc);
+  sm3_compress(st.sm3, w, mc);
   if (final_block) {
     uint8_t* dst = records + msg * HB_ALL_RECORD_BYTES;
     uint32_t o[8];
