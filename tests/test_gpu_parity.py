@@ -373,6 +373,23 @@ def test_full_size_65536_by_16KiB_sampled(hb, oracle_mod):
         _assert_slots_equal(got, _oracle_slots(oracle_mod, b, alg, idx), "C4 alg %d" % alg)
 
 
+@pytest.mark.parametrize("n,length,seed,k", [(1 << 22, 55, 1, 20000), (65536, 16384, 3, 1500)])
+def test_full_size_fused_sampled(hb, oracle_mod, tmp_path, n, length, seed, k):
+    # the default benchmark step: the fused kernel in its autotuned shape
+    from paper_2407_09333_b300 import autotune
+    b = workloads.fixed(n, length, seed=seed)
+    packed, off, ln, _ = hb.to_device(b)
+    rec = torch.empty((b.n, 96), dtype=torch.uint8, device="cuda")
+    autotune.tune(hb.ALL, packed, off, ln, rec, path=str(tmp_path / "tune.json"))
+    hb.hash_batch_all(packed, off, ln, out=rec)
+    idx = _sample(b.n, k, seed)
+    got = rec[torch.from_numpy(idx).cuda()].cpu().numpy()
+    for alg in ALGS:
+        _assert_slots_equal(got[:, 32 * alg:32 * alg + 32], _oracle_slots(oracle_mod, b, alg, idx),
+                            "fused %dx%d alg %d" % (n, length, alg))
+    assert hb.device_status() == 0
+
+
 def test_full_size_ragged_2pow20_sampled(hb, oracle_mod):
     b = workloads.ragged(1 << 20, seed=2)
     packed, off, ln, algs = hb.to_device(b)
