@@ -87,6 +87,31 @@ def test_rounds_hash_a_ring_segment_by_segment(env, oracle_mod, in_place):
         r.close()
 
 
+def test_round_reports_a_request_index_outside_the_table(env, oracle_mod):
+    api = env[0]
+    b = workloads.fixed(40, 300, seed=83)
+    ring = _ring(api, 64, 4)
+    packed = torch.from_numpy(np.ascontiguousarray(b.packed)).cuda()
+    ring["src"][:40] = torch.from_numpy(b.offsets.astype(np.int64) + packed.data_ptr()).cuda()
+    ring["len"][:40] = torch.from_numpy(b.lengths.view(np.int32)).cuda()
+    ring["alg"][:40] = 2
+    req = np.zeros(40, dtype=np.int32)
+    req[7] = 1000                                     # outside the 4-entry request table
+    ring["req"][:40] = torch.from_numpy(req).cuda()
+    ring["req_remaining"][0] = 39
+    ring["state"][:40] = api.RING_READY
+    api.device_status()
+    r = api.Round(ring, 64, None, 1 << 20, 4096, shape=16)
+    s = torch.cuda.Stream()
+    r.launch(0, 40, stream=s)
+    torch.cuda.synchronize()
+    assert api.device_status() & api.DEV_BOUNDS
+    assert int(ring["req_remaining"][0].item()) == 0 and ring["req_done"][0].item() == 1
+    want = oracle_mod.hash_batch(2, b.packed, b.offsets, b.lengths)
+    assert np.array_equal(ring["slots"][:40].cpu().numpy(), want)   # every digest still written
+    r.close()
+
+
 def test_round_arguments_are_checked(env):
     api = env[0]
     ring = _ring(api, 64, 4)
