@@ -27,6 +27,19 @@ constexpr bool kMd5Fma = false;
 constexpr bool kSha1Fma = true;
 constexpr bool kSm3Fma = true;
 
+// The fused three-algorithm kernel: whether its MD5 adds go to the FMA pipe,
+// and whether MD5 and SM3 run interleaved step by step (md5_sm3_compress).
+// Both are off by default; measured on B300, neither is faster (the MD5 chain
+// pays the IMAD latency, and the interleaved code is as large as the two
+// unrolled functions).
+#ifndef HB_MD5_FUSED_FMA
+#define HB_MD5_FUSED_FMA 0
+#endif
+#ifndef HB_FUSED_INTERLEAVE
+#define HB_FUSED_INTERLEAVE 0
+#endif
+constexpr bool kMd5FusedFma = HB_MD5_FUSED_FMA != 0;
+
 // SM3 rotations that run on the FMA pipe (rotl_fma), one bit per site:
 //   1 C <- B<<<9   2 G <- F<<<19   4 A<<<12   8 (A<<<12 + E + T)<<<7
 //   16 both rotations of P0   32 W<<<15 in the expansion   64 W<<<7 in the
@@ -70,99 +83,68 @@ __device__ __forceinline__ void md5_init(uint32_t (&st)[8]) {
   st[3] = 0x10325476u;
 }
 
-// One operation a = b + ((a + g(b,c,d) + X[k] + T[i]) <<< s).  The sum
-// a + X[k] + T[i] does not depend on b, c, d and is one IADD3.  (V selects
-// between two equivalent forms of the rotate-and-add; they differ only when
-// the adds go to the FMA pipe.)
-#define HB_MD5_OP(LUT, a, b, c, d, xk, t, s, V)           \
-  do {                                                   \
-    a += (xk) + (t);                                     \
-    a = add_f<kMd5Fma>(lop3<LUT>(b, c, d), a, mc);       \
-    if (V)                                               \
-      a = rotl_add_f<s, kMd5Fma>(a, b, mc);              \
-    else                                                 \
-      a = add_f<kMd5Fma>(rotl<s>(a), b, mc);             \
-  } while (0)
+// Step J of the 64 (RFC 1321 Sec. 3.4): a = b + ((a + g(b,c,d) + X[k] + T[J])
+// <<< s), with g, the word index k and the shift s fixed by the round J / 16:
+//   round 1  F = (x & y) | (~x & z)   k = j           s = 7 12 17 22
+//   round 2  G = (x & z) | (y & ~z)   k = 1 + 5j      s = 5 9 14 20
+//   round 3  H = x ^ y ^ z            k = 5 + 3j      s = 4 11 16 23
+//   round 4  I = y ^ (x | ~z)         k = 7j          s = 6 10 15 21
+// (j = J mod 16, k mod 16).  The four registers rotate one place per step:
+// step J updates the one at position -J mod 4 of (A, B, C, D).  The sum
+// a + X[k] + T[J] does not depend on b, c, d and is one IADD3.  F selects
+// whether the adds run on the FMA pipe; the rotate-and-add alternates between
+// its two equivalent forms, which differ only there.
+template <int J>
+struct Md5Step {
+  static constexpr int kRound = J / 16;
+  static constexpr int kJ = J % 16;
+  static constexpr int kWord = kRound == 0   ? kJ
+                               : kRound == 1 ? (1 + 5 * kJ) % 16
+                               : kRound == 2 ? (5 + 3 * kJ) % 16
+                                             : (7 * kJ) % 16;
+  static constexpr int kShift = (kRound == 0   ? 0x16110c07
+                                 : kRound == 1 ? 0x140e0905
+                                 : kRound == 2 ? 0x17100b04
+                                               : 0x150f0a06) >> (8 * (J % 4)) & 0xff;
+  static constexpr uint32_t kLut = kRound == 0   ? LUT_CHOOSE
+                                   : kRound == 1 ? LUT_MD5_G
+                                   : kRound == 2 ? LUT_XOR3
+                                                 : LUT_MD5_I;
+  static constexpr int kA = (4 - J % 4) % 4;  // the register this step updates
+};
 
-// Round 2's G(x,y,z) = (x & z) | (y & ~z): LUT built with x->a, y->b, z->c.
+template <int J, bool F>
+__device__ __forceinline__ void md5_step(uint32_t (&r)[4], const uint32_t (&X)[16],
+                                         const MulConsts& mc) {
+  using S = Md5Step<J>;
+  constexpr uint32_t T[64] = {HB_MD5_T_TABLE};
+  uint32_t& a = r[S::kA];
+  const uint32_t b = r[(S::kA + 1) % 4], c = r[(S::kA + 2) % 4], d = r[(S::kA + 3) % 4];
+  a += X[S::kWord] + T[J];
+  a = add_f<F>(lop3<S::kLut>(b, c, d), a, mc);
+  if constexpr (J % 2 == 0)
+    a = rotl_add_f<S::kShift, F>(a, b, mc);
+  else
+    a = add_f<F>(rotl<S::kShift>(a), b, mc);
+}
+
+template <int J, bool F>
+__device__ __forceinline__ void md5_steps(uint32_t (&r)[4], const uint32_t (&X)[16],
+                                          const MulConsts& mc) {
+  if constexpr (J < 64) {
+    md5_step<J, F>(r, X, mc);
+    md5_steps<J + 1, F>(r, X, mc);
+  }
+}
+
+template <bool F = kMd5Fma>
 __device__ __forceinline__ void md5_compress(uint32_t (&st)[8], const uint32_t (&X)[16],
                                              const MulConsts& mc) {
-  constexpr uint32_t T[64] = {HB_MD5_T_TABLE};
-  uint32_t a = st[0], b = st[1], c = st[2], d = st[3];
-  // Round 1: F, words in order, shifts 7 12 17 22.
-  HB_MD5_OP(LUT_CHOOSE, a, b, c, d, X[0], T[0], 7, 1);
-  HB_MD5_OP(LUT_CHOOSE, d, a, b, c, X[1], T[1], 12, 0);
-  HB_MD5_OP(LUT_CHOOSE, c, d, a, b, X[2], T[2], 17, 1);
-  HB_MD5_OP(LUT_CHOOSE, b, c, d, a, X[3], T[3], 22, 0);
-  HB_MD5_OP(LUT_CHOOSE, a, b, c, d, X[4], T[4], 7, 1);
-  HB_MD5_OP(LUT_CHOOSE, d, a, b, c, X[5], T[5], 12, 0);
-  HB_MD5_OP(LUT_CHOOSE, c, d, a, b, X[6], T[6], 17, 1);
-  HB_MD5_OP(LUT_CHOOSE, b, c, d, a, X[7], T[7], 22, 0);
-  HB_MD5_OP(LUT_CHOOSE, a, b, c, d, X[8], T[8], 7, 1);
-  HB_MD5_OP(LUT_CHOOSE, d, a, b, c, X[9], T[9], 12, 0);
-  HB_MD5_OP(LUT_CHOOSE, c, d, a, b, X[10], T[10], 17, 1);
-  HB_MD5_OP(LUT_CHOOSE, b, c, d, a, X[11], T[11], 22, 0);
-  HB_MD5_OP(LUT_CHOOSE, a, b, c, d, X[12], T[12], 7, 1);
-  HB_MD5_OP(LUT_CHOOSE, d, a, b, c, X[13], T[13], 12, 0);
-  HB_MD5_OP(LUT_CHOOSE, c, d, a, b, X[14], T[14], 17, 1);
-  HB_MD5_OP(LUT_CHOOSE, b, c, d, a, X[15], T[15], 22, 0);
-  // Round 2: G, words 1 + 5j mod 16, shifts 5 9 14 20.
-  HB_MD5_OP(LUT_MD5_G, a, b, c, d, X[1], T[16], 5, 1);
-  HB_MD5_OP(LUT_MD5_G, d, a, b, c, X[6], T[17], 9, 0);
-  HB_MD5_OP(LUT_MD5_G, c, d, a, b, X[11], T[18], 14, 1);
-  HB_MD5_OP(LUT_MD5_G, b, c, d, a, X[0], T[19], 20, 0);
-  HB_MD5_OP(LUT_MD5_G, a, b, c, d, X[5], T[20], 5, 1);
-  HB_MD5_OP(LUT_MD5_G, d, a, b, c, X[10], T[21], 9, 0);
-  HB_MD5_OP(LUT_MD5_G, c, d, a, b, X[15], T[22], 14, 1);
-  HB_MD5_OP(LUT_MD5_G, b, c, d, a, X[4], T[23], 20, 0);
-  HB_MD5_OP(LUT_MD5_G, a, b, c, d, X[9], T[24], 5, 1);
-  HB_MD5_OP(LUT_MD5_G, d, a, b, c, X[14], T[25], 9, 0);
-  HB_MD5_OP(LUT_MD5_G, c, d, a, b, X[3], T[26], 14, 1);
-  HB_MD5_OP(LUT_MD5_G, b, c, d, a, X[8], T[27], 20, 0);
-  HB_MD5_OP(LUT_MD5_G, a, b, c, d, X[13], T[28], 5, 1);
-  HB_MD5_OP(LUT_MD5_G, d, a, b, c, X[2], T[29], 9, 0);
-  HB_MD5_OP(LUT_MD5_G, c, d, a, b, X[7], T[30], 14, 1);
-  HB_MD5_OP(LUT_MD5_G, b, c, d, a, X[12], T[31], 20, 0);
-  // Round 3: H, words 5 + 3j mod 16, shifts 4 11 16 23.
-  HB_MD5_OP(LUT_XOR3, a, b, c, d, X[5], T[32], 4, 1);
-  HB_MD5_OP(LUT_XOR3, d, a, b, c, X[8], T[33], 11, 0);
-  HB_MD5_OP(LUT_XOR3, c, d, a, b, X[11], T[34], 16, 1);
-  HB_MD5_OP(LUT_XOR3, b, c, d, a, X[14], T[35], 23, 0);
-  HB_MD5_OP(LUT_XOR3, a, b, c, d, X[1], T[36], 4, 1);
-  HB_MD5_OP(LUT_XOR3, d, a, b, c, X[4], T[37], 11, 0);
-  HB_MD5_OP(LUT_XOR3, c, d, a, b, X[7], T[38], 16, 1);
-  HB_MD5_OP(LUT_XOR3, b, c, d, a, X[10], T[39], 23, 0);
-  HB_MD5_OP(LUT_XOR3, a, b, c, d, X[13], T[40], 4, 1);
-  HB_MD5_OP(LUT_XOR3, d, a, b, c, X[0], T[41], 11, 0);
-  HB_MD5_OP(LUT_XOR3, c, d, a, b, X[3], T[42], 16, 1);
-  HB_MD5_OP(LUT_XOR3, b, c, d, a, X[6], T[43], 23, 0);
-  HB_MD5_OP(LUT_XOR3, a, b, c, d, X[9], T[44], 4, 1);
-  HB_MD5_OP(LUT_XOR3, d, a, b, c, X[12], T[45], 11, 0);
-  HB_MD5_OP(LUT_XOR3, c, d, a, b, X[15], T[46], 16, 1);
-  HB_MD5_OP(LUT_XOR3, b, c, d, a, X[2], T[47], 23, 0);
-  // Round 4: I, words 7j mod 16, shifts 6 10 15 21.
-  HB_MD5_OP(LUT_MD5_I, a, b, c, d, X[0], T[48], 6, 1);
-  HB_MD5_OP(LUT_MD5_I, d, a, b, c, X[7], T[49], 10, 0);
-  HB_MD5_OP(LUT_MD5_I, c, d, a, b, X[14], T[50], 15, 1);
-  HB_MD5_OP(LUT_MD5_I, b, c, d, a, X[5], T[51], 21, 0);
-  HB_MD5_OP(LUT_MD5_I, a, b, c, d, X[12], T[52], 6, 1);
-  HB_MD5_OP(LUT_MD5_I, d, a, b, c, X[3], T[53], 10, 0);
-  HB_MD5_OP(LUT_MD5_I, c, d, a, b, X[10], T[54], 15, 1);
-  HB_MD5_OP(LUT_MD5_I, b, c, d, a, X[1], T[55], 21, 0);
-  HB_MD5_OP(LUT_MD5_I, a, b, c, d, X[8], T[56], 6, 1);
-  HB_MD5_OP(LUT_MD5_I, d, a, b, c, X[15], T[57], 10, 0);
-  HB_MD5_OP(LUT_MD5_I, c, d, a, b, X[6], T[58], 15, 1);
-  HB_MD5_OP(LUT_MD5_I, b, c, d, a, X[13], T[59], 21, 0);
-  HB_MD5_OP(LUT_MD5_I, a, b, c, d, X[4], T[60], 6, 1);
-  HB_MD5_OP(LUT_MD5_I, d, a, b, c, X[11], T[61], 10, 0);
-  HB_MD5_OP(LUT_MD5_I, c, d, a, b, X[2], T[62], 15, 1);
-  HB_MD5_OP(LUT_MD5_I, b, c, d, a, X[9], T[63], 21, 0);
-  st[0] = add_f<kMd5Fma>(st[0], a, mc);
-  st[1] = add_f<kMd5Fma>(st[1], b, mc);
-  st[2] = add_f<kMd5Fma>(st[2], c, mc);
-  st[3] = add_f<kMd5Fma>(st[3], d, mc);
+  uint32_t r[4] = {st[0], st[1], st[2], st[3]};
+  md5_steps<0, F>(r, X, mc);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) st[i] = add_f<F>(st[i], r[i], mc);
 }
-#undef HB_MD5_OP
 
 // ---------------------------------------------------------------------------
 // SHA-1 (FIPS 180-4).
@@ -249,11 +231,14 @@ __device__ __forceinline__ void sm3_init(uint32_t (&st)[8]) {
 }
 
 // T_j <<< (j mod 32), Sec. 4.2 and 5.3.3, folded at compile time.
+__host__ __device__ constexpr uint32_t sm3_t_rot(int j) {
+  const uint32_t t = j < 16 ? 0x79cc4519u : 0x7a879d8au;
+  const int s = j % 32;
+  return s == 0 ? t : (uint32_t)((t << s) | (t >> (32 - s)));
+}
 template <int J>
 __device__ __forceinline__ constexpr uint32_t sm3_tj_rot() {
-  constexpr uint32_t t = J < 16 ? 0x79cc4519u : 0x7a879d8au;
-  constexpr int s = J % 32;
-  return s == 0 ? t : (uint32_t)((t << s) | (t >> (32 - s)));
+  return sm3_t_rot(J);
 }
 
 __device__ __forceinline__ uint32_t sm3_p0(uint32_t x, const MulConsts& mc) {
@@ -271,8 +256,9 @@ __device__ __forceinline__ uint32_t sm3_p1(uint32_t x, const MulConsts& mc) {
 // the Boolean functions, P0 and SS1's sum on the ALU; the six adds of TT1 and
 // TT2 on the FMA pipe; the expansion (three LOP3, four rotations) on the ALU.
 template <int J>
-__device__ __forceinline__ void sm3_rounds(uint32_t (&v)[8], uint32_t (&W)[16], const MulConsts& mc) {
-  if constexpr (J < 64) {
+__device__ __forceinline__ void sm3_round_t(uint32_t (&v)[8], uint32_t (&W)[16], const MulConsts& mc,
+                                            uint32_t tj) {
+  {
     constexpr int M = J + 4;  // index of the word produced this round
     if constexpr (M >= 16 && M < 68) {
       const uint32_t x = lop3<LUT_XOR3>(W[(M - 16) & 15], W[(M - 9) & 15],
@@ -293,9 +279,9 @@ __device__ __forceinline__ void sm3_rounds(uint32_t (&v)[8], uint32_t (&W)[16], 
     const uint32_t a12 = rotl_f<12, (kSm3Rot & 4u) != 0>(A, mc);
     uint32_t s0;
     if constexpr ((kSm3Rot & 256u) != 0)
-      s0 = add_f<true>(a12, add_f<true>(E, sm3_tj_rot<J>(), mc), mc);
+      s0 = add_f<true>(a12, add_f<true>(E, tj, mc), mc);
     else
-      s0 = a12 + E + sm3_tj_rot<J>();
+      s0 = a12 + E + tj;
     const uint32_t ss1 = rotl_f<7, (kSm3Rot & 8u) != 0>(s0, mc);
     const uint32_t ss2 = ss1 ^ a12;
     uint32_t ff, gg;
@@ -316,10 +302,59 @@ __device__ __forceinline__ void sm3_rounds(uint32_t (&v)[8], uint32_t (&W)[16], 
     G = rotl_f<19, (kSm3Rot & 2u) != 0>(F, mc);
     F = E;
     E = sm3_p0(tt2, mc);
-    sm3_rounds<J + 1>(v, W, mc);
   }
 }
 
+template <int J>
+__device__ __forceinline__ void sm3_round(uint32_t (&v)[8], uint32_t (&W)[16], const MulConsts& mc) {
+  sm3_round_t<J>(v, W, mc, sm3_tj_rot<J>());
+}
+
+template <int J, int END = 64>
+__device__ __forceinline__ void sm3_rounds(uint32_t (&v)[8], uint32_t (&W)[16], const MulConsts& mc) {
+  if constexpr (J < END) {
+    sm3_round<J>(v, W, mc);
+    sm3_rounds<J + 1, END>(v, W, mc);
+  }
+}
+
+// The rolled form of rounds 16-63: every round from 16 on has the same shape
+// (Boolean functions, expansion) and the ring positions repeat every 16
+// rounds, so rounds 16-31, 32-47 and 48-63 are one 16-round body run three
+// times.  Only the constant T_j <<< (j mod 32) changes between passes; the
+// body reads it from a constant-memory table at a warp-uniform index.  The
+// rolled code is half the size: worth it where the three algorithms
+// share one kernel (its instruction footprint is what the SM's instruction
+// cache has to hold), not in the SM3-only kernel, whose unrolled form lets
+// the scheduler overlap rounds across pass boundaries.
+//   HB_SM3_ROLLED  0: unrolled everywhere  1: rolled in the three-algorithm
+//                  kernel only (default)  2: rolled everywhere
+#ifndef HB_SM3_ROLLED
+#define HB_SM3_ROLLED 1
+#endif
+
+// T_j <<< (j mod 32) for j = 16..63 (Sec. 4.2, 5.3.3), for the rolled form.
+struct Sm3TTable {
+  uint32_t t[48];
+};
+__host__ __device__ constexpr Sm3TTable make_sm3_t_table() {
+  Sm3TTable tb{};
+  for (int j = 16; j < 64; ++j) tb.t[j - 16] = sm3_t_rot(j);
+  return tb;
+}
+static __constant__ Sm3TTable kSm3TRot = make_sm3_t_table();
+
+// Rounds 16 + 16 * pass + R .. 16 + 16 * pass + 15.
+template <int R>
+__device__ __forceinline__ void sm3_pass(uint32_t (&v)[8], uint32_t (&W)[16], const MulConsts& mc,
+                                         int pass) {
+  if constexpr (R < 16) {
+    sm3_round_t<16 + R>(v, W, mc, kSm3TRot.t[16 * pass + R]);
+    sm3_pass<R + 1>(v, W, mc, pass);
+  }
+}
+
+template <bool ROLLED = (HB_SM3_ROLLED == 2)>
 __device__ __forceinline__ void sm3_compress(uint32_t (&st)[8], const uint32_t (&X)[16],
                                              const MulConsts& mc) {
   uint32_t W[16];
@@ -328,9 +363,51 @@ __device__ __forceinline__ void sm3_compress(uint32_t (&st)[8], const uint32_t (
   uint32_t v[8];
 #pragma unroll
   for (int i = 0; i < 8; ++i) v[i] = st[i];
-  sm3_rounds<0>(v, W, mc);
+  if constexpr (ROLLED) {
+    sm3_rounds<0, 16>(v, W, mc);
+#pragma unroll 1
+    for (int pass = 0; pass < 3; ++pass) sm3_pass<0>(v, W, mc, pass);
+  } else {
+    sm3_rounds<0>(v, W, mc);
+  }
 #pragma unroll
   for (int i = 0; i < 8; ++i) st[i] ^= v[i];
+}
+
+// ---------------------------------------------------------------------------
+// MD5 and SM3 of the same block, step J of one beside round J of the other.
+// Both run 64 steps; MD5's is one dependent chain, SM3's round has several
+// independent parts, so issuing them side by side gives the scheduler work
+// for the MD5 chain's latency.  X holds the block's words as MD5 reads them
+// (little-endian), Y the same words big-endian for SM3.
+
+template <int J, bool F>
+__device__ __forceinline__ void md5_sm3_steps(uint32_t (&r)[4], const uint32_t (&X)[16],
+                                              uint32_t (&v)[8], uint32_t (&W)[16],
+                                              const MulConsts& mc) {
+  if constexpr (J < 64) {
+    md5_step<J, F>(r, X, mc);
+    sm3_round<J>(v, W, mc);
+    md5_sm3_steps<J + 1, F>(r, X, v, W, mc);
+  }
+}
+
+template <bool F>
+__device__ __forceinline__ void md5_sm3_compress(uint32_t (&md5)[8], uint32_t (&sm3)[8],
+                                                 const uint32_t (&X)[16], const uint32_t (&Y)[16],
+                                                 const MulConsts& mc) {
+  uint32_t r[4] = {md5[0], md5[1], md5[2], md5[3]};
+  uint32_t W[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) W[i] = Y[i];
+  uint32_t v[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = sm3[i];
+  md5_sm3_steps<0, F>(r, X, v, W, mc);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) md5[i] = add_f<F>(md5[i], r[i], mc);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) sm3[i] ^= v[i];
 }
 
 // ---------------------------------------------------------------------------
@@ -346,9 +423,9 @@ __device__ __forceinline__ void alg_init(uint32_t (&st)[8]) {
 template <int ALG>
 __device__ __forceinline__ void alg_compress(uint32_t (&st)[8], const uint32_t (&X)[16],
                                              const MulConsts& mc) {
-  if constexpr (ALG == HB_MD5) md5_compress(st, X, mc);
+  if constexpr (ALG == HB_MD5) md5_compress<>(st, X, mc);
   else if constexpr (ALG == HB_SHA1) sha1_compress(st, X, mc);
-  else sm3_compress(st, X, mc);
+  else sm3_compress<>(st, X, mc);
 }
 
 // Digest words in memory order for the 32-byte slot (zero fill after the

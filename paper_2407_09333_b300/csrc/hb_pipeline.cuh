@@ -331,7 +331,18 @@ __device__ __forceinline__ void process_block_all(AllState& st, uint32_t slot, u
     sha1_init(st.sha1);
     sm3_init(st.sm3);
   }
-  md5_compress(st.md5, w, mc);
+#if HB_FUSED_INTERLEAVE
+  uint32_t y[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) y[i] = bswap32(w[i]);
+  if (final_block) {
+    y[14] = hi;
+    y[15] = lo;
+  }
+  sha1_compress(st.sha1, y, mc);
+  md5_sm3_compress<kMd5FusedFma>(st.md5, st.sm3, w, y, mc);
+#else
+  md5_compress<kMd5FusedFma>(st.md5, w, mc);
 #pragma unroll
   for (int i = 0; i < 16; ++i) w[i] = bswap32(w[i]);
   if (final_block) {
@@ -339,7 +350,8 @@ __device__ __forceinline__ void process_block_all(AllState& st, uint32_t slot, u
     w[15] = lo;
   }
   sha1_compress(st.sha1, w, mc);
-  sm3_compress(st.sm3, w, mc);
+  sm3_compress<HB_SM3_ROLLED != 0>(st.sm3, w, mc);
+#endif
   if (final_block) {
     uint8_t* dst = records + msg * HB_ALL_RECORD_BYTES;
     uint32_t o[8];
