@@ -603,12 +603,16 @@ def e2e_measure(args, batch, mixed, api, torch, dist):
     len_h = torch.from_numpy(batch.lengths.view(np.int32)).pin_memory()
     algs_h = torch.from_numpy(batch.algs).pin_memory() if mixed else None
     fused = not mixed and not args.separate
-    out_h = torch.empty((n, 96 if fused else 32), dtype=torch.uint8).pin_memory()
     calls = [None] if mixed else [api.ALL] if fused else [0, 1, 2]
+    # digests come back packed (16 / 20 / 32 bytes, 68 for all three) unless
+    # the batch is mixed (variable sizes) or --e2e-slots asks for the slots
+    pack = not mixed and not args.e2e_slots
+    outs = {a: torch.empty((n, api.host_digest_bytes(a, pack)), dtype=torch.uint8).pin_memory()
+            for a in calls}
 
     def step():
         for a in calls:
-            api.hash_batch_host(a, packed_h, off_h, len_h, out_h, algs=algs_h)
+            api.hash_batch_host(a, packed_h, off_h, len_h, outs[a], algs=algs_h, packed_digests=pack)
 
     if args.host_limit_mib:
         api.set_host_memory_limit(args.host_limit_mib << 20)
@@ -638,8 +642,10 @@ def e2e_measure(args, batch, mixed, api, torch, dist):
     return {"value": job_rate(dist, hashed * steps, dt) / 1e9, "unit": "GB/s",
             "device_memory_limit_bytes": args.host_limit_mib << 20,
             "h2d_bytes_per_step": len(calls) * per_call_in,
-            "d2h_bytes_per_step": out_h.numel() * len(calls), "steps": steps,
-            "api": "hash_batch_host (pinned host buffers)"}
+            "d2h_bytes_per_step": sum(o.numel() for o in outs.values()), "steps": steps,
+            "api": "hash_batch_host%s (pinned host buffers)" % ("_packed" if pack else ""),
+            "digests": ("packed: digest bytes only" if pack else
+                        "32-byte slots" + (" (96-byte records)" if fused else ""))}
 
 
 def plain_equal_bytes_gbs(api, torch, lengths, algs, pool, reps=3, max_msgs=1 << 18):
@@ -951,6 +957,8 @@ def main(argv=None):
     p.add_argument("--pool-mib", type=int, default=2048, help="random-byte pool for requests (c5)")
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--e2e-steps", type=int, default=10)
+    p.add_argument("--e2e-slots", action="store_true",
+                   help="e2e copies back 32-byte slots instead of packed digests")
     p.add_argument("--shape", type=int, default=None,
                    help="fixed launch shape index instead of the autotuner's choice")
     p.add_argument("--buckets", default="",

@@ -399,6 +399,24 @@ int hash_batch_host(int alg, const uint8_t *algs_host, const uint8_t *packed_hos
                     void *stream);
 
 /*
+ * hash_batch_host_packed -- hash_batch_host with the digests packed back to
+ * back on the host: message i's digest (RFC 1321 Sec. 3.5, FIPS 180-4
+ * Sec. 6.1.2, GB/T 32905 Sec. 5.4: 16, 20 or 32 bytes in the standard's byte
+ * order) at digests_host + i * hash_digest_size(alg), no zero fill; for
+ * HB_ALL, i * HB_ALL_DIGEST_BYTES holds the MD5, SHA-1 and SM3 digests in
+ * that order.  The slots are packed on the device before the copy back, so
+ * the copy carries digest bytes only (the host path is bound by the PCIe
+ * link, and for one-block messages the 96-byte records are most of what it
+ * moves).  One algorithm or HB_ALL (there is no per-message algorithm array:
+ * the sizes would vary).  digests_host holds n times that many bytes.
+ * Otherwise, including device memory, windows and errors, as hash_batch_host.
+ */
+#define HB_ALL_DIGEST_BYTES 68
+int hash_batch_host_packed(int alg, const uint8_t *packed_host, uint64_t packed_len,
+                           const uint64_t *offsets_host, const uint32_t *lengths_host,
+                           uint64_t n, uint8_t *digests_host, void *stream);
+
+/*
  * hash_device_status -- synchronises `stream`, then returns the OR of the
  * HB_DEV_* bits recorded on the current device since the last call, and
  * clears them.  *status_out receives the bits.

@@ -17,6 +17,7 @@ MD5, SHA1, SM3 = 0, 1, 2
 TUNE_MIXED = 3
 ALL = 4                 # all three algorithms per message (hash_batch_all)
 ALL_RECORD_BYTES = 96
+ALL_DIGEST_BYTES = 68
 SLOT_BYTES = 32
 ALG_NAMES = {MD5: "md5", SHA1: "sha1", SM3: "sm3"}
 ALG_CODES = {v: k for k, v in ALG_NAMES.items()}
@@ -44,6 +45,7 @@ _SIGNATURES = {
     "hash_batch_segments": (_c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _c_u64, _vp, _vp]),
     "hash_batch_check_bounds": (_c_int, [_vp, _vp, _c_u64, _c_u64, _vp, _vp]),
     "hash_batch_host": (_c_int, [_c_int, _vp, _vp, _c_u64, _vp, _vp, _c_u64, _vp, _vp]),
+    "hash_batch_host_packed": (_c_int, [_c_int, _vp, _c_u64, _vp, _vp, _c_u64, _vp, _vp]),
     "hash_device_status": (_c_int, [_vp, ctypes.POINTER(_c_int)]),
     "hash_release_device": (_c_int, []),
     "hash_tune_shapes": (_c_int, []),
@@ -316,22 +318,37 @@ def _host_ptr(a, name):
     return ctypes.c_void_p(a.ctypes.data)
 
 
-def hash_batch_host(alg, packed, offsets, lengths, out, algs=None, stream=None):
+def host_digest_bytes(alg, packed_digests: bool = False) -> int:
+    """Bytes per message that hash_batch_host writes to `out`."""
+    if packed_digests:
+        return ALL_DIGEST_BYTES if alg == ALL else digest_size(alg)
+    return ALL_RECORD_BYTES if alg == ALL else SLOT_BYTES
+
+
+def hash_batch_host(alg, packed, offsets, lengths, out, algs=None, stream=None,
+                    packed_digests: bool = False):
     """End-to-end call from host buffers (pinned for full speed).  `out`
-    holds n 32-byte slots, or n 96-byte records for alg == ALL."""
+    holds n 32-byte slots, or n 96-byte records for alg == ALL; with
+    packed_digests, the digests back to back (16 / 20 / 32 bytes, 68 for
+    ALL), which is what crosses the PCIe link."""
     n = int(len(offsets))
     packed_len = int(packed.numel() if hasattr(packed, "numel") else packed.size)
-    rec = ALL_RECORD_BYTES if alg == ALL else SLOT_BYTES
+    if packed_digests and algs is not None:
+        raise ValueError("packed digests need one algorithm (or ALL) for the whole batch")
+    rec = host_digest_bytes(alg, packed_digests)
     out_bytes = int(out.numel() * out.element_size()) if hasattr(out, "numel") else int(out.nbytes)
     if out_bytes < n * rec or len(lengths) != n or (algs is not None and len(algs) != n):
         raise ValueError("out must hold %d bytes per message; offsets, lengths (and algs) "
                          "one entry per message" % rec)
-    rc = lib().hash_batch_host(
-        -1 if alg is None else int(alg), _host_ptr(algs, "algs"),
-        _host_ptr(packed, "packed") if packed_len else None, packed_len,
-        _host_ptr(offsets, "offsets"), _host_ptr(lengths, "lengths"), n,
-        _host_ptr(out, "out"), _stream_handle(stream))
-    _check(rc, "hash_batch_host")
+    src = (_host_ptr(packed, "packed") if packed_len else None, packed_len,
+           _host_ptr(offsets, "offsets"), _host_ptr(lengths, "lengths"), n,
+           _host_ptr(out, "out"), _stream_handle(stream))
+    a = -1 if alg is None else int(alg)
+    if packed_digests:
+        rc = lib().hash_batch_host_packed(a, *src)
+    else:
+        rc = lib().hash_batch_host(a, _host_ptr(algs, "algs"), *src)
+    _check(rc, "hash_batch_host_packed" if packed_digests else "hash_batch_host")
     return out
 
 

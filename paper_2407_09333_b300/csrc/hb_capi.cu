@@ -69,7 +69,7 @@ struct Ctx {
   cudaEvent_t ws_event = nullptr;        // last use of `ws`
   bool ws_used = false;
   // host-buffer path
-  DeviceBuf h_packed, h_off, h_len, h_algs, h_dig, h_flag;
+  DeviceBuf h_packed, h_off, h_len, h_algs, h_dig, h_flag, h_cmp;
   int* flag_host = nullptr;              // pinned: [0] bounds, [1] ends not monotone
   // pipelined host path: hashing and copy-out streams, per-chunk events
   cudaStream_t host_hash = nullptr, host_out = nullptr;
@@ -447,6 +447,11 @@ constexpr uint64_t kWinMsgBytes = 8 + 4 + 1 + HB_ALL_RECORD_BYTES;  // largest r
 
 uint64_t align_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
 
+// Host bytes per message in the packed digest layout.
+uint64_t packed_digest_bytes(int alg) {
+  return alg == HB_ALL ? HB_ALL_DIGEST_BYTES : hash_digest_size(alg);
+}
+
 // Batches larger than the host-path limit: windows of consecutive messages
 // whose bytes (from the previous window's last message end to their own last
 // end) and metadata fit half the limit go through two alternating device
@@ -457,11 +462,13 @@ uint64_t align_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
 int host_windowed(Ctx* c, int alg, const uint8_t* algs_host, const uint8_t* packed_host,
                   uint64_t packed_len, const uint64_t* offsets_host,
                   const uint32_t* lengths_host, uint64_t n, uint8_t* digests_host,
-                  cudaStream_t s, bool* layout_failed) {
+                  cudaStream_t s, bool pack, bool* layout_failed) {
   *layout_failed = false;
   const uint64_t rec = (alg == HB_ALL && !algs_host) ? HB_ALL_RECORD_BYTES : HB_SLOT_BYTES;
+  const uint64_t orec = pack ? packed_digest_bytes(alg) : rec;  // host bytes per message
+  const uint64_t msg_bytes = kWinMsgBytes + (pack ? orec : 0);
   const uint64_t B = g_host_limit / 2;  // bytes per window buffer
-  const uint64_t max_msgs = B / (2 * kWinMsgBytes);
+  const uint64_t max_msgs = B / (2 * msg_bytes);
   if (max_msgs == 0) return HB_ERR_TOO_LARGE;
   auto end_of = [&](uint64_t i) { return offsets_host[i] + lengths_host[i]; };
   cudaError_t e;
@@ -485,7 +492,7 @@ int host_windowed(Ctx* c, int alg, const uint8_t* algs_host, const uint8_t* pack
     uint64_t lo = m + 1, hi = std::min<uint64_t>(n, m + max_msgs);
     auto fits = [&](uint64_t x) {
       const uint64_t re = std::max<uint64_t>(end_of(x - 1), rs);
-      return align_up(re - rs, 256) + kWinMsgBytes * (x - m) + 1024 <= B;
+      return align_up(re - rs, 256) + msg_bytes * (x - m) + 1024 <= B;
     };
     if (!fits(lo)) {
       // nothing may still be writing the caller's buffers when we return
@@ -494,7 +501,7 @@ int host_windowed(Ctx* c, int alg, const uint8_t* algs_host, const uint8_t* pack
       cudaStreamSynchronize(so);
       if (offsets_host[m] > packed_len || lengths_host[m] > packed_len - offsets_host[m])
         return HB_ERR_BOUNDS;
-      if (align_up(lengths_host[m], 256) + kWinMsgBytes + 1024 > B)
+      if (align_up(lengths_host[m], 256) + msg_bytes + 1024 > B)
         return HB_ERR_TOO_LARGE;  // one message larger than a window
       *layout_failed = true;
       return HB_ERR_ARG;          // the message lies too far past the previous window
@@ -512,6 +519,7 @@ int host_windowed(Ctx* c, int alg, const uint8_t* algs_host, const uint8_t* pack
     uint32_t* d_len = reinterpret_cast<uint32_t*>(d_off + cnt);
     uint8_t* d_dig = reinterpret_cast<uint8_t*>(align_up(reinterpret_cast<uint64_t>(d_len + cnt), 256));
     uint8_t* d_algs = d_dig + cnt * rec;
+    uint8_t* d_cmp = reinterpret_cast<uint8_t*>(align_up(reinterpret_cast<uint64_t>(d_algs + cnt), 256));
     // this window's buffer is free once the window two back has been copied out
     if (k >= 2 && cudaStreamWaitEvent(s, c->ev_win_out[j], 0)) return fail();
     if ((re > rs && cudaMemcpyAsync(d_packed, packed_host + rs, re - rs, cudaMemcpyHostToDevice, s)) ||
@@ -528,9 +536,12 @@ int host_windowed(Ctx* c, int alg, const uint8_t* algs_host, const uint8_t* pack
     int rc = host_hash_range(c, alg, algs_host ? d_algs : nullptr, d_packed, d_off, d_len, 0, cnt,
                              d_dig, d_flag, sh);
     if (rc) return rc;
+    if (pack && (e = hb::launch_pack(d_dig, (uint32_t)rec, cnt, d_cmp, (uint32_t)orec,
+                                     grid_for_elementwise(c, cnt * (orec / 4)), sh)))
+      return cuda_fail(e);
     if (cudaEventRecord(c->ev_hashed[k % kHostChunks], sh) ||
         cudaStreamWaitEvent(so, c->ev_hashed[k % kHostChunks], 0) ||
-        cudaMemcpyAsync(digests_host + m * rec, d_dig, cnt * (size_t)rec,
+        cudaMemcpyAsync(digests_host + m * orec, pack ? d_cmp : d_dig, cnt * (size_t)orec,
                         cudaMemcpyDeviceToHost, so) ||
         cudaEventRecord(c->ev_win_out[j], so))
       return fail();
@@ -578,15 +589,19 @@ uint64_t hash_set_host_memory_limit(uint64_t bytes) {
 // the index -- true of any back-to-back layout.  A device check confirms
 // that; when it fails, every message is hashed again once all bytes are in,
 // so the result never depends on the layout.
-int hash_batch_host(int alg, const uint8_t* algs_host, const uint8_t* packed_host,
-                    uint64_t packed_len, const uint64_t* offsets_host,
-                    const uint32_t* lengths_host, uint64_t n, uint8_t* digests_host,
-                    void* stream) {
+// PACK: digests_host takes the digest bytes back to back (packed on the
+// device before the copy back) instead of 32-byte slots / 96-byte records.
+static int host_call(int alg, const uint8_t* algs_host, const uint8_t* packed_host,
+                     uint64_t packed_len, const uint64_t* offsets_host,
+                     const uint32_t* lengths_host, uint64_t n, uint8_t* digests_host,
+                     void* stream, bool pack) {
   if (!algs_host && alg != HB_ALL && hash_digest_size(alg) == 0) return HB_ERR_INVALID_ALG;
   if (n == 0) return HB_OK;
   if (n >= (algs_host ? kMaxMixedN : kMaxPlainN)) return HB_ERR_TOO_LARGE;
-  // digest bytes per message: one slot, or (HB_ALL) a three-slot record
+  // digest bytes per message on the device: one slot, or (HB_ALL) a
+  // three-slot record; on the host the same, or the packed digest bytes
   const uint64_t rec = (alg == HB_ALL && !algs_host) ? HB_ALL_RECORD_BYTES : HB_SLOT_BYTES;
+  const uint64_t orec = pack ? packed_digest_bytes(alg) : rec;
   if (!offsets_host || !lengths_host || !digests_host || (!packed_host && packed_len))
     return HB_ERR_NULL;
   Ctx* c = nullptr;
@@ -601,7 +616,7 @@ int hash_batch_host(int alg, const uint8_t* algs_host, const uint8_t* packed_hos
   if (g_host_limit && footprint > g_host_limit) {
     bool layout_failed = false;
     return host_windowed(c, alg, algs_host, packed_host, packed_len, offsets_host, lengths_host,
-                         n, digests_host, s, &layout_failed);
+                         n, digests_host, s, pack, &layout_failed);
   }
   cudaError_t e;
   if ((e = c->h_packed.reserve(pbytes)) != cudaSuccess ||
@@ -609,7 +624,8 @@ int hash_batch_host(int alg, const uint8_t* algs_host, const uint8_t* packed_hos
       (e = c->h_len.reserve(n * sizeof(uint32_t))) != cudaSuccess ||
       (e = c->h_dig.reserve(n * (size_t)rec)) != cudaSuccess ||
       (e = c->h_flag.reserve(2 * sizeof(int))) != cudaSuccess ||
-      (algs_host && (e = c->h_algs.reserve(n)) != cudaSuccess))
+      (algs_host && (e = c->h_algs.reserve(n)) != cudaSuccess) ||
+      (pack && (e = c->h_cmp.reserve(n * (size_t)orec)) != cudaSuccess))
     return cuda_fail(e);
   if (algs_host && (rc = reserve_ws(c, n))) return rc;
   uint8_t* d_packed = static_cast<uint8_t*>(c->h_packed.p);
@@ -618,6 +634,14 @@ int hash_batch_host(int alg, const uint8_t* algs_host, const uint8_t* packed_hos
   uint8_t* d_dig = static_cast<uint8_t*>(c->h_dig.p);
   int* d_flag = static_cast<int*>(c->h_flag.p);
   uint8_t* d_algs = algs_host ? static_cast<uint8_t*>(c->h_algs.p) : nullptr;
+  uint8_t* d_cmp = pack ? static_cast<uint8_t*>(c->h_cmp.p) : nullptr;
+  // the bytes copied back for messages [m, m + cnt), packed first if asked
+  auto out_range = [&](uint64_t m, uint64_t cnt, cudaStream_t st) -> const uint8_t* {
+    if (!pack) return d_dig + m * rec;
+    e = hb::launch_pack(d_dig + m * rec, (uint32_t)rec, cnt, d_cmp + m * orec, (uint32_t)orec,
+                        grid_for_elementwise(c, cnt * (orec / 4)), st);
+    return e == cudaSuccess ? d_cmp + m * orec : nullptr;
+  };
   cudaStream_t sh = c->host_hash, so = c->host_out;
   auto fail = [&]() { return cuda_fail(cudaGetLastError()); };
 
@@ -655,10 +679,12 @@ int hash_batch_host(int alg, const uint8_t* algs_host, const uint8_t* packed_hos
     if ((rc = host_hash_range(c, alg, d_algs, d_packed, d_off, d_len, prev_m, lo - prev_m, d_dig,
                               d_flag, sh)))
       return rc;
+    const uint8_t* src = out_range(prev_m, lo - prev_m, sh);
+    if (!src) return cuda_fail(e);
     if (cudaEventRecord(c->ev_hashed[k], sh) || cudaStreamWaitEvent(so, c->ev_hashed[k], 0))
       return fail();
-    if (lo > prev_m && cudaMemcpyAsync(digests_host + prev_m * rec, d_dig + prev_m * rec,
-                                       (lo - prev_m) * (size_t)rec,
+    if (lo > prev_m && cudaMemcpyAsync(digests_host + prev_m * orec, src,
+                                       (lo - prev_m) * (size_t)orec,
                                        cudaMemcpyDeviceToHost, so))
       return fail();
     prev_b = b;
@@ -677,11 +703,28 @@ int hash_batch_host(int alg, const uint8_t* algs_host, const uint8_t* packed_hos
     // ends decrease somewhere: every byte is in now, hash everything again
     if ((rc = host_hash_range(c, alg, d_algs, d_packed, d_off, d_len, 0, n, d_dig, d_flag, s)))
       return rc;
-    if (cudaMemcpyAsync(digests_host, d_dig, n * (size_t)rec, cudaMemcpyDeviceToHost, s) ||
+    const uint8_t* src = out_range(0, n, s);
+    if (!src) return cuda_fail(e);
+    if (cudaMemcpyAsync(digests_host, src, n * (size_t)orec, cudaMemcpyDeviceToHost, s) ||
         cudaStreamSynchronize(s))
       return fail();
   }
   return HB_OK;
+}
+
+int hash_batch_host(int alg, const uint8_t* algs_host, const uint8_t* packed_host,
+                    uint64_t packed_len, const uint64_t* offsets_host,
+                    const uint32_t* lengths_host, uint64_t n, uint8_t* digests_host,
+                    void* stream) {
+  return host_call(alg, algs_host, packed_host, packed_len, offsets_host, lengths_host, n,
+                   digests_host, stream, false);
+}
+
+int hash_batch_host_packed(int alg, const uint8_t* packed_host, uint64_t packed_len,
+                           const uint64_t* offsets_host, const uint32_t* lengths_host, uint64_t n,
+                           uint8_t* digests_host, void* stream) {
+  return host_call(alg, nullptr, packed_host, packed_len, offsets_host, lengths_host, n,
+                   digests_host, stream, true);
 }
 
 int hash_digits(int alg, uint64_t first, uint64_t count, uint8_t* digests_out, void* stream) {

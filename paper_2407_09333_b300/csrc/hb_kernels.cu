@@ -10,8 +10,9 @@
 //                      counter longest-first (hash_batch_mixed)
 //   hb_digits_kernel   the paper's nine-digit workload generated in registers
 //   hb_bounds_kernel   offsets/lengths against the packed buffer size
-//   hb_monotone_kernel, hb_rebase_kernel   host-path helpers (chunk check,
-//                      window-relative offsets)
+//   hb_monotone_kernel, hb_rebase_kernel, hb_pack_kernel   host-path helpers
+//                      (chunk check, window-relative offsets, digests packed
+//                      back to back for the copy to the host)
 //   hb_set_count_kernel, hb_gather_kernel  batch size for captured graphs,
 //                      byte-range packing
 //   hb_int_peak_kernel integer-issue microbenchmark (measurement only)
@@ -494,6 +495,31 @@ __global__ void hb_rebase_kernel(uint64_t* offsets, uint64_t n, uint64_t base) {
 cudaError_t launch_rebase(uint64_t* offsets, uint64_t n, uint64_t base, int grid,
                           cudaStream_t stream) {
   hb_rebase_kernel<<<grid, 256, 0, stream>>>(offsets, n, base);
+  return cudaGetLastError();
+}
+
+// Digest bytes of 32-byte slots (or 96-byte records of the three algorithms)
+// packed back to back: out word w is word k = w mod q of message i = w / q,
+// q = dsz / 4; in a record, words 0-3 are MD5's, 8-12 SHA-1's, 16-23 SM3's.
+// One thread per output word, so the stores are coalesced.
+__global__ void hb_pack_kernel(const uint32_t* __restrict__ slots, uint32_t rec_words,
+                               uint64_t n, uint32_t* __restrict__ out, uint32_t q, int all) {
+  const uint64_t total = n * q;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; w < total; w += stride) {
+    const uint64_t i = w / q;
+    const uint32_t k = (uint32_t)(w - i * q);
+    const uint32_t src = !all ? k : k < 4 ? k : k < 9 ? 8 + (k - 4) : 16 + (k - 9);
+    out[w] = slots[i * rec_words + src];
+  }
+}
+
+cudaError_t launch_pack(const uint8_t* slots, uint32_t rec, uint64_t n, uint8_t* out, uint32_t dsz,
+                        int grid, cudaStream_t stream) {
+  if (n == 0) return cudaSuccess;
+  hb_pack_kernel<<<grid, 256, 0, stream>>>(reinterpret_cast<const uint32_t*>(slots), rec / 4, n,
+                                           reinterpret_cast<uint32_t*>(out), dsz / 4,
+                                           rec == HB_ALL_RECORD_BYTES ? 1 : 0);
   return cudaGetLastError();
 }
 

@@ -125,6 +125,10 @@ cudaError_t launch_bounds(const uint64_t* offsets, const uint32_t* lengths, uint
 cudaError_t launch_digits(int alg, uint64_t first, uint64_t count, uint8_t* digests, int grid,
                           cudaStream_t stream);
 // offsets[i] -= base for i < n.
+// Packs n slots of `rec` bytes (32, or 96 for three-algorithm records) into
+// n x dsz bytes of digest (dsz = 16, 20, 32, or 68 for a record).
+cudaError_t launch_pack(const uint8_t* slots, uint32_t rec, uint64_t n, uint8_t* out, uint32_t dsz,
+                        int grid, cudaStream_t stream);
 cudaError_t launch_rebase(uint64_t* offsets, uint64_t n, uint64_t base, int grid,
                           cudaStream_t stream);
 // flag = 1 when offsets[i] + lengths[i] decreases anywhere in index order.

@@ -57,6 +57,9 @@ def test_argument_checks_before_cuda(lib):
     assert lib.hash_batch_host(5, None, p, 1, p, p, 1, p, None) == -1
     assert lib.hash_batch_host(0, None, p, 1, None, p, 1, p, None) == -2
     assert lib.hash_batch_host(0, None, None, 0, None, None, 0, None, None) == 0
+    assert lib.hash_batch_host_packed(3, p, 1, p, p, 1, p, None) == -1
+    assert lib.hash_batch_host_packed(0, p, 1, None, p, 1, p, None) == -2
+    assert lib.hash_batch_host_packed(0, None, 0, None, None, 0, None, None) == 0
 
 
 def test_tuning_shape_table(lib):

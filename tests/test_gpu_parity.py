@@ -311,6 +311,49 @@ def test_host_path_streams_batches_over_the_memory_limit(hb, oracle_mod):
     _assert_slots_equal(out[:50], _oracle_slots(oracle_mod, ref, 2, np.arange(50)), "after")
 
 
+@pytest.mark.parametrize("layout", ["packed", "shuffled"])
+def test_host_path_packed_digests(hb, oracle_mod, layout):
+    # Digests back to back on the host (16 / 20 / 32 bytes, 68 for all three):
+    # the same bytes as the slots without their zero fill, over several copy
+    # chunks, with message ends out of order (hashed again) and through the
+    # device-memory windows.
+    rng = np.random.default_rng(41)
+    lens = rng.integers(0, 9000, size=9000).astype(np.uint32)
+    lens[:7] = workloads.BOUNDARY_LENGTHS
+    b = workloads.scattered(lens, seed=42, overlap=False, mixed=False)
+    if layout == "shuffled":
+        perm = rng.permutation(b.n)
+        b = workloads.Batch(b.packed, b.offsets[perm], b.lengths[perm], None)
+    sel = np.arange(0, b.n, 7)
+    want = {alg: _oracle_slots(oracle_mod, b, alg, sel) for alg in ALGS}
+    sizes = {0: 16, 1: 20, 2: 32}
+    for alg in ALGS:
+        out = np.zeros((b.n, sizes[alg]), dtype=np.uint8)
+        hb.hash_batch_host(alg, b.packed, b.offsets, b.lengths, out, packed_digests=True)
+        _assert_slots_equal(out[sel], want[alg][:, :sizes[alg]], "packed %s alg %d" % (layout, alg))
+    out = np.zeros((b.n, hb.ALL_DIGEST_BYTES), dtype=np.uint8)
+    hb.hash_batch_host(hb.ALL, b.packed, b.offsets, b.lengths, out, packed_digests=True)
+    _assert_slots_equal(out[sel], np.concatenate([want[0][:, :16], want[1][:, :20], want[2]], axis=1),
+                        "packed %s all" % layout)
+    if layout == "packed":
+        old = hb.set_host_memory_limit(4 << 20)
+        try:
+            out2 = np.zeros_like(out)
+            hb.hash_batch_host(hb.ALL, b.packed, b.offsets, b.lengths, out2, packed_digests=True)
+            out3 = np.zeros((b.n, 20), dtype=np.uint8)
+            hb.hash_batch_host(1, b.packed, b.offsets, b.lengths, out3, packed_digests=True)
+        finally:
+            hb.set_host_memory_limit(old)
+        assert np.array_equal(out, out2)
+        _assert_slots_equal(out3[sel], want[1][:, :20], "packed windows sha1")
+    with pytest.raises(ValueError):
+        hb.hash_batch_host(0, b.packed, b.offsets, b.lengths, np.zeros((b.n, 8), np.uint8),
+                           packed_digests=True)
+    with pytest.raises(ValueError):
+        hb.hash_batch_host(None, b.packed, b.offsets, b.lengths, np.zeros((b.n, 32), np.uint8),
+                           algs=np.zeros(b.n, np.uint8), packed_digests=True)
+
+
 def test_host_path_rejects_out_of_bounds(hb):
     b = workloads.fixed(100, 40, seed=2)
     offs = b.offsets.copy()
