@@ -5,7 +5,8 @@ stage, cooperative copies): the threads per block, how far ahead each warp
 stages its messages (stages x blocks per stage x 32 lanes x 64 bytes, plus
 alignment slack) and whether a warp copies message by message (cooperative)
 or lane by lane.  For a given algorithm and a representative batch, every
-shape is timed with CUDA events on the caller's stream and the fastest is
+shape is timed with CUDA events on the caller's stream, the three fastest
+are timed again in turns (median of several launches), and the winner is
 installed in the library (hash_tune_set); the ragged path also tunes its
 bucketing and its resident warps per SM.  Results are cached in JSON keyed by device name,
 SM count, algorithm (or "mixed") and a length class (floor(log2(mean
@@ -69,6 +70,21 @@ def _time_ms(torch, fn, reps: int) -> float:
     return best
 
 
+def _final_round(torch, timings: dict, make, reps: int, finalists: int = 3):
+    """The best of the first pass's `finalists` fastest candidates, timed
+    again in turns (so that a drift of the clock hits all of them alike),
+    by the median of several launches: one lucky launch in the first pass
+    does not decide."""
+    cands = sorted(timings, key=timings.get)[:finalists]
+    if len(cands) == 1:
+        return cands[0]
+    samples = {k: [] for k in cands}
+    for _ in range(max(5, 2 * reps)):
+        for k in cands:
+            samples[k].append(_time_ms(torch, make(k), 1))
+    return min(cands, key=lambda k: sorted(samples[k])[len(samples[k]) // 2])
+
+
 def tune(alg, packed, offsets, lengths, out, algs=None, mean_len: float | None = None,
          reps: int = 3, use_cache: bool = True, path: str | None = None) -> dict:
     """Pick and install the fastest shape for `alg` (None = the mixed path,
@@ -125,14 +141,18 @@ def tune(alg, packed, offsets, lengths, out, algs=None, mean_len: float | None =
                     continue
                 api.tune_mixed_warps(wps)
                 timings[(idx, wps)] = _time_ms(torch, run(idx), reps)
-        (best, best_wps) = min(timings, key=timings.get)
+        def with_warps(k):
+            api.tune_mixed_warps(k[1])
+            return run(k[0])
+
+        (best, best_wps) = _final_round(torch, timings, with_warps, reps)
         api.tune_mixed_warps(best_wps)
         result["warps_per_sm"] = best_wps
         ms = {"%d,%d" % k: v for k, v in timings.items()}
     else:
         for idx in range(len(shapes)):
             timings[idx] = _time_ms(torch, run(idx), reps)
-        best = min(timings, key=timings.get)
+        best = _final_round(torch, timings, run, reps)
         ms = {str(k): v for k, v in timings.items()}
     api.tune_set(tune_alg, best)
     result.update({"shape": best, "warps": shapes[best][0], "stages": shapes[best][1],
