@@ -354,7 +354,7 @@ def test_host_path_packed_digests(hb, oracle_mod, layout):
                            algs=np.zeros(b.n, np.uint8), packed_digests=True)
 
 
-def test_host_path_rejects_out_of_bounds(hb):
+def test_host_path_rejects_out_of_bounds(hb, oracle_mod):
     b = workloads.fixed(100, 40, seed=2)
     offs = b.offsets.copy()
     offs[50] = b.packed.size - 10          # runs 30 bytes past the end
@@ -364,6 +364,21 @@ def test_host_path_rejects_out_of_bounds(hb):
     assert e.value.code == -8
     # the library stays usable
     hb.hash_batch_host(0, b.packed, b.offsets, b.lengths, out)
+    # a batch copied in several chunks whose last message runs past the end:
+    # the call fails before hashing anything and the library stays usable
+    big = workloads.fixed(4000, 10000, seed=3)       # 40 MB, five chunks
+    offs = big.offsets.copy()
+    offs[-1] = big.packed.size - 100
+    out = np.zeros((big.n, 20), dtype=np.uint8)
+    for packed_digests in (False, True):
+        o = out if packed_digests else np.zeros((big.n, 32), np.uint8)
+        with pytest.raises(hb.HashBatchError) as e:
+            hb.hash_batch_host(1, big.packed, offs, big.lengths, o, packed_digests=packed_digests)
+        assert e.value.code == -8
+    hb.hash_batch_host(1, big.packed, big.offsets, big.lengths, out, packed_digests=True)
+    ref = workloads.Batch(big.packed, big.offsets, big.lengths, None)
+    sel = np.arange(0, big.n, 97)
+    _assert_slots_equal(out[sel], _oracle_slots(oracle_mod, ref, 1, sel)[:, :20], "after bounds")
 
 
 def test_check_bounds(hb):
