@@ -342,7 +342,7 @@ __device__ __forceinline__ void process_block_all(AllState& st, uint32_t slot, u
   sha1_compress(st.sha1, y, mc);
   md5_sm3_compress<kMd5FusedFma>(st.md5, st.sm3, w, y, mc);
 #else
-  md5_compress<kMd5FusedFma>(st.md5, w, mc);
+  md5_compress<kMd5FusedFma, kMd5FusedXt>(st.md5, w, mc);
 #pragma unroll
   for (int i = 0; i < 16; ++i) w[i] = bswap32(w[i]);
   if (final_block) {
