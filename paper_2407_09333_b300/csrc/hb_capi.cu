@@ -612,7 +612,7 @@ static int host_call(int alg, const uint8_t* algs_host, const uint8_t* packed_ho
   // Make sure no earlier call on another stream still uses the buffers.
   if (cudaDeviceSynchronize() != cudaSuccess) return cuda_fail(cudaGetLastError());
   const size_t pbytes = ((size_t)packed_len + 15) / 16 * 16 + 16;
-  const uint64_t footprint = pbytes + n * (kWinMsgBytes + 4);
+  const uint64_t footprint = pbytes + n * (kWinMsgBytes + 4 + (pack ? orec : 0));
   if (g_host_limit && footprint > g_host_limit) {
     bool layout_failed = false;
     return host_windowed(c, alg, algs_host, packed_host, packed_len, offsets_host, lengths_host,
