@@ -42,6 +42,12 @@ constexpr bool kSm3Fma = true;
 #define HB_MD5_FUSED_XT 1
 #endif
 constexpr bool kMd5FusedXt = HB_MD5_FUSED_XT != 0;
+// SM3's SS1 sum as two IMADs in the fused kernel (sm3_round_t's S0F): +1.5%
+// there; the SM3-only kernel measured 7-8% slower with it and keeps the IADD3.
+#ifndef HB_SM3_FUSED_S0_FMA
+#define HB_SM3_FUSED_S0_FMA 1
+#endif
+constexpr bool kSm3FusedS0Fma = HB_SM3_FUSED_S0_FMA != 0;
 #ifndef HB_FUSED_INTERLEAVE
 #define HB_FUSED_INTERLEAVE 0
 #endif
@@ -271,7 +277,9 @@ __device__ __forceinline__ uint32_t sm3_p1(uint32_t x, const MulConsts& mc) {
 // so that W'_J = W_J ^ W_{J+4} is available.  Split per round: rotations,
 // the Boolean functions, P0 and SS1's sum on the ALU; the six adds of TT1 and
 // TT2 on the FMA pipe; the expansion (three LOP3, four rotations) on the ALU.
-template <int J>
+// S0F: SS1's sum A<<<12 + E + T_j as two IMADs on the FMA pipe instead of
+// one IADD3 (the fused kernel's choice).
+template <int J, bool S0F = false>
 __device__ __forceinline__ void sm3_round_t(uint32_t (&v)[8], uint32_t (&W)[16], const MulConsts& mc,
                                             uint32_t tj) {
   {
@@ -294,7 +302,7 @@ __device__ __forceinline__ void sm3_round_t(uint32_t (&v)[8], uint32_t (&W)[16],
     const uint32_t wpj = wj ^ W[M & 15];
     const uint32_t a12 = rotl_f<12, (kSm3Rot & 4u) != 0>(A, mc);
     uint32_t s0;
-    if constexpr ((kSm3Rot & 256u) != 0)
+    if constexpr (S0F || (kSm3Rot & 256u) != 0)
       s0 = add_f<true>(a12, add_f<true>(E, tj, mc), mc);
     else
       s0 = a12 + E + tj;
@@ -321,16 +329,16 @@ __device__ __forceinline__ void sm3_round_t(uint32_t (&v)[8], uint32_t (&W)[16],
   }
 }
 
-template <int J>
+template <int J, bool S0F = false>
 __device__ __forceinline__ void sm3_round(uint32_t (&v)[8], uint32_t (&W)[16], const MulConsts& mc) {
-  sm3_round_t<J>(v, W, mc, sm3_tj_rot<J>());
+  sm3_round_t<J, S0F>(v, W, mc, sm3_tj_rot<J>());
 }
 
-template <int J, int END = 64>
+template <int J, int END = 64, bool S0F = false>
 __device__ __forceinline__ void sm3_rounds(uint32_t (&v)[8], uint32_t (&W)[16], const MulConsts& mc) {
   if constexpr (J < END) {
-    sm3_round<J>(v, W, mc);
-    sm3_rounds<J + 1, END>(v, W, mc);
+    sm3_round<J, S0F>(v, W, mc);
+    sm3_rounds<J + 1, END, S0F>(v, W, mc);
   }
 }
 
@@ -361,16 +369,16 @@ __host__ __device__ constexpr Sm3TTable make_sm3_t_table() {
 static __constant__ Sm3TTable kSm3TRot = make_sm3_t_table();
 
 // Rounds 16 + 16 * pass + R .. 16 + 16 * pass + 15.
-template <int R>
+template <int R, bool S0F = false>
 __device__ __forceinline__ void sm3_pass(uint32_t (&v)[8], uint32_t (&W)[16], const MulConsts& mc,
                                          int pass) {
   if constexpr (R < 16) {
-    sm3_round_t<16 + R>(v, W, mc, kSm3TRot.t[16 * pass + R]);
-    sm3_pass<R + 1>(v, W, mc, pass);
+    sm3_round_t<16 + R, S0F>(v, W, mc, kSm3TRot.t[16 * pass + R]);
+    sm3_pass<R + 1, S0F>(v, W, mc, pass);
   }
 }
 
-template <bool ROLLED = (HB_SM3_ROLLED == 2)>
+template <bool ROLLED = (HB_SM3_ROLLED == 2), bool S0F = false>
 __device__ __forceinline__ void sm3_compress(uint32_t (&st)[8], const uint32_t (&X)[16],
                                              const MulConsts& mc) {
   uint32_t W[16];
@@ -380,11 +388,11 @@ __device__ __forceinline__ void sm3_compress(uint32_t (&st)[8], const uint32_t (
 #pragma unroll
   for (int i = 0; i < 8; ++i) v[i] = st[i];
   if constexpr (ROLLED) {
-    sm3_rounds<0, 16>(v, W, mc);
+    sm3_rounds<0, 16, S0F>(v, W, mc);
 #pragma unroll 1
-    for (int pass = 0; pass < 3; ++pass) sm3_pass<0>(v, W, mc, pass);
+    for (int pass = 0; pass < 3; ++pass) sm3_pass<0, S0F>(v, W, mc, pass);
   } else {
-    sm3_rounds<0>(v, W, mc);
+    sm3_rounds<0, 64, S0F>(v, W, mc);
   }
 #pragma unroll
   for (int i = 0; i < 8; ++i) st[i] ^= v[i];

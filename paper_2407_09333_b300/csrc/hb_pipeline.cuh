@@ -350,7 +350,7 @@ __device__ __forceinline__ void process_block_all(AllState& st, uint32_t slot, u
     w[15] = lo;
   }
   sha1_compress(st.sha1, w, mc);
-  sm3_compress<HB_SM3_ROLLED != 0>(st.sm3, w, mc);
+  sm3_compress<HB_SM3_ROLLED != 0, kSm3FusedS0Fma>(st.sm3, w, mc);
 #endif
   if (final_block) {
     uint8_t* dst = records + msg * HB_ALL_RECORD_BYTES;
