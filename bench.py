@@ -189,6 +189,8 @@ class Dist:
         if self.world > 1:
             import torch
             import torch.distributed as dist
+            if torch.cuda.is_available():
+                torch.cuda.set_device(self.local_rank)  # one GPU per rank from the start
             backend = "nccl" if torch.cuda.is_available() else "gloo"
             os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
             dist.init_process_group(backend=backend)
