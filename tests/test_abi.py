@@ -138,3 +138,20 @@ def test_digits_argument_checks(lib):
     assert lib.hash_digits(0, 10 ** 9 - 1, 2, p, None) == -3
     assert lib.hash_digits(0, 0, 1, None, None) == -2
     assert lib.hash_digits(0, 0, 1, ctypes.c_void_p(p.value + 4), None) == -7
+
+
+def test_host_digest_layouts():
+    import numpy as np
+    assert [api.host_digest_bytes(a) for a in (0, 1, 2, api.ALL)] == [32, 32, 32, 96]
+    assert [api.host_digest_bytes(a, True) for a in (0, 1, 2, api.ALL)] == [16, 20, 32, 68]
+    packed = np.zeros(64, np.uint8)
+    off = np.zeros(2, np.uint64)
+    ln = np.zeros(2, np.uint32)
+    # these are refused before any library call
+    with pytest.raises(ValueError):
+        api.hash_batch_host(api.SHA1, packed, off, ln, np.zeros((2, 16), np.uint8), packed_digests=True)
+    with pytest.raises(ValueError):
+        api.hash_batch_host(None, packed, off, ln, np.zeros((2, 32), np.uint8),
+                            algs=np.zeros(2, np.uint8), packed_digests=True)
+    with pytest.raises(ValueError):
+        api.hash_batch_host(api.ALL, packed, off, ln, np.zeros((2, 68), np.uint8))
