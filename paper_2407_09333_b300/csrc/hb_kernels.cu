@@ -159,48 +159,109 @@ __global__ void __launch_bounds__(WARPS * 32) hb_mixed_kernel(KernelArgs a) {
 // thread hashes the ten strings 10q .. 10q+9, which share their first eight
 // characters, so the digits of q are worked out once per ten messages.
 
+// Message words of the strings 10q .. 10q+9 except word 2 (the last digit,
+// then the 0x80 marker), in the algorithm's word order.
+template <bool BE>
+__device__ __forceinline__ void digit_words(uint64_t q, uint32_t (&w)[16]) {
+  uint32_t c[8];  // characters of q, most significant first
+  uint32_t v = (uint32_t)q;
+#pragma unroll
+  for (int k = 7; k >= 0; --k) {
+    c[k] = '0' + v % 10u;
+    v /= 10u;
+  }
+#pragma unroll
+  for (int k = 0; k < 16; ++k) w[k] = 0u;
+  if (BE) {
+    w[0] = (c[0] << 24) | (c[1] << 16) | (c[2] << 8) | c[3];
+    w[1] = (c[4] << 24) | (c[5] << 16) | (c[6] << 8) | c[7];
+    w[15] = 72u;
+  } else {
+    w[0] = c[0] | (c[1] << 8) | (c[2] << 16) | (c[3] << 24);
+    w[1] = c[4] | (c[5] << 8) | (c[6] << 16) | (c[7] << 24);
+    w[14] = 72u;
+  }
+}
+
+template <bool BE>
+__device__ __forceinline__ uint32_t digit_word2(uint32_t d) {
+  const uint32_t ch = '0' + d;
+  return BE ? ((ch << 24) | (0x80u << 16)) : (ch | (0x80u << 8));
+}
+
+constexpr int kDigitsThreads = 256;
+
 template <int ALG>
-__global__ void __launch_bounds__(256) hb_digits_kernel(uint64_t first, uint64_t count,
-                                                        uint8_t* digests, MulConsts mc) {
+__global__ void __launch_bounds__(kDigitsThreads) hb_digits_kernel(uint64_t first, uint64_t count,
+                                                                   uint8_t* digests, MulConsts mc) {
   constexpr bool BE = AlgTraits<ALG>::kBigEndian;
   const uint64_t end = first + count;
   const uint64_t q_end = (end + 9) / 10;
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t q = first / 10 + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < q_end;
-       q += stride) {
-    uint32_t c[8];  // characters of q, most significant first
-    uint32_t v = (uint32_t)q;
-#pragma unroll
-    for (int k = 7; k >= 0; --k) {
-      c[k] = '0' + v % 10u;
-      v /= 10u;
-    }
-    uint32_t w[16];
-#pragma unroll
-    for (int k = 0; k < 16; ++k) w[k] = 0u;
-    if (BE) {
-      w[0] = (c[0] << 24) | (c[1] << 16) | (c[2] << 8) | c[3];
-      w[1] = (c[4] << 24) | (c[5] << 16) | (c[6] << 8) | c[7];
-      w[15] = 72u;
-    } else {
-      w[0] = c[0] | (c[1] << 8) | (c[2] << 16) | (c[3] << 24);
-      w[1] = c[4] | (c[5] << 8) | (c[6] << 16) | (c[7] << 24);
-      w[14] = 72u;
-    }
+  if constexpr (ALG == HB_MD5) {
+    // MD5 is quick enough that lane-strided 16-byte stores (each lane's ten
+    // slots are 320 bytes apart from the next lane's) bound it.  A warp takes
+    // 32 consecutive runs -- 320 consecutive messages -- keeps their digests
+    // in shared memory, and writes the 10 KB of slots in order: each store
+    // instruction covers 512 consecutive bytes.
+    __shared__ uint4 staged[kDigitsThreads / 32][320];
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t wib = threadIdx.x >> 5;
+    uint4* mine = staged[wib];
+    const uint64_t warps = (uint64_t)gridDim.x * (kDigitsThreads / 32);
+    for (uint64_t qw = first / 10 + ((uint64_t)blockIdx.x * (kDigitsThreads / 32) + wib) * 32;
+         qw < q_end; qw += warps * 32) {  // warp-uniform
+      const uint64_t q = qw + lane;
+      if (q < q_end) {
+        uint32_t w[16];
+        digit_words<BE>(q, w);
 #pragma unroll 1
-    for (uint32_t d = 0; d < 10; ++d) {
-      const uint64_t i = q * 10 + d;
-      if (i < first || i >= end) continue;
-      const uint32_t ch = '0' + d;
-      w[2] = BE ? ((ch << 24) | (0x80u << 16)) : (ch | (0x80u << 8));
-      uint32_t st[8];
-      alg_init<ALG>(st);
-      alg_compress<ALG>(st, w, mc);
-      uint32_t o[8];
-      alg_digest_words<ALG>(st, o);
-      uint8_t* dst = digests + (i - first) * HB_SLOT_BYTES;
-      stg128_cs(dst, o[0], o[1], o[2], o[3]);
-      stg128_cs(dst + 16, o[4], o[5], o[6], o[7]);
+        for (uint32_t d = 0; d < 10; ++d) {
+          uint32_t x[16];
+#pragma unroll
+          for (int k = 0; k < 16; ++k) x[k] = w[k];
+          x[2] = digit_word2<BE>(d);
+          // keep the words that vary opaque, so that their sums with MD5's
+          // constants are not hoisted out of this loop into extra registers
+          asm volatile("" : "+r"(x[0]), "+r"(x[1]));
+          uint32_t st[8];
+          alg_init<ALG>(st);
+          alg_compress<ALG>(st, x, mc);
+          mine[lane * 10 + d] = make_uint4(st[0], st[1], st[2], st[3]);
+        }
+      }
+      __syncwarp();
+      // 16-byte piece c of the warp's 320 slots: the digest (even c) or the
+      // zero fill (odd c) of message 10 qw + c / 2
+#pragma unroll 1
+      for (uint32_t c = lane; c < 640; c += 32) {
+        const uint64_t m = qw * 10 + c / 2;
+        if (m >= first && m < end) {
+          const uint4 v = (c & 1u) ? make_uint4(0u, 0u, 0u, 0u) : mine[c / 2];
+          stg128_cs(digests + (m - first) * HB_SLOT_BYTES + 16 * (c & 1u), v.x, v.y, v.z, v.w);
+        }
+      }
+      __syncwarp();
+    }
+  } else {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t q = first / 10 + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < q_end;
+         q += stride) {
+      uint32_t w[16];
+      digit_words<BE>(q, w);
+#pragma unroll 1
+      for (uint32_t d = 0; d < 10; ++d) {
+        const uint64_t i = q * 10 + d;
+        if (i < first || i >= end) continue;
+        w[2] = digit_word2<BE>(d);
+        uint32_t st[8];
+        alg_init<ALG>(st);
+        alg_compress<ALG>(st, w, mc);
+        uint32_t o[8];
+        alg_digest_words<ALG>(st, o);
+        uint8_t* dst = digests + (i - first) * HB_SLOT_BYTES;
+        stg128_cs(dst, o[0], o[1], o[2], o[3]);
+        stg128_cs(dst + 16, o[4], o[5], o[6], o[7]);
+      }
     }
   }
 }
@@ -209,9 +270,9 @@ cudaError_t launch_digits(int alg, uint64_t first, uint64_t count, uint8_t* dige
                           cudaStream_t stream) {
   const MulConsts mc = make_mul_consts();
   switch (alg) {
-    case HB_MD5: hb_digits_kernel<HB_MD5><<<grid, 256, 0, stream>>>(first, count, digests, mc); break;
-    case HB_SHA1: hb_digits_kernel<HB_SHA1><<<grid, 256, 0, stream>>>(first, count, digests, mc); break;
-    case HB_SM3: hb_digits_kernel<HB_SM3><<<grid, 256, 0, stream>>>(first, count, digests, mc); break;
+    case HB_MD5: hb_digits_kernel<HB_MD5><<<grid, kDigitsThreads, 0, stream>>>(first, count, digests, mc); break;
+    case HB_SHA1: hb_digits_kernel<HB_SHA1><<<grid, kDigitsThreads, 0, stream>>>(first, count, digests, mc); break;
+    case HB_SM3: hb_digits_kernel<HB_SM3><<<grid, kDigitsThreads, 0, stream>>>(first, count, digests, mc); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
