@@ -1,13 +1,15 @@
-// hb_kernels.cu -- every kernel of the library and its host-side launcher.
+// hb_kernels.cu -- the library's kernels other than the hashing kernels,
+// and the host-side launchers of all of them.
 //
-//   hb_plain_kernel    one algorithm (or all three, HB_ALL), one message per
-//                      thread, static grid-stride over 32-message tasks
-//                      (hash_batch, hash_batch_all)
+//   hb_plain_kernel    (hb_hash_kernels.cuh) one algorithm (or all three,
+//                      HB_ALL), one message per thread, static grid-stride
+//                      over 32-message tasks (hash_batch, hash_batch_all)
 //   hb_hist_kernel     ragged path, step 1: histogram of (cost bucket, alg)
 //   hb_scan_kernel     ragged path, step 2: group starts, padding, counters
 //   hb_scatter_kernel  ragged path, step 3: message ids into their group
-//   hb_mixed_kernel    ragged path, step 4: persistent, chunks popped from a
-//                      counter longest-first (hash_batch_mixed)
+//   hb_mixed_kernel    (hb_hash_kernels.cuh) ragged path, step 4:
+//                      persistent, chunks popped from a counter
+//                      longest-first (hash_batch_mixed)
 //   hb_digits_kernel   the paper's nine-digit workload generated in registers
 //   hb_bounds_kernel   offsets/lengths against the packed buffer size
 //   hb_monotone_kernel, hb_rebase_kernel, hb_pack_kernel   host-path helpers
@@ -23,25 +25,10 @@
 #include <cstdint>
 
 #include "hb_launch.h"
+#include "hb_hash_kernels.cuh"
 #include "hb_pipeline.cuh"
 
 namespace hb {
-
-// ---------------------------------------------------------------------------
-// Fixed-algorithm kernel.
-
-template <int ALG, int WARPS, int STAGES, int KB, bool COOP>
-__global__ void __launch_bounds__(WARPS * 32) hb_plain_kernel(KernelArgs a) {
-  extern __shared__ __align__(128) uint8_t smem[];
-  const uint32_t lane = threadIdx.x & 31u;
-  const uint32_t warp = threadIdx.x >> 5;
-  if (a.abort_flag && *a.abort_flag) return;
-  uint8_t* wsm = smem + warp * WarpSmem<STAGES, KB>::kBytes;
-  const uint64_t gwarp = (uint64_t)blockIdx.x * WARPS + warp;
-  const uint64_t nwarps = (uint64_t)gridDim.x * WARPS;
-  StaticSource<ALG> src(a, gwarp, nwarps, lane);
-  warp_pipeline<STAGES, KB, COOP, ALG, false, false>(src, wsm, a, lane);
-}
 
 // ---------------------------------------------------------------------------
 // Ragged path: bucketing by estimated cost, then the persistent kernel.
@@ -137,18 +124,6 @@ __global__ void hb_scatter_kernel(MixedArgs m) {
     base = __shfl_sync(kFull, base, leader);
     if (key != 0xFFFFFFFFu) m.perm[base + rank] = (uint32_t)i;
   }
-}
-
-// SEG: messages arrive as segments (a.seg), see hb_pipeline.cuh.
-template <int WARPS, int STAGES, int KB, bool COOP, bool SEG>
-__global__ void __launch_bounds__(WARPS * 32) hb_mixed_kernel(KernelArgs a) {
-  extern __shared__ __align__(128) uint8_t smem[];
-  const uint32_t lane = threadIdx.x & 31u;
-  const uint32_t warp = threadIdx.x >> 5;
-  if (a.abort_flag && *a.abort_flag) return;
-  uint8_t* wsm = smem + warp * WarpSmem<STAGES, KB, SEG>::kBytes;
-  DynamicSource<SEG> src(a, lane);
-  warp_pipeline<STAGES, KB, COOP, HB_MD5, true, SEG>(src, wsm, a, lane);
 }
 
 // ---------------------------------------------------------------------------
@@ -415,65 +390,17 @@ __global__ void hb_selftest_wait_kernel(uint64_t limit_ns, int* status) {
 // ---------------------------------------------------------------------------
 // Launch shapes and host launchers.
 
-// Launch shapes: (warps per block, stages in flight per warp, blocks per
-// stage, cooperative copies).  The table is the single list every kernel is
-// instantiated for.
-#define HB_SHAPES(X)     \
-  X(0, 4, 4, 1, false)   \
-  X(1, 4, 2, 1, false)   \
-  X(2, 8, 3, 1, false)   \
-  X(3, 1, 4, 1, false)   \
-  X(4, 2, 3, 1, false)   \
-  X(5, 16, 2, 1, false)  \
-  X(6, 8, 2, 4, false)   \
-  X(7, 4, 3, 4, false)   \
-  X(8, 8, 2, 2, false)   \
-  X(9, 4, 2, 4, false)   \
-  X(10, 4, 3, 4, true)   \
-  X(11, 8, 2, 4, true)   \
-  X(12, 16, 2, 1, true)  \
-  X(13, 4, 4, 1, true)   \
-  X(14, 8, 2, 2, true)   \
-  X(15, 8, 3, 2, true)   \
-  X(16, 4, 3, 2, true)   \
-  X(17, 4, 4, 2, true)   \
-  X(18, 1, 3, 4, true)   \
-  X(19, 1, 2, 4, true)   \
-  X(20, 1, 4, 2, true)   \
-  X(21, 1, 2, 2, true)   \
-  X(22, 1, 3, 2, true)   \
-  X(23, 2, 2, 2, true)
-
-struct ShapeDesc {
-  int warps, stages, kb;
-  bool coop;
-};
-#define HB_SHAPE_DESC(i, w, st, kb, co) {w, st, kb, co},
 static const ShapeDesc kShapes[] = {HB_SHAPES(HB_SHAPE_DESC)};
 static constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 
-using KernelFn = void (*)(KernelArgs);
-
-template <int ALG>
-static KernelFn plain_fn(int shape) {
-#define HB_PLAIN_CASE(i, w, st, kb, co) \
-  case i: return hb_plain_kernel<ALG, w, st, kb, co>;
-  switch (shape) {
-    HB_SHAPES(HB_PLAIN_CASE)
-    default: return nullptr;
-  }
-#undef HB_PLAIN_CASE
-}
-
-static KernelFn mixed_fn(int shape, bool seg) {
-#define HB_MIXED_CASE(i, w, st, kb, co) \
-  case i: return seg ? hb_mixed_kernel<w, st, kb, co, true> : hb_mixed_kernel<w, st, kb, co, false>;
-  switch (shape) {
-    HB_SHAPES(HB_MIXED_CASE)
-    default: return nullptr;
-  }
-#undef HB_MIXED_CASE
-}
+// The kernels' instantiation tables are compiled in their own translation
+// units (hb_inst_*.cu), in parallel.
+extern template KernelFn plain_fn<HB_MD5>(int);
+extern template KernelFn plain_fn<HB_SHA1>(int);
+extern template KernelFn plain_fn<HB_SM3>(int);
+extern template KernelFn plain_fn<HB_ALL>(int);
+extern template KernelFn mixed_fn<false>(int);
+extern template KernelFn mixed_fn<true>(int);
 
 static int shape_smem(int shape, bool seg) {
 #define HB_SMEM_CASE(i, w, st, kb, co) \
@@ -499,7 +426,7 @@ bool shape_desc(int shape, int* warps, int* stages, int* kb, int* coop) {
 int shape_smem_bytes(int shape, bool seg) { return shape_smem(shape, seg); }
 
 static KernelFn pick(bool mixed, int alg, int shape, bool seg) {
-  if (mixed) return mixed_fn(shape, seg);
+  if (mixed) return seg ? mixed_fn<true>(shape) : mixed_fn<false>(shape);
   switch (alg) {
     case HB_MD5: return plain_fn<HB_MD5>(shape);
     case HB_SHA1: return plain_fn<HB_SHA1>(shape);
