@@ -187,6 +187,10 @@ int hash_batch_segments(const uint8_t *algs, const uint8_t *packed_bytes,
  *   - All calls on a device share the array.  Each call clears what must
  *     start at zero, but calls whose work overlaps on the GPU race on it:
  *     order them (one stream, or events).
+ *   - Device-detected errors go to a status word inside the array;
+ *     hash_device_status() ORs it into the bits it returns and clears it
+ *     (that read is a plain copy and allocates nothing once the library's
+ *     context exists).  The kernels honour hash_set_wait_limit_ns().
  * Arguments, layout and results are those of hash_batch_mixed; the digests
  * are identical.  Returns HB_OK, HB_ERR_TOO_LARGE, HB_ERR_NULL, HB_ERR_ALIGN
  * or HB_ERR_CUDA.
@@ -277,8 +281,11 @@ int hash_plan_destroy(hb_plan *plan);
  *   1. claim: every entry of the window [head, tail) (counters taken modulo
  *      capacity) in state HB_RING_READY, oldest first, becomes HB_RING_BUSY
  *      while its next segment fits the round's limits (max_msgs segments,
- *      staging_bytes of staging, each segment starting 16-byte aligned).
- *      A segment is the next min(len - prior, segment_bytes[alg]) bytes;
+ *      staging_bytes of staging; a staged segment takes its own 16-byte
+ *      aligned span and sits in it at its source's offset within a 16-byte
+ *      granule, so sources may have any alignment and still copy as 16-byte
+ *      vectors).  A segment is the next min(len - prior, segment_bytes[alg])
+ *      bytes;
  *   2. copy: the segments' bytes go from src + prior to the staging area
  *      (with staging NULL, none: step 3 reads them where they are, and
  *      staging_bytes only caps the bytes one round claims);
@@ -419,7 +426,8 @@ int hash_batch_host_packed(int alg, const uint8_t *packed_host, uint64_t packed_
 /*
  * hash_device_status -- synchronises `stream`, then returns the OR of the
  * HB_DEV_* bits recorded on the current device since the last call, and
- * clears them.  *status_out receives the bits.
+ * clears them.  *status_out receives the bits.  The bits include those of
+ * hash_batch_mixed_noalloc, whose status word lives in its fixed scratch.
  */
 int hash_device_status(void *stream, int *status_out);
 

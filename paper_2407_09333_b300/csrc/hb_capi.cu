@@ -358,6 +358,11 @@ int* current_status_word() {
   Ctx* c = nullptr;
   return get_ctx(&c) == HB_OK ? c->status : nullptr;
 }
+
+uint64_t wait_limit_ns() {
+  std::lock_guard<std::mutex> lock(g_mu);
+  return g_wait_limit_ns;
+}
 }  // namespace hb
 
 extern "C" {
@@ -750,11 +755,14 @@ int hash_device_status(void* stream, int* status_out) {
   int rc = get_ctx(&c);
   if (rc) return rc;
   if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return cuda_fail(cudaGetLastError());
-  int v = 0;
+  int v = 0, na = 0;
   if (cudaMemcpy(&v, c->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
       cudaMemset(c->status, 0, sizeof(int)) != cudaSuccess)
     return cuda_fail(cudaGetLastError());
-  *status_out = v;
+  // bits of the no-allocation entry point, whose word is in its own scratch
+  cudaError_t e = hb::noalloc_take_status(&na);
+  if (e != cudaSuccess) return cuda_fail(e);
+  *status_out = v | na;
   return HB_OK;
 }
 

@@ -148,4 +148,13 @@ cudaError_t launch_set_count(uint64_t* n_dev, uint64_t n, cudaStream_t stream);
 // when that fails.
 int* current_status_word();
 
+// Device-side wait limit of the hashing kernels (hash_set_wait_limit_ns).
+uint64_t wait_limit_ns();
+
+// HB_DEV_* bits recorded by hash_batch_mixed_noalloc's kernels on the current
+// device since the last call (its status word lives in its fixed scratch
+// array, not in the device context), cleared as they are read.  Synchronous;
+// allocates nothing.  0 when that entry point has not run on this device.
+cudaError_t noalloc_take_status(int* bits);
+
 }  // namespace hb

@@ -18,6 +18,13 @@
 // start of each call, and every permutation entry is rewritten before it is
 // read.  Calls whose work overlaps on the GPU (for example on two streams
 // without ordering between them) use the same array and race: order them.
+//
+// Device-detected errors.  The kernels record HB_DEV_* bits in a status word
+// at the start of the array (the library's per-device status word lives in a
+// context that is allocated on first use, so this path cannot use it).
+// hash_device_status() reads that word with a plain device-to-host copy, ORs
+// it into what it returns and clears it, so a caller sees these bits where it
+// sees every other entry point's.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -80,6 +87,24 @@ int setup_current_device(DeviceSetup** out) {
 
 }  // namespace
 
+namespace hb {
+cudaError_t noalloc_take_status(int* bits) {
+  *bits = 0;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_setup_mu);
+  const DeviceSetup& s = g_setup[dev];
+  if (!s.ready) return cudaSuccess;  // never ran here: nothing recorded
+  int v = 0;
+  e = cudaMemcpy(&v, s.scratch, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && v != 0) e = cudaMemset(s.scratch, 0, sizeof(int));
+  if (e == cudaSuccess) *bits = v;
+  return e;
+}
+}  // namespace hb
+
 extern "C" int hash_batch_mixed_noalloc(const uint8_t* algs, const uint8_t* packed_bytes,
                                         const uint64_t* offsets, const uint32_t* lengths,
                                         uint64_t n, uint8_t* digests_out, void* stream) {
@@ -124,7 +149,7 @@ extern "C" int hash_batch_mixed_noalloc(const uint8_t* algs, const uint8_t* pack
   a.digests = digests_out;
   a.status = status;
   a.abort_flag = nullptr;
-  a.wait_limit_ns = 2000000000ull;
+  a.wait_limit_ns = hb::wait_limit_ns();
   a.mc = hb::make_mul_consts();
   if (hb::launch_hash(true, 0, kShape, s->sms * s->blocks_per_sm, a, st) != cudaSuccess)
     return HB_ERR_CUDA;
