@@ -4,10 +4,14 @@
 Default workload (the configuration the headline metric is quoted on): a
 plain fixed-length batch of 2^22 messages x 55 bytes (one 64-byte block
 after padding), uniform random bytes, packed back to back with uint64
-offsets and uint32 lengths, 32-byte digest slots.  One step hashes the batch
-with each of MD5, SHA-1 and SM3 (three launches).  Inputs (220 MiB + 48 MiB
-of metadata) are larger than the 126 MB L2, so no flush is needed between
-steps.
+offsets and uint32 lengths.  One step hashes every message with each of MD5,
+SHA-1 and SM3: by default one launch of the fused kernel (hash_batch_all,
+96-byte records), with --separate one launch per algorithm (32-byte slots).
+`value` counts input bytes once per algorithm (3 x 230.7 MB per step: the
+bytes each algorithm hashed), so it is "byte-hashes per second over the
+three algorithms"; the per-algorithm rates of the single-algorithm kernels
+are reported beside it.  Inputs (220 MiB + 48 MiB of metadata) are larger
+than the 126 MB L2, so no flush is needed between steps.
 
     python bench.py [--gpus N] [--steps K] [--warmup W]
                     [--workload c2|c4|c3|c1] [--impl ours|reference]
@@ -41,13 +45,12 @@ from paper_2407_09333_b300 import workloads  # noqa: E402
 METRIC = "hashed GB/s and Mhash/s per alg (plain vs ragged batch); serve p50/p99 latency"
 ALG_NAMES = ("md5", "sha1", "sm3", None, "all")   # index 4: the fused kernel
 
-# Algorithmic 32-bit operations per 64-byte block (3-input ALU ops: LOP3 for
-# each Boolean function or 3-way XOR, IADD3 for up to three addends, SHF for
-# each rotation, PRMT for each byte swap), counted from the definitions:
-#   MD5   64 steps x (1 g + 2 add + 1 rot + 1 add) + 4 chaining adds  = 324
-#   SHA-1 80 rounds x 5 + 64 schedule words x 3 + 5 adds + 16 swaps  = 613
-#   SM3   64 rounds x 16 + 52 expanded words x 7 + 8 xors + 16 swaps = 1412
-OPS_PER_BLOCK = {0: 324, 1: 613, 2: 1412}
+from paper_2407_09333_b300 import shard  # noqa: E402
+
+# Algorithmic 32-bit operations per 64-byte block, one table for the roofline
+# and the multi-GPU split (shard.OPS_PER_BLOCK: 324 / 613 / 1412 for MD5 /
+# SHA-1 / SM3, counted from the definitions).
+OPS_PER_BLOCK = {a: int(shard.OPS_PER_BLOCK[a]) for a in range(3)}
 
 
 def padded_blocks(lengths: np.ndarray) -> np.ndarray:
