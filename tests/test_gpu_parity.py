@@ -178,6 +178,48 @@ def test_on_device_nine_digit_strings(hb, oracle_mod, first, count):
         _assert_slots_equal(got, _oracle_slots(oracle_mod, b, alg), "digits %d+%d" % (first, count))
 
 
+def _digit_strings(values):
+    # the 9-character decimal strings of `values`, laid out back to back
+    vals = np.asarray(values, dtype=np.int64) % 1_000_000_000
+    digits = np.empty((vals.shape[0], 9), dtype=np.uint8)
+    for k in range(8, -1, -1):
+        digits[:, k] = (vals % 10).astype(np.uint8) + ord("0")
+        vals = vals // 10
+    n = digits.shape[0]
+    return workloads.Batch(digits.reshape(-1).copy(), np.arange(n, dtype=np.uint64) * np.uint64(9),
+                           np.full(n, 9, dtype=np.uint32), None)
+
+
+def test_on_device_nine_digit_strings_several_passes(hb, oracle_mod):
+    # more runs of ten strings than the grid holds at once (sms x 8 blocks x
+    # 256 threads), starting off a multiple of ten: every thread and warp
+    # makes a second pass over the grid stride, and MD5's warps reuse their
+    # shared-memory staging.  Compared on every warp's first and last slot of
+    # every pass, the batch ends and a seeded sample.
+    first, count = 7, 4_000_003
+    end = first + count
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    runs = (end + 9) // 10 - first // 10
+    grid = max(1, min((runs + 255) // 256, sms * 8))
+    assert runs > grid * 256, "the case must need more than one pass"
+    warps = grid * 8
+    qw = first // 10 + np.arange(0, runs, 32, dtype=np.int64)      # each warp-pass's first run
+    heads = np.maximum(qw * 10, first)
+    tails = np.minimum(qw * 10 + 319, end - 1)
+    rng = np.random.default_rng(71)
+    msgs = np.unique(np.concatenate([heads, tails, np.arange(first, first + 300),
+                                     np.arange(end - 300, end), rng.integers(first, end, 20000)]))
+    assert (qw.shape[0] + warps - 1) // warps >= 2
+    sample = _digit_strings(msgs)
+    k = torch.from_numpy(msgs - first).cuda()
+    for alg in ALGS:
+        out = hb.hash_digits(alg, first, count)
+        got = out[k].cpu().numpy()
+        _assert_slots_equal(got, _oracle_slots(oracle_mod, sample, alg), "digits passes alg %d" % alg)
+        del out
+    assert hb.device_status() == 0
+
+
 def test_on_device_nine_digit_limits(hb):
     with pytest.raises(hb.HashBatchError) as e:
         hb.hash_digits(0, hb.DIGITS_COUNT - 5, 6)
@@ -448,17 +490,57 @@ def test_full_size_fused_sampled(hb, oracle_mod, tmp_path, n, length, seed, k):
     assert hb.device_status() == 0
 
 
-def test_full_size_ragged_2pow20_sampled(hb, oracle_mod):
+@pytest.fixture(scope="module")
+def c3(hb, oracle_mod):
+    # the ragged benchmark batch: 2^20 messages, log-uniform lengths in
+    # [0, 64 KiB], 1% at padding boundaries, algorithm per message (seed 2)
     b = workloads.ragged(1 << 20, seed=2)
-    packed, off, ln, algs = hb.to_device(b)
-    out = hb.hash_batch_mixed(algs, packed, off, ln)
+    dev = hb.to_device(b)
+    # the oracle's digests of a fixed sample: the first and last 256, 6000
+    # seeded indices and every forced boundary-length message
     idx = _sample(b.n, 6000, 2)
-    # all forced boundary-length messages too
     bl = np.nonzero(np.isin(b.lengths, workloads.BOUNDARY_LENGTHS))[0]
     idx = np.unique(np.concatenate([idx, bl]))
+    want = _oracle_slots(oracle_mod, b, None, idx)
+    yield b, dev, idx, want
+    del dev
+    torch.cuda.empty_cache()
+
+
+def test_full_size_ragged_2pow20_sampled(hb, c3):
+    b, (packed, off, ln, algs), idx, want = c3
+    out = hb.hash_batch_mixed(algs, packed, off, ln)
     got = out[torch.from_numpy(idx).cuda()].cpu().numpy()
-    _assert_slots_equal(got, _oracle_slots(oracle_mod, b, None, idx), "C3")
+    _assert_slots_equal(got, want, "C3")
     assert hb.device_status() == 0
+
+
+def test_full_size_ragged_graph_replay_matches_oracle(hb, c3, tmp_path):
+    # exactly the benchmark's ragged step: the autotuned shape, bucketing and
+    # warps per SM, the launch sequence captured once as a graph, replayed with
+    # the message count read on the device -- compared with the oracle, for
+    # the whole batch and for prefixes (slots past the prefix stay untouched)
+    from paper_2407_09333_b300 import autotune
+    b, (packed, off, ln, algs), idx, want = c3
+    out = torch.zeros((b.n, 32), dtype=torch.uint8, device="cuda")
+    autotune.tune(None, packed, off, ln, out, algs=algs, path=str(tmp_path / "tune.json"))
+    plan = hb.Plan(b.n)
+    plan.capture(algs, packed, off, ln, out)
+    try:
+        for m in (b.n, 700_001, 65_536, 33, 1, b.n):
+            out.zero_()
+            plan.replay(m)
+            torch.cuda.synchronize()
+            sel = idx < m
+            got = out[torch.from_numpy(idx[sel]).cuda()].cpu().numpy()
+            _assert_slots_equal(got, want[sel], "C3 replay n=%d" % m)
+            assert not bool(out[m:].any().item()), "slots past n=%d were written" % m
+        assert hb.device_status() == 0
+    finally:
+        plan.close()
+        hb.tune_set(hb.TUNE_MIXED, 10)
+        hb.tune_buckets(3, 1)
+        hb.tune_mixed_warps(8)
 
 
 def test_autotuner_installs_a_valid_shape(hb, oracle_mod, tmp_path):
