@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(kClaimThreads) hb_round_claim_kernel(RoundArgs
     bool claimed = false;
     if (j < window && ld_cg_u32(r.state + k) == HB_RING_READY)
       claimed = atomicCAS(r.state + k, HB_RING_READY, HB_RING_BUSY) == HB_RING_READY;
-    uint64_t prior = 0, seg = 0;
+    uint64_t prior = 0, seg = 0, from = 0;
     bool more = false;
     if (claimed) {
       prior = ld_cg_u64(r.prior + k);
@@ -107,10 +107,15 @@ __global__ void __launch_bounds__(kClaimThreads) hb_round_claim_kernel(RoundArgs
       const uint64_t rem = (uint64_t)ld_cg_u32(r.len + k) - prior;
       more = rem > S;
       seg = more ? S : rem;
+      from = ld_cg_u64(r.src + k) + prior;  // the segment's first byte
     }
     const uint32_t mask = __ballot_sync(0xFFFFFFFFu, claimed);
     if (mask == 0) continue;
-    const uint64_t b16 = claimed ? (seg + 15) & ~15ull : 0;
+    // A staged segment keeps its source's position within a 16-byte granule
+    // (it starts `lead` bytes into its 16-byte aligned staging span), so the
+    // copy moves aligned 16-byte vectors whatever the client's alignment.
+    const uint64_t lead = r.staging ? (from & 15u) : 0u;
+    const uint64_t b16 = claimed ? (lead + seg + 15) & ~15ull : 0;
     uint64_t incl = b16;  // inclusive scan of staged bytes
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
@@ -130,15 +135,15 @@ __global__ void __launch_bounds__(kClaimThreads) hb_round_claim_kernel(RoundArgs
     }
     if (claimed) {
       const uint64_t i = old_cnt + __popc(mask & ((1u << lane) - 1u));
-      const uint64_t off = old_bytes + incl - b16;
+      const uint64_t off = old_bytes + incl - b16 + lead;
       r.b_algs[i] = (uint8_t)__ldcg(r.alg + k);
       // staged: offset into the staging area; in place: the source itself
-      r.b_offsets[i] = r.staging ? off : ld_cg_u64(r.src + k) + prior - r.in_place_base;
+      r.b_offsets[i] = r.staging ? off : from - r.in_place_base;
       r.b_lengths[i] = (uint32_t)seg;
       r.b_seg[i] = prior | (more ? HB_SEG_MORE : 0ull);
       r.b_slot[i] = (uint32_t)k;
       HbCopy c;
-      c.src = ld_cg_u64(r.src + k) + prior;
+      c.src = from;
       c.dst = reinterpret_cast<uint64_t>(r.staging) + off;
       c.bytes = seg;
       r.b_copies[i] = c;
@@ -150,8 +155,11 @@ __global__ void __launch_bounds__(kClaimThreads) hb_round_claim_kernel(RoundArgs
   }
 }
 
-// One warp per segment: 16-byte vectors when source and destination are
-// 16-byte aligned, 4-byte words when both are 4-byte aligned, else bytes.
+// One warp per segment.  Source and destination have the same position
+// within a 16-byte granule (the claim places staged segments so): the bytes
+// up to the first granule boundary go one per lane, the rest as 16-byte
+// vectors, the tail one byte per lane.  Other pairs fall back to 4-byte
+// words when both are 4-byte aligned, else bytes.
 __global__ void hb_round_copy_kernel(const HbCopy* copies, const RoundCtl* ctl) {
   const uint32_t lane = threadIdx.x & 31u;
   const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -162,10 +170,13 @@ __global__ void hb_round_copy_kernel(const HbCopy* copies, const RoundCtl* ctl) 
     const uint8_t* src = reinterpret_cast<const uint8_t*>(c.src);
     uint8_t* dst = reinterpret_cast<uint8_t*>(c.dst);
     uint64_t done = 0;
-    if (((c.src | c.dst) & 15u) == 0) {
-      const uint64_t nv = c.bytes >> 4;
-      const uint4* s4 = reinterpret_cast<const uint4*>(src);
-      uint4* d4 = reinterpret_cast<uint4*>(dst);
+    if (((c.src ^ c.dst) & 15u) == 0) {
+      const uint64_t head = (16u - (c.src & 15u)) & 15u;
+      done = head < c.bytes ? head : c.bytes;
+      if (lane < done) dst[lane] = __ldg(src + lane);
+      const uint64_t nv = (c.bytes - done) >> 4;
+      const uint4* s4 = reinterpret_cast<const uint4*>(src + done);
+      uint4* d4 = reinterpret_cast<uint4*>(dst + done);
       uint64_t v = lane;
       for (; v + 96 < nv; v += 128) {
         const uint4 a = __ldg(s4 + v), b = __ldg(s4 + v + 32), x = __ldg(s4 + v + 64),
@@ -176,7 +187,7 @@ __global__ void hb_round_copy_kernel(const HbCopy* copies, const RoundCtl* ctl) 
         d4[v + 96] = y;
       }
       for (; v < nv; v += 32) d4[v] = __ldg(s4 + v);
-      done = nv << 4;
+      done += nv << 4;
     } else if (((c.src | c.dst) & 3u) == 0) {
       const uint64_t nw = c.bytes >> 2;
       const uint32_t* s1 = reinterpret_cast<const uint32_t*>(src);
@@ -358,7 +369,7 @@ int hash_round_create(const hb_ring* ring, uint32_t max_msgs, uint8_t* staging,
   k.n = max_msgs;
   k.digests = ring->slots;
   k.status = status;
-  k.wait_limit_ns = 2000000000ull;
+  k.wait_limit_ns = wait_limit_ns();
   k.mc = make_mul_consts();
   k.seg = a.b_seg;
   k.slot_index = a.b_slot;

@@ -32,6 +32,12 @@ ring and the request table have room (`RingBook`), one batch of metadata
 copies per loop for the newly admitted requests, round launches, and the
 done flags.  Digests stay on the device; `keep_digests` copies each request's
 digests out when it completes (for tests).
+
+Admission by predicted time (`Admission`, optional): the fitted cost model
+(costmodel: Eq. 2's linear form plus the serial-chain bound) gives each
+request a predicted completion time when it is admitted; the server can hold
+requests on the host while the predicted in-flight work exceeds a cap, and
+shed a request at arrival when its predicted latency exceeds a target.
 """
 from __future__ import annotations
 
@@ -115,11 +121,118 @@ class Req:
     admitted: float = -1.0
     done: float = -1.0
     digests: np.ndarray | None = None
+    rejected: bool = False       # shed at arrival by the admission policy
+    work_s: float = 0.0          # predicted GPU-seconds (Admission)
+    chain_s: float = 0.0         # predicted longest serial chain (Admission)
+    predicted_done: float = -1.0 # predicted completion time, set at admission
 
     def __post_init__(self):
         self.lengths = np.asarray(self.lengths, dtype=np.uint32)
         self.src = np.asarray(self.src, dtype=np.uint64)
         self.nbytes = int(self.lengths.astype(np.uint64).sum())
+
+
+class Admission:
+    """Admission of requests by predicted completion time.
+
+    The GPU is modelled as one work-conserving server: an admitted request
+    adds its predicted GPU-seconds (`model.work_seconds`: the fitted
+    throughput and per-message terms) to a backlog that drains at one
+    GPU-second per second while requests are in flight.  A request admitted
+    at time t is predicted to finish at
+
+        t + max(backlog(t) + work, chain) + t0
+
+    -- after the work admitted before it and its own, and not before its
+    longest message's serial chain (`model.chain_time`); t0 is the fixed
+    cost of a request (admission copies, the rounds' cadence).
+
+    Policies (both optional):
+      cap_s  hold: while the backlog exceeds cap_s GPU-seconds and something
+             is in flight, waiting requests stay on the host (in arrival
+             order), so the device holds only the work that keeps it busy
+             and the predicted order of completion is the admission order;
+      slo_s  shed: at arrival, a request whose predicted completion --
+             counted from its arrival, after the backlog and the work of the
+             requests still waiting ahead of it -- would exceed slo_s is
+             rejected at once instead of queued.
+
+    Time is whatever clock the caller passes (seconds), so the policy runs
+    under a fake clock in tests.
+    """
+
+    def __init__(self, model, cap_s: float | None = None, slo_s: float | None = None,
+                 t0: float = 0.0):
+        self.model = model
+        self.cap_s = cap_s
+        self.slo_s = slo_s
+        self.t0 = t0
+        self._backlog = 0.0
+        self._t = 0.0
+        self.inflight = 0
+        self.waiting_s = 0.0       # predicted work of requests waiting to be admitted
+
+    def estimate(self, req):
+        """(work seconds, chain seconds) of a request, also stored on it."""
+        req.work_s = self.model.work_seconds(req.lengths, req.alg)
+        req.chain_s = self.model.chain_time(req.lengths, req.alg)
+        return req.work_s, req.chain_s
+
+    def backlog(self, now: float) -> float:
+        """Predicted GPU-seconds of admitted work not yet done at `now`."""
+        if now > self._t:
+            if self.inflight:
+                self._backlog = max(0.0, self._backlog - (now - self._t))
+            self._t = now
+        return self._backlog
+
+    def predicted_latency(self, req, now: float) -> float:
+        """Latency from arrival if the request joined the queue at `now`."""
+        ahead = self.backlog(now) + self.waiting_s
+        return (now - req.arrival) + max(ahead + req.work_s, req.chain_s) + self.t0
+
+    def arrive(self, req, now: float) -> bool:
+        """False when the request is shed; otherwise it waits for admission."""
+        self.estimate(req)
+        if self.slo_s is not None and self.predicted_latency(req, now) > self.slo_s:
+            req.rejected = True
+            return False
+        self.waiting_s += req.work_s
+        return True
+
+    def hold(self, now: float) -> bool:
+        """Whether waiting requests should stay on the host for now."""
+        return (self.cap_s is not None and self.inflight > 0
+                and self.backlog(now) > self.cap_s)
+
+    def admit(self, req, now: float):
+        b = self.backlog(now)
+        req.predicted_done = now + max(b + req.work_s, req.chain_s) + self.t0
+        self._backlog = b + req.work_s
+        self.waiting_s = max(0.0, self.waiting_s - req.work_s)
+        self.inflight += 1
+
+    def finish(self, req, now: float):
+        self.backlog(now)
+        self.inflight -= 1
+        if self.inflight == 0:
+            self._backlog = 0.0    # nothing in flight: the device is idle
+
+
+def prediction_stats(requests: list) -> dict:
+    """Predicted against measured completion of the served requests: the
+    median ratio of measured to predicted latency (from arrival) and the
+    share of requests within 25% of their prediction."""
+    done = [r for r in requests if r.done >= 0 and r.predicted_done >= 0]
+    if not done:
+        return {"requests": 0}
+    pred = np.array([r.predicted_done - r.arrival for r in done])
+    meas = np.array([r.done - r.arrival for r in done])
+    ratio = meas / np.maximum(pred, 1e-9)
+    return {"requests": len(done), "median_measured_over_predicted": float(np.median(ratio)),
+            "p10_ratio": float(np.percentile(ratio, 10)), "p90_ratio": float(np.percentile(ratio, 90)),
+            "within_25pct": float(np.mean(np.abs(ratio - 1.0) <= 0.25)),
+            "p99_predicted_ms": float(np.percentile(pred, 99) * 1e3)}
 
 
 def device_bytes(capacity: int, req_capacity: int, rounds: int, max_msgs: int) -> int:
@@ -247,20 +360,24 @@ class Server:
             self.admit_event.record(self.admit_stream)
 
     # -- the loop ----------------------------------------------------------
-    def run(self, requests: list, keep_digests: bool = False, time_limit_s: float = 600.0):
+    def run(self, requests: list, keep_digests: bool = False, time_limit_s: float = 600.0,
+            admission: Admission | None = None):
         """Serve `requests` (sorted by arrival) in real time; returns them,
-        finished (done >= 0) or rejected (done < 0)."""
+        finished (done >= 0) or rejected (done < 0).  With `admission`, each
+        admitted request gets a predicted completion time and the policy may
+        hold requests on the host or shed them at arrival."""
         # the loop allocates no reference cycles; a collector pause would
         # stall round launches, so the cyclic collector waits until the end
         gc_was_on = gc.isenabled()
         gc.disable()
         try:
-            return self._run(requests, keep_digests, time_limit_s)
+            return self._run(requests, keep_digests, time_limit_s, admission)
         finally:
             if gc_was_on:
                 gc.enable()
 
-    def _run(self, requests: list, keep_digests: bool, time_limit_s: float):
+    def _run(self, requests: list, keep_digests: bool, time_limit_s: float,
+             adm: Admission | None = None):
         torch, book = self.torch, self.book
         torch.cuda.synchronize()
         nreq = len(requests)
@@ -275,8 +392,12 @@ class Server:
             if now > time_limit_s:
                 raise RuntimeError("serving run exceeded %.0f s" % time_limit_s)
             while i < nreq and requests[i].arrival <= now:
-                pending.append(requests[i])
+                r = requests[i]
                 i += 1
+                if adm is not None and r.lengths.shape[0] and not adm.arrive(r, now):
+                    rejected += 1               # shed: predicted too late
+                    continue
+                pending.append(r)
             # admission, first come first served
             new = []
             while pending:
@@ -285,6 +406,8 @@ class Server:
                 if m > book.capacity:
                     pending.popleft()
                     rejected += 1
+                    if adm is not None:
+                        adm.waiting_s = max(0.0, adm.waiting_s - r.work_s)
                     continue
                 if m == 0:                      # nothing to hash: done on arrival
                     pending.popleft()
@@ -292,11 +415,15 @@ class Server:
                     r.digests = np.zeros((0, 32), np.uint8) if keep_digests else None
                     finished += 1
                     continue
+                if adm is not None and adm.hold(now):
+                    break
                 if not book.fits(m):
                     break
                 pending.popleft()
                 r.counter, r.first = book.admit(m)
                 r.admitted = now
+                if adm is not None:
+                    adm.admit(r, now)
                 inflight[r.counter % book.req_capacity] = r
                 new.append(r)
             self.loop_iters += 1
@@ -343,6 +470,8 @@ class Server:
                         r = inflight.pop(q)
                         r.done = t
                         self.fin_np[q] = True
+                        if adm is not None:
+                            adm.finish(r, t)
                         if keep_digests:
                             r.digests = self._digests(r)
                         book.finish(r.counter)
@@ -369,17 +498,21 @@ class Server:
 # synthetic load
 
 def make_requests(count: int, rate_per_s: float, seed: int, pool_bytes: int,
-                  max_msgs: int = 4096, min_len: int = 16, max_len: int = 1 << 20) -> list:
+                  max_msgs: int = 4096, min_len: int = 16, max_len: int = 1 << 20,
+                  align: int = 16) -> list:
     """Poisson request stream; each message's bytes are a range of the
-    random-byte pool starting at a 16-byte aligned offset chosen from the
-    request's seed."""
+    random-byte pool starting at an offset that is a multiple of `align`
+    (1 = any byte), chosen from the request's seed."""
     from . import workloads
+    if align < 1:
+        raise ValueError("align must be >= 1")
     out = []
     for k, r in enumerate(workloads.serve_requests(count, rate_per_s, seed, max_msgs, min_len, max_len)):
         rng = np.random.Generator(np.random.PCG64(r.seed))
         lens = r.lengths.astype(np.uint64)
-        hi = (np.uint64(pool_bytes) - lens) // np.uint64(16)
-        src = (rng.random(lens.shape[0]) * (hi.astype(np.float64) + 1)).astype(np.uint64) * np.uint64(16)
+        hi = (np.uint64(pool_bytes) - lens) // np.uint64(align)
+        src = (rng.random(lens.shape[0]) * (hi.astype(np.float64) + 1)).astype(np.uint64) * np.uint64(align)
+        src = np.minimum(src, np.uint64(pool_bytes) - lens)
         out.append(Req(k, r.arrival_s, r.alg, r.lengths, src))
     return out
 

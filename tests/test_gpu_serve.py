@@ -192,6 +192,63 @@ def test_small_ring_makes_admission_wait_and_reuses_entries(env, oracle_mod):
     _check_requests(api, oracle_mod, reqs, pool_host, oracle_every=2)
 
 
+@pytest.fixture(scope="module")
+def big_pool(env):
+    # room for 1 MiB messages at any byte offset
+    pool_bytes = 256 << 20
+    pool_host = workloads.fixed(1, pool_bytes, seed=78).packed
+    pool_dev = torch.from_numpy(np.ascontiguousarray(pool_host)).cuda()
+    yield pool_host, pool_dev, pool_bytes
+    del pool_dev
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("in_place", [True, False])
+def test_served_at_config5_shape_unaligned_equals_oracle(env, big_pool, oracle_mod, in_place):
+    # The serving workload's own request shape: 1-4096 messages per request
+    # (log-uniform count), lengths log-uniform in [16 B, 1 MiB], one random
+    # algorithm per request, every message at a random byte offset of the
+    # clients' pool; served by the benchmark's server (8 GiB budget, two
+    # rounds, default segments), arrivals overlapping.  Every digest of every
+    # request is compared with the ragged path run once over all messages,
+    # and a sample of each request (first, last, longest and five seeded
+    # messages) with the oracle.
+    api, serve = env[0], env[1]
+    pool_host, pool_dev, pool_bytes = big_pool
+    reqs = serve.make_requests(200, 2000.0, seed=91 + int(in_place), pool_bytes=pool_bytes,
+                               align=1)
+    assert max(r.lengths.shape[0] for r in reqs) > 1000
+    assert max(int(r.lengths.max()) for r in reqs) > (1 << 19)
+    assert sum(int((r.src % 16 != 0).sum()) for r in reqs) > 0
+    srv = serve.Server(pool_dev, in_place=in_place)
+    srv.run(reqs, keep_digests=True)
+    srv.close()
+    assert srv.segments > sum(r.lengths.shape[0] for r in reqs)   # long messages were cut
+    assert all(r.done >= 0 for r in reqs)
+    got = np.concatenate([r.digests for r in reqs])
+    src = np.concatenate([r.src for r in reqs])
+    lens = np.concatenate([r.lengths for r in reqs])
+    algs = np.concatenate([np.full(r.lengths.shape[0], r.alg, np.uint8) for r in reqs])
+    alone = api.hash_batch_mixed(torch.from_numpy(algs).cuda(), pool_dev,
+                                 torch.from_numpy(src.view(np.int64)).cuda(),
+                                 torch.from_numpy(lens.view(np.int32)).cuda()).cpu().numpy()
+    bad = np.nonzero((got != alone).any(axis=1))[0]
+    assert bad.size == 0, "%d of %d served digests differ from the ragged path" % (bad.size, len(got))
+    rng = np.random.default_rng(92)
+    pick, base = [], 0
+    for r in reqs:
+        m = r.lengths.shape[0]
+        pick += [base, base + m - 1, base + int(np.argmax(r.lengths))]
+        pick += (base + rng.integers(0, m, size=5)).tolist()
+        base += m
+    pick = np.unique(np.array(pick, dtype=np.int64))
+    want = oracle_mod.hash_batch(None, pool_host, src[pick], lens[pick], algs=algs[pick],
+                                 threads=oracle_mod.host_threads())
+    bad = np.nonzero((got[pick] != want).any(axis=1))[0]
+    assert bad.size == 0, "%d of %d sampled digests differ from the oracle" % (bad.size, len(pick))
+    assert api.device_status() == 0
+
+
 def test_completion_flags_must_be_mapped_host_memory(env):
     api = env[0]
     plan = api.Plan(64)

@@ -94,3 +94,134 @@ def test_requests_are_seeded_and_messages_lie_inside_the_pool():
         assert 1 <= x.lengths.shape[0] <= 64 and x.alg in (0, 1, 2)
     arr = [r.arrival for r in a]
     assert arr == sorted(arr) and arr[0] >= 0
+
+
+# ---------------------------------------------------------------------------
+# admission by predicted completion time, under a fake clock
+
+from paper_2407_09333_b300.serve import Admission, Req, prediction_stats  # noqa: E402
+
+
+class _Model:
+    """Cost model stand-in: work = bytes x per-byte rate of the algorithm,
+    chain = longest message x per-byte chain rate."""
+    RATE = (1e-12, 2e-12, 4e-12)        # s per byte, at full GPU throughput
+    CHAIN = (2e-11, 3e-11, 6e-11)       # s per byte of one serial chain
+
+    def work_seconds(self, lengths, alg):
+        return float(np.asarray(lengths, dtype=np.float64).sum() * self.RATE[alg])
+
+    def chain_time(self, lengths, alg):
+        return float(np.asarray(lengths, dtype=np.float64).max(initial=0) * self.CHAIN[alg])
+
+
+def _requests(n, rate_per_s, seed):
+    rng = np.random.default_rng(seed)
+    t, out = 0.0, []
+    for k in range(n):
+        t += rng.exponential(1.0 / rate_per_s)
+        m = int(rng.integers(1, 50))
+        lens = np.exp(rng.uniform(np.log(16), np.log(1 << 20), size=m)).astype(np.uint32)
+        out.append(Req(k, t, int(rng.integers(0, 3)), lens, np.zeros(m, np.uint64)))
+    return out
+
+
+def _serve(adm, reqs):
+    """Event-driven fake server: admitted work is done first come first
+    served at one GPU-second per second; a request completes when its work
+    is done, and not before its longest chain has run since admission.
+    Drives `adm` with the simulated clock; returns the requests."""
+    import heapq
+    pending, done_heap, order = [], [], []
+    work_free = 0.0                        # when the FIFO server finishes the admitted work
+    i = 0
+    t = 0.0
+    while i < len(reqs) or pending or done_heap:
+        t_arr = reqs[i].arrival if i < len(reqs) else float("inf")
+        t_done = done_heap[0][0] if done_heap else float("inf")
+        if t_done <= t_arr:
+            t, _, r = heapq.heappop(done_heap)
+            r.done = t
+            adm.finish(r, t)
+        else:
+            t, r = t_arr, reqs[i]
+            i += 1
+            if adm.arrive(r, t):
+                pending.append(r)
+        while pending and not adm.hold(t):
+            r = pending.pop(0)
+            r.admitted = t
+            adm.admit(r, t)
+            order.append(r.rid)
+            work_free = max(work_free, t) + r.work_s
+            heapq.heappush(done_heap, (max(work_free, t + r.chain_s) + adm.t0, r.rid, r))
+    return order
+
+
+def test_admission_predicts_completion_of_a_first_come_first_served_device():
+    reqs = _requests(400, 2000.0, seed=1)
+    adm = Admission(_Model(), t0=1e-4)
+    order = _serve(adm, reqs)
+    assert order == sorted(order)                       # admitted in arrival order
+    for r in reqs:
+        assert r.admitted == r.arrival                  # no cap: admitted on arrival
+        assert r.done == pytest.approx(r.predicted_done, abs=1e-12)
+    st = prediction_stats(reqs)
+    assert st["requests"] == 400 and st["median_measured_over_predicted"] == pytest.approx(1.0)
+    assert st["within_25pct"] == 1.0
+
+
+def test_admission_holds_requests_while_the_backlog_exceeds_the_cap():
+    reqs = _requests(600, 1e6, seed=2)                   # a burst: far above capacity
+    cap = 2e-4
+    seen = []
+
+    class Watch(Admission):
+        def admit(self, req, now):
+            seen.append((self.backlog(now), self.inflight))
+            super().admit(req, now)
+
+    adm = Watch(_Model(), cap_s=cap)
+    order = _serve(adm, reqs)
+    assert order == sorted(order)
+    assert all(b <= cap + 1e-12 or inflight == 0 for b, inflight in seen)
+    assert any(r.admitted > r.arrival for r in reqs)    # some had to wait
+    for r in reqs:                                      # predictions stay exact
+        assert r.done == pytest.approx(r.predicted_done, abs=1e-12)
+
+
+def test_admission_sheds_requests_predicted_past_the_target():
+    model = _Model()
+    probe = _requests(20000, 1.0, seed=3)
+    mean_work = float(np.mean([model.work_seconds(r.lengths, r.alg) for r in probe]))
+    load = 1.5                                          # offered load above capacity
+    slo = 500 * mean_work
+    plain = _requests(20000, load / mean_work, seed=3)
+    _serve(Admission(model), plain)
+    shed = _requests(20000, load / mean_work, seed=3)
+    _serve(Admission(model, slo_s=slo), shed)
+    lat_plain = np.array([r.done - r.arrival for r in plain])
+    served = [r for r in shed if not r.rejected]
+    lat_shed = np.array([r.done - r.arrival for r in served])
+    assert np.percentile(lat_plain, 99) > 5 * slo       # unbounded queue without shedding
+    assert lat_shed.max() <= slo + 1e-12                # every served request met the target
+    # large requests are the first to miss the target, so what is shed is
+    # about the excess work (1 - 1/load of it), in fewer requests
+    shed_work = sum(r.work_s for r in shed if r.rejected) / sum(r.work_s for r in shed)
+    assert 0.25 < shed_work < 0.45
+    assert 0 < sum(r.rejected for r in shed) < len(shed) * shed_work
+    assert all(r.done < 0 for r in shed if r.rejected)
+
+
+def test_admission_without_chain_calibration_uses_work_alone():
+    from paper_2407_09333_b300 import costmodel
+    m = costmodel.CostModel(np.array([1e-12, 2e-12, 3e-12]), 0.0, 1.0)
+    assert m.chain_time([100, 5000], 2) == 0.0
+    r = Req(0, 0.0, 2, [55, 56], [0, 0])
+    adm = Admission(m)
+    w, c = adm.estimate(r)
+    assert w == pytest.approx(3e-12 * (1 + 2) * 1412) and c == 0.0
+    m2 = costmodel.fit_chain(m, [(2, 16384, 257 * 1412 / 1e7), (2, 16384, 257 * 1412 / 2e7),
+                                 (2, 16384, 257 * 1412 / 3e7)])
+    assert m2.chain[2] == pytest.approx(2e7) and m2.chain[0] == 0
+    assert m2.chain_time([100, 16384], 2) == pytest.approx(257 * 1412 / 2e7)
