@@ -124,7 +124,7 @@ def tune(alg, packed, offsets, lengths, out, algs=None, mean_len: float | None =
         # then the launch shape with the chosen bucketing.
         api.tune_mixed_warps(8)
         btimes = {}
-        for sub in (1, 2, 3):
+        for sub in (2, 3, 4):
             for major in (0, 1):
                 api.tune_buckets(sub, major)
                 btimes[(sub, major)] = _time_ms(torch, run(api.tune_get(api.TUNE_MIXED)), reps)

@@ -844,7 +844,8 @@ int hash_tune_mixed_warps(int warps_per_sm) {
 }
 
 int hash_tune_buckets(int sub_log2, int alg_major) {
-  if (sub_log2 < 0 || sub_log2 > 3 || (alg_major != 0 && alg_major != 1)) return HB_ERR_ARG;
+  if (sub_log2 < 0 || sub_log2 > (int)hb::kMaxSubLog2 || (alg_major != 0 && alg_major != 1))
+    return HB_ERR_ARG;
   Ctx* c = nullptr;
   int rc = get_ctx(&c);
   if (rc) return rc;

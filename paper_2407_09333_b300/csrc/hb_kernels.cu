@@ -78,30 +78,51 @@ __global__ void hb_hist_kernel(MixedArgs m) {
     if (counts[g]) atomicAdd(&m.ws->counts[g], counts[g]);
 }
 
-// One block of kGroups threads.  Groups are laid out in group order, each
-// padded to a multiple of 32 so that every chunk holds a single algorithm
-// and starts with a real message.
-__global__ void hb_scan_kernel(MixedArgs m) {
-  __shared__ uint32_t padded[kGroups];
-  const uint32_t g = threadIdx.x;
-  const uint32_t cnt = m.ws->counts[g];
-  padded[g] = (cnt + 31u) & ~31u;
+// One block of kScanThreads threads, kScanPer consecutive groups each.
+// Groups are laid out in group order, each padded to a multiple of 32 so
+// that every chunk holds a single algorithm and starts with a real message:
+// an exclusive prefix sum of the padded counts (per thread, then across the
+// block's warps) gives each group's first permutation entry.
+constexpr uint32_t kScanThreads = 512;
+constexpr uint32_t kScanPer = kGroups / kScanThreads;
+static_assert(kGroups % kScanThreads == 0, "scan covers every group");
+
+__global__ void __launch_bounds__(kScanThreads) hb_scan_kernel(MixedArgs m) {
+  __shared__ uint32_t warp_sums[kScanThreads / 32];
+  const uint32_t t = threadIdx.x, lane = t & 31u, warp = t >> 5;
+  uint32_t cnt[kScanPer], pad[kScanPer], own = 0;
+#pragma unroll
+  for (uint32_t k = 0; k < kScanPer; ++k) {
+    cnt[k] = m.ws->counts[t * kScanPer + k];
+    pad[k] = (cnt[k] + 31u) & ~31u;
+    own += pad[k];
+  }
+  uint32_t incl = own;  // inclusive scan within the warp
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t v = __shfl_up_sync(kFull, incl, d);
+    if (lane >= (uint32_t)d) incl += v;
+  }
+  if (lane == 31) warp_sums[warp] = incl;
   __syncthreads();
-  if (g == 0) {
-    uint32_t run = 0;
-    for (uint32_t k = 0; k < kGroups; ++k) {
-      const uint32_t p = padded[k];
-      padded[k] = run;
-      run += p;
-    }
-    m.ws->nchunks = run / 32u;
+  uint32_t before = 0, total = 0;
+  for (uint32_t w = 0; w < kScanThreads / 32; ++w) {
+    const uint32_t v = warp_sums[w];
+    before += w < warp ? v : 0u;
+    total += v;
+  }
+  uint32_t start = before + incl - own;
+#pragma unroll
+  for (uint32_t k = 0; k < kScanPer; ++k) {
+    const uint32_t g = t * kScanPer + k;
+    m.ws->cursor[g] = start;
+    for (uint32_t e = start + cnt[k]; e < start + pad[k]; ++e) m.perm[e] = 0xFFFFFFFFu;
+    start += pad[k];
+  }
+  if (t == 0) {
+    m.ws->nchunks = total / 32u;
     m.ws->chunk_counter = 0u;
   }
-  __syncthreads();
-  const uint32_t start = padded[g];
-  m.ws->cursor[g] = start;
-  const uint32_t end = start + ((cnt + 31u) & ~31u);
-  for (uint32_t k = start + cnt; k < end; ++k) m.perm[k] = 0xFFFFFFFFu;
 }
 
 __global__ void hb_scatter_kernel(MixedArgs m) {
@@ -459,7 +480,7 @@ cudaError_t launch_bucketing(const MixedArgs& m, int grid, cudaStream_t stream) 
   cudaError_t e = cudaMemsetAsync(m.ws->counts, 0, sizeof(m.ws->counts), stream);
   if (e != cudaSuccess) return e;
   hb_hist_kernel<<<grid, 256, 0, stream>>>(m);
-  hb_scan_kernel<<<1, kGroups, 0, stream>>>(m);
+  hb_scan_kernel<<<1, kScanThreads, 0, stream>>>(m);
   hb_scatter_kernel<<<grid, 256, 0, stream>>>(m);
   return cudaGetLastError();
 }

@@ -57,15 +57,18 @@ struct KernelArgs {
 // Ragged-path bucketing: groups are (cost bucket, algorithm) pairs ordered
 // from the most to the least expensive estimated work per message.  Cost
 // buckets split each octave of estimated cost into 2^sub_log2 parts
-// (sub_log2 <= 3, so at most 32 * 8 buckets).  With alg_major the order is
+// (sub_log2 <= 4, so at most 32 * 16 buckets): the finer the buckets, the
+// closer the lengths of a chunk's 32 messages, and the fewer lanes idle
+// while the chunk's longest message finishes.  With alg_major the order is
 // all SM3 groups, then SHA-1, then MD5 (each longest first), so that warps
 // running at the same time mostly run the same algorithm; otherwise the
 // algorithms interleave bucket by bucket (strict longest-first).
-constexpr uint32_t kCostBuckets = 256;
+constexpr uint32_t kMaxSubLog2 = 4;
+constexpr uint32_t kCostBuckets = 32u << kMaxSubLog2;
 constexpr uint32_t kGroups = kCostBuckets * 3;
 
 struct BucketCfg {
-  uint32_t sub_log2;   // 0..3
+  uint32_t sub_log2;   // 0..kMaxSubLog2
   uint32_t alg_major;  // 0 or 1
 };
 

@@ -308,28 +308,30 @@ struct SegCtx {
   uint32_t slot;   // the message's 32-byte slot
 };
 
+// Where block b of a message stands (all 32-bit: b < nb <= 2^26 + 2):
+//   the 0x80 marker goes into block len / 64, at byte len % 64 (the block
+//   holding the message's end, or the first padding block when len is a
+//   multiple of 64); the bit length fills the last two words of block nb - 1.
+// A segment that is not its message's last (`more`) has neither: its last
+// block (nb - 1, nb = len / 64) ends by storing the chaining value instead.
+
 // One block of a message for all three algorithms (HB_ALL): the staged
 // words feed MD5 as loaded and SHA-1 / SM3 byte-swapped; the final block
 // writes the message's 96-byte record.
 __device__ __forceinline__ void process_block_all(AllState& st, uint32_t slot, uint32_t s,
-                                                  uint32_t len, uint32_t b, uint64_t msg,
-                                                  uint8_t* records, const MulConsts& mc) {
-  const int64_t rem = (int64_t)len - 64 * (int64_t)b;  // message bytes from this block on
-  if (rem >= 0 && rem < 64) sts8(slot + s + (uint32_t)rem, 0x80u);
+                                                  uint32_t len, uint32_t b, uint32_t nb,
+                                                  uint64_t msg, uint8_t* records,
+                                                  const MulConsts& mc) {
+  if (b == (len >> 6)) sts8(slot + s + (len & 63u), 0x80u);
   // One copy of the words is live at a time: MD5 takes them as loaded, then
   // they are byte-swapped in place for SHA-1 and SM3.
   uint32_t w[16];
   read_block_words<false>(slot, s, w);
-  const bool final_block = rem <= 55;
+  const bool final_block = b + 1 == nb;
   const uint32_t lo = len << 3, hi = len >> 29;  // bit length mod 2^64
   if (final_block) {
     w[14] = lo;
     w[15] = hi;
-  }
-  if (b == 0) {
-    md5_init(st.md5);
-    sha1_init(st.sha1);
-    sm3_init(st.sm3);
   }
 #if HB_FUSED_INTERLEAVE
   uint32_t y[16];
@@ -369,31 +371,22 @@ __device__ __forceinline__ void process_block_all(AllState& st, uint32_t slot, u
 
 template <int ALG, bool SEG = false>
 __device__ __forceinline__ void process_block(uint32_t (&st)[8], uint32_t slot, uint32_t s,
-                                              uint32_t len, uint32_t b, uint64_t msg,
+                                              uint32_t len, uint32_t b, uint32_t nb, uint64_t msg,
                                               uint8_t* digests, const MulConsts& mc,
                                               const KernelArgs& a, const SegCtx& sc = SegCtx{}) {
   constexpr bool BE = AlgTraits<ALG>::kBigEndian;
-  const int64_t rem = (int64_t)len - 64 * (int64_t)b;  // message bytes from this block on
   const bool more = SEG && sc.more;
-  if (!more && rem >= 0 && rem < 64) sts8(slot + s + (uint32_t)rem, 0x80u);
+  if (!more && b == (len >> 6)) sts8(slot + s + (len & 63u), 0x80u);
   uint32_t w[16];
   read_block_words<BE>(slot, s, w);
-  const bool final_block = !more && rem <= 55;
+  const bool last = b + 1 == nb;
+  const bool final_block = !more && last;
   if (final_block) {
     // bit length of the whole message mod 2^64
     const uint64_t bits = SEG ? (sc.prior + len) << 3 : (uint64_t)len << 3;
     const uint32_t lo = (uint32_t)bits, hi = (uint32_t)(bits >> 32);
     w[14] = BE ? hi : lo;
     w[15] = BE ? lo : hi;
-  }
-  if (b == 0) {
-    if (SEG && sc.prior != 0) {
-      const uint4 v0 = lds128(sc.state), v1 = lds128(sc.state + 16);
-      st[0] = v0.x; st[1] = v0.y; st[2] = v0.z; st[3] = v0.w;
-      st[4] = v1.x; st[5] = v1.y; st[6] = v1.z; st[7] = v1.w;
-    } else {
-      alg_init<ALG>(st);
-    }
   }
   alg_compress<ALG>(st, w, mc);
   if (final_block) {
@@ -403,7 +396,7 @@ __device__ __forceinline__ void process_block(uint32_t (&st)[8], uint32_t slot, 
     stg128_cs(dst, o[0], o[1], o[2], o[3]);
     stg128_cs(dst + 16, o[4], o[5], o[6], o[7]);
     note_message_done(a, msg);
-  } else if (more && rem == 64) {
+  } else if (more && last) {
     // last block of a segment that is not the message's last: keep the
     // chaining value (words past the algorithm's state are zero)
     constexpr int kW = AlgTraits<ALG>::kStateWords;
@@ -419,19 +412,34 @@ __device__ __forceinline__ void process_block(uint32_t (&st)[8], uint32_t slot, 
 // otherwise ALG is fixed.
 
 // Consumes the KB blocks of one stage for one lane (blocks past the
-// message's padded length are skipped).
+// message's padded length are skipped).  A message's chain starts in the
+// stage that holds its block 0: from the algorithm's initial value, or, for
+// a later segment, from the chaining value staged with it.
 template <int ALG, int KB, bool SEG = false>
 __device__ __forceinline__ void process_stage(typename StateFor<ALG>::type& st, uint32_t slot,
                                               uint32_t s, uint32_t len, uint32_t b0, uint64_t msg,
                                               const KernelArgs& a, const SegCtx& sc = SegCtx{}) {
   const uint32_t nb = (SEG && sc.more) ? (len >> 6) : padded_blocks(len);
+  if (b0 == 0) {
+    if constexpr (ALG == HB_ALL) {
+      md5_init(st.md5);
+      sha1_init(st.sha1);
+      sm3_init(st.sm3);
+    } else if (SEG && sc.prior != 0) {
+      const uint4 v0 = lds128(sc.state), v1 = lds128(sc.state + 16);
+      st[0] = v0.x; st[1] = v0.y; st[2] = v0.z; st[3] = v0.w;
+      st[4] = v1.x; st[5] = v1.y; st[6] = v1.z; st[7] = v1.w;
+    } else {
+      alg_init<ALG>(st);
+    }
+  }
+  const uint32_t nj = nb - b0 < (uint32_t)KB ? nb - b0 : (uint32_t)KB;
 #pragma unroll 1
-  for (int j = 0; j < KB; ++j) {
-    if (b0 + j >= nb) break;
+  for (uint32_t j = 0; j < nj; ++j) {
     if constexpr (ALG == HB_ALL)
-      process_block_all(st, slot + 64 * j, s, len, b0 + j, msg, a.digests, a.mc);
+      process_block_all(st, slot + 64 * j, s, len, b0 + j, nb, msg, a.digests, a.mc);
     else
-      process_block<ALG, SEG>(st, slot + 64 * j, s, len, b0 + j, msg, a.digests, a.mc, a, sc);
+      process_block<ALG, SEG>(st, slot + 64 * j, s, len, b0 + j, nb, msg, a.digests, a.mc, a, sc);
   }
 }
 
@@ -532,21 +540,36 @@ __device__ __forceinline__ void warp_pipeline(Source& src, uint8_t* wsm, const K
       const uint32_t mlo = lane / kMain;
       const uint32_t tab = table + mlo * 16;
       const uint32_t dst0 = slots + (is * 32 + mlo) * kSlotBytes + 16 * gi;
+      if (__all_sync(kFull, avail == kSlotBytes)) {
+        // every lane's whole slot lies inside its message (the usual case in
+        // long messages): full granules, no clamping
 #pragma unroll
-      for (int r = 0; r < kMain; ++r) {
-        const uint4 e = lds128(tab + 16 * kPerRound * r);
-        const int32_t v = (int32_t)e.z - 16 * (int32_t)gi;
-        const uint32_t nbytes = v <= 0 ? 0u : (v >= 16 ? 16u : (uint32_t)v);
-        const uint64_t from = nbytes ? (((uint64_t)e.y << 32) | e.x) + 16ull * gi : safe_src;
-        cp_async16_zfill(dst0 + kPerRound * kSlotBytes * r, reinterpret_cast<const void*>(from),
-                         nbytes);
-      }
-      if (act && (t.addr & 15u) != 0u) {
-        const int32_t v = avail - 16 * kMain;
-        const uint32_t nbytes = v <= 0 ? 0u : (v >= 16 ? 16u : (uint32_t)v);
-        const uint64_t from = nbytes ? g0 + 16ull * kMain : safe_src;
-        cp_async16_zfill(slots + (is * 32 + lane) * kSlotBytes + 16 * kMain,
-                         reinterpret_cast<const void*>(from), nbytes);
+        for (int r = 0; r < kMain; ++r) {
+          const uint4 e = lds128(tab + 16 * kPerRound * r);
+          const uint64_t from = (((uint64_t)e.y << 32) | e.x) + 16ull * gi;
+          cp_async16_zfill(dst0 + kPerRound * kSlotBytes * r, reinterpret_cast<const void*>(from),
+                           16u);
+        }
+        if ((t.addr & 15u) != 0u)
+          cp_async16_zfill(slots + (is * 32 + lane) * kSlotBytes + 16 * kMain,
+                           reinterpret_cast<const void*>(g0 + 16ull * kMain), 16u);
+      } else {
+#pragma unroll
+        for (int r = 0; r < kMain; ++r) {
+          const uint4 e = lds128(tab + 16 * kPerRound * r);
+          const int32_t v = (int32_t)e.z - 16 * (int32_t)gi;
+          const uint32_t nbytes = v <= 0 ? 0u : (v >= 16 ? 16u : (uint32_t)v);
+          const uint64_t from = nbytes ? (((uint64_t)e.y << 32) | e.x) + 16ull * gi : safe_src;
+          cp_async16_zfill(dst0 + kPerRound * kSlotBytes * r, reinterpret_cast<const void*>(from),
+                           nbytes);
+        }
+        if (act && (t.addr & 15u) != 0u) {
+          const int32_t v = avail - 16 * kMain;
+          const uint32_t nbytes = v <= 0 ? 0u : (v >= 16 ? 16u : (uint32_t)v);
+          const uint64_t from = nbytes ? g0 + 16ull * kMain : safe_src;
+          cp_async16_zfill(slots + (is * 32 + lane) * kSlotBytes + 16 * kMain,
+                           reinterpret_cast<const void*>(from), nbytes);
+        }
       }
     }
     ++inflight;
