@@ -147,7 +147,7 @@ class ClockSampler:
                 self._proc = subprocess.Popen(
                     ["nvidia-smi", "-i", str(self.device_index),
                      "--query-gpu=clocks.sm,clocks.max.sm,clocks_event_reasons.active",
-                     "--format=csv,noheader,nounits", "-lms", "100"],
+                     "--format=csv,noheader,nounits", "-lms", str(max(20, int(self.period * 1e3)))],
                     stdout=self._tmp, stderr=subprocess.DEVNULL)
             except OSError as e:
                 self.error = "%s; nvidia-smi: %s" % (self.error, e)
@@ -389,6 +389,51 @@ def kernel_source_hash() -> str:
 
 
 def run_ours(args, dist):
+    """The default run: the headline workload, then (one GPU, default
+    workload) short measurements of the long-message and ragged workloads as
+    extra keys, each with its own roofline, so that one run reports all three
+    measured configurations."""
+    import copy
+    import torch
+    line = measure(args, dist)
+    if args.workload == "c2" and dist.world == 1 and not args.no_extras and args.shape is None:
+        line["extra_workloads"] = {}
+        for name, steps in (("c4", 50), ("c3", 20)):
+            torch.cuda.empty_cache()
+            sub = copy.copy(args)
+            sub.workload, sub.steps, sub.warmup = name, steps, 3
+            sub.no_e2e = sub.no_cpu_baseline = True
+            sub.messages = 0
+            x = measure(sub, dist)
+            keep = ("value", "unit", "ms_per_step", "mhash_per_s", "per_alg", "roofline", "clocks",
+                    "config", "plain_equal_bytes_gbs", "ragged_vs_plain_equal_bytes", "cost_model",
+                    "tuned_shapes", "steps", "warmup", "gpu_launches")
+            line["extra_workloads"][name] = {k: x[k] for k in keep if k in x}
+    if dist.rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def clock_window(step, device_index, seconds=1.5):
+    """SM clock and throttle reasons while `step` runs back to back for at
+    least `seconds` (the counted steps can be too short for the sampler):
+    the same launches, outside the timed region."""
+    import torch
+    with ClockSampler(device_index, period_s=0.01) as clocks:
+        t0 = time.perf_counter()
+        n = 0
+        while time.perf_counter() - t0 < seconds:
+            for _ in range(8):
+                step()
+            n += 8
+            torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+    out = clocks.summary()
+    out.update({"window_s": dt, "window_steps": n,
+                "window": "the timed step repeated back to back right after the timed region"})
+    return out
+
+
+def measure(args, dist):
     import torch
     from paper_2407_09333_b300 import api, build
 
@@ -443,6 +488,10 @@ def run_ours(args, dist):
             tuned["mixed"]["algorithm_major"] = bool(r["buckets"][1])
         if "warps_per_sm" in r:
             tuned["mixed"]["warps_per_sm"] = r["warps_per_sm"] or "occupancy"
+        if a is None and "ms" in r:
+            # every (shape, warps per SM) the tuner timed, and the bucketings
+            tuned["mixed"]["timings_ms"] = r["ms"]
+            tuned["mixed"]["bucket_timings_ms"] = r.get("bucket_ms")
 
     if mixed:
         # the whole ragged sequence (bucketing + persistent kernel) captured
@@ -496,7 +545,19 @@ def run_ours(args, dist):
                      for j in range(nl)]
     value = job_bytes / (ms * 1e-3) / 1e9
     peaks = load_peaks()
-    clk = clocks.summary()
+    # clocks: the sampler also ran during the counted steps, which can be too
+    # short for it; a window of the same steps repeated for a second gives
+    # the clock record (time x clock lets runs at different clocks compare)
+    timed_clk = clocks.summary()
+
+    def one_step():
+        for _, fn in launches:
+            fn()
+    clk = clock_window(one_step, torch.cuda.current_device())
+    clk["during_timed_steps"] = {"samples": timed_clk["samples"], "sm_mhz": timed_clk["sm_mhz"],
+                                 "reasons": timed_clk["reasons"]}
+    if clk["sm_mhz"]:
+        clk["ms_per_step_x_sm_mhz"] = ms / args.steps * clk["sm_mhz"]
     sm_mhz = clk["sm_mhz"] or peaks["sm_max_mhz"]
 
     def launch_figures(a, t):
@@ -592,14 +653,12 @@ def run_ours(args, dist):
         line["plain_equal_bytes_gbs"] = pg
         line["plain_mean_length"] = pl
         line["ragged_vs_plain_equal_bytes"] = per_alg["mixed"]["GB/s"] / pg
-        line["cost_model"] = cost_model_report(api, torch, batch.lengths, batch.algs, packed,
-                                               per_alg["mixed"]["ms"])
+        line["cost_model"] = cost_model_report(api, torch, batch, packed, per_alg["mixed"]["ms"])
     if not args.no_e2e:
         line["e2e"] = e2e_measure(args, batch, mixed, api, torch, dist)
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(batch, mixed)
-    if dist.rank == 0:
-        print(json.dumps(line), flush=True)
+    return line
 
 
 def e2e_measure(args, batch, mixed, api, torch, dist):
@@ -695,45 +754,61 @@ def plain_equal_bytes_gbs(api, torch, lengths, algs, pool, reps=3, max_msgs=1 <<
     return b_total / t_total / 1e9, L
 
 
-def cost_model_report(api, torch, lengths, algs, pool, measured_ms, reps=3):
-    """Fits the linear launch-cost model on fixed-length launches (each
-    algorithm, three batch sizes, the set's mean length, messages read from
-    `pool`) and predicts the measured ragged launch from its lengths and
-    algorithms alone."""
-    from paper_2407_09333_b300 import costmodel
-    L = max(1, int(round(float(lengths.astype(np.float64).mean()))))
-    span = max(1, (pool.numel() - L) // 16)
-    def timed(fn):
-        fn()
-        torch.cuda.synchronize()
-        best = float("inf")
-        for _ in range(reps):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(); fn(); e1.record(); e1.synchronize()
-            best = min(best, e0.elapsed_time(e1))
-        return best * 1e-3
+def _timed_s(torch, fn, reps=3):
+    """Best of `reps` CUDA-event timings of fn() after one untimed call."""
+    fn()
+    torch.cuda.synchronize()
+    best = float("inf")
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(); fn(); e1.record(); e1.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return best * 1e-3
 
+
+def fit_launch_model(api, torch, pool, shape=-1, lengths=(1024, 16384), launch_bytes=1 << 30,
+                     reps=3):
+    """Eq. 2's linear form (per-algorithm rate per op, per-message term,
+    launch cost T0) for the persistent ragged kernel in launch shape `shape`,
+    fitted on launches that its throughput bounds: per algorithm, messages
+    of one fixed length (every chain equally long, so no chain outlasts the
+    rest) read from `pool` at 16-byte aligned offsets, at two lengths (which
+    separates the per-message term) and two batch sizes (which separates
+    T0) -- twelve launches."""
+    from paper_2407_09333_b300 import costmodel
     samples = []
-    sizes = (1 << 18, 3 << 18, 1 << 20)
+    span = max(1, (pool.numel() - max(lengths)) // 16)
     for a in (0, 1, 2):
-        batches = []
-        for n in sizes:
-            i = torch.arange(n, dtype=torch.int64, device=pool.device)
-            o = ((i * 2654435761) % span) * 16
-            l = torch.full((n,), L, dtype=torch.int32, device=pool.device)
-            batches.append((n, o, l, torch.empty((n, 32), dtype=torch.uint8, device=pool.device)))
-        # the algorithm's best launch shape on the largest batch, used for all sizes
-        n, o, l, out = batches[-1]
-        shape = min(range(len(api.shapes())),
-                    key=lambda sh: timed(lambda: api.hash_batch(a, pool, o, l, out=out, shape=sh)))
-        for n, o, l, out in batches:
-            t = timed(lambda: api.hash_batch(a, pool, o, l, out=out, shape=shape))
-            samples.append((costmodel.work_by_alg(np.full(n, L), alg=a), t))
-        del batches
-    m = costmodel.fit(samples)
-    pred = m.predict_batch(lengths, algs=algs) * 1e3
-    return {"form": "T = sum over algorithms of rate x (padded blocks x ops per block) + T0",
-            "rate_ps_per_op": [r * 1e12 for r in m.rate], "overhead_us": m.overhead * 1e6,
+        for L in lengths:
+            n_full = max(1024, launch_bytes // L)
+            for n in (n_full, n_full // 2):
+                i = torch.arange(n, dtype=torch.int64, device=pool.device)
+                o = ((i * 2654435761) % span) * 16
+                l = torch.full((n,), L, dtype=torch.int32, device=pool.device)
+                g = torch.full((n,), a, dtype=torch.uint8, device=pool.device)
+                out = torch.empty((n, 32), dtype=torch.uint8, device=pool.device)
+                t = _timed_s(torch, lambda: api.hash_batch_mixed(g, pool, o, l, out=out, shape=shape),
+                             reps)
+                samples.append((costmodel.work_by_alg(np.full(n, L), alg=a),
+                                costmodel.msgs_by_alg(n, alg=a), t))
+                del i, o, l, g, out
+    return costmodel.fit(samples)
+
+
+def cost_model_report(api, torch, batch, pool, measured_ms):
+    """The ragged kernel's cost model (fit_launch_model, in the launch shape
+    the batch was hashed with) predicting the measured ragged launch from its
+    lengths and algorithms alone.  The batch also has a tail the model does
+    not describe: its longest messages are serial chains that start first and
+    end last, on a GPU that the rest of the work has left by then."""
+    m = fit_launch_model(api, torch, pool)
+    pred = m.predict_batch(batch.lengths, algs=batch.algs) * 1e3
+    return {"form": "T = sum over algorithms of (rate x padded blocks x ops per block + per-message "
+                    "x messages) + T0",
+            "fitted_on": "12 launches of the ragged kernel (tuned shape): each algorithm, messages of "
+                         "1 KiB and of 16 KiB, 1 GiB and 0.5 GiB per launch",
+            "rate_ps_per_op": [r * 1e12 for r in m.rate],
+            "per_message_ns": [x * 1e9 for x in m.per_msg], "overhead_us": m.overhead * 1e6,
             "r2": m.r2, "predicted_ms": pred, "measured_ms": measured_ms,
             "measured_over_predicted": measured_ms / pred}
 
@@ -777,16 +852,18 @@ def run_serve(args, dist):
                                            args.segment_kib << 10), shape=args.serve_shape,
                             warps_per_sm=args.serve_warps, in_place=place)
 
-    def serve_point(srv, load, seed):
+    def serve_point(srv, load, seed, adm=None, count=None):
         rate = load * ref_gbs * 1e9 / mean_req
-        reqs = serve.make_requests(args.requests, rate, seed, pool_bytes)
+        reqs = serve.make_requests(count or args.requests, rate, seed, pool_bytes, align=args.align)
         r0, s0 = srv.rounds_launched, srv.segments
-        srv.run(reqs)
+        srv.run(reqs, admission=adm)
         st = serve.latency_stats(reqs)
         st.update({"offered_load": load, "offered_gbs": rate * mean_req / 1e9,
                    "requests": len(reqs), "rounds": srv.rounds_launched - r0,
                    "segments": srv.segments - s0})
-        return st
+        if adm is not None:
+            st["prediction"] = serve.prediction_stats(reqs)
+        return st, reqs
 
     probe = serve.make_requests(args.requests, 1.0, shard_seed(4, dist.rank), pool_bytes)
     mean_req = float(np.mean([r.nbytes for r in probe]))
@@ -794,9 +871,26 @@ def run_serve(args, dist):
     all_algs = np.concatenate([np.full(r.lengths.shape[0], r.alg, np.uint8) for r in probe])
     points = []
     srv = make_server(in_place)
+    # Eq. 2's linear form for the served work: throughput and per-message
+    # terms from ragged launches of the rounds' pieces, then the serial-chain
+    # term and the fixed latency calibrated on a shorter run at half load;
+    # every load point then predicts each request's completion at admission
+    from paper_2407_09333_b300 import costmodel
+    model = fit_launch_model(api, torch, pool, shape=args.serve_shape)
+    _, cal = serve_point(srv, 0.5, shard_seed(4, dist.rank) + 991, serve.Admission(model),
+                         count=min(args.requests, 4000))
+    model = costmodel.fit_chain(model, [(r.alg, int(r.lengths.max()), r.done - r.arrival)
+                                        for r in cal if r.done >= 0])
     with ClockSampler(torch.cuda.current_device()) as clocks:
         for k, load in enumerate(args.loads):
-            points.append(serve_point(srv, load, shard_seed(4, dist.rank) + 17 * k))
+            points.append(serve_point(srv, load, shard_seed(4, dist.rank) + 17 * k,
+                                      serve.Admission(model))[0])
+        # admission control at the top load: a request whose predicted
+        # completion lies more than --slo-ms after its arrival is shed there
+        shed_point = serve_point(srv, max(args.loads), shard_seed(4, dist.rank) + 17 * len(args.loads),
+                                 serve.Admission(model, slo_s=args.slo_ms * 1e-3))[0]
+        shed_point["slo_ms"] = args.slo_ms
+        shed_point["shed_fraction"] = shed_point.get("rejected", 0) / max(shed_point["requests"], 1)
     budget_used = {"ring_and_rounds": serve.device_bytes(srv.book.capacity, srv.book.req_capacity,
                                                          len(srv.slots), srv.max_msgs),
                    "staging": 0 if srv.in_place else srv.staging_per_round * len(srv.slots)}
@@ -804,15 +898,47 @@ def run_serve(args, dist):
     del srv
     # the other mode at the highest offered load, for comparison
     other = make_server(not in_place)
-    other_point = serve_point(other, max(args.loads), shard_seed(4, dist.rank) + 17 * len(args.loads))
+    other_point = serve_point(other, max(args.loads), shard_seed(4, dist.rank) + 17 * len(args.loads))[0]
     other.close()
     del other
     torch.cuda.empty_cache()
+    host_ingress = None
+    if args.host_requests > 0:
+        # host ingress: the clients' bytes in pinned host memory; each round's
+        # copy step brings its segments over the bus, so the device holds
+        # segments only.  Loads are fractions of the measured host-to-device
+        # copy rate, which bounds this mode.
+        host_pool = torch.from_numpy(np.ascontiguousarray(pool_host)).pin_memory()
+        probe_dev = torch.empty(1 << 30, dtype=torch.uint8, device="cuda")
+        bus_s = _timed_s(torch, lambda: probe_dev.copy_(host_pool[:1 << 30], non_blocking=True))
+        bus_gbs = (1 << 30) / bus_s / 1e9
+        del probe_dev
+        hsrv = serve.Server(host_pool, budget=args.budget_gib << 30, rounds=args.rounds,
+                            segment_bytes=(3 * args.segment_kib << 10, 2 * args.segment_kib << 10,
+                                           args.segment_kib << 10), shape=args.serve_shape,
+                            warps_per_sm=args.serve_warps, in_place=False)
+        hpoints = []
+        for k, load in enumerate(args.host_loads):
+            rate = load * bus_gbs * 1e9 / mean_req
+            reqs = serve.make_requests(args.host_requests, rate, shard_seed(4, dist.rank) + 331 * (k + 1),
+                                       pool_bytes, align=args.align)
+            hsrv.run(reqs)
+            st = serve.latency_stats(reqs)
+            st.update({"offered_load_of_bus": load, "offered_gbs": rate * mean_req / 1e9,
+                       "requests": len(reqs)})
+            hpoints.append(st)
+        hsrv.close()
+        del hsrv, host_pool
+        torch.cuda.empty_cache()
+        host_ingress = {"bus_h2d_gbs": bus_gbs, "points": hpoints,
+                        "mode": "pinned host pool, segments copied over the bus by each round "
+                                "(staging copy), %d GiB device budget" % args.budget_gib}
     plain_gbs, plain_L = plain_equal_bytes_gbs(api, torch, all_lengths, all_algs, pool)
     top = max(points, key=lambda p: p["offered_load"])
-    # sustained rate: requests finishing between the 10th and 90th percentile
-    # of finishing times at the highest offered load (every rank's servers)
-    job_gbs = dist.sum(top["steady_gbs"])
+    # sustained rate at the highest offered load: bytes of every request over
+    # the whole span from the first arrival to the last completion (every
+    # rank's servers); the 10th-90th percentile window is reported beside it
+    job_gbs = dist.sum(top["gbs"])
     line = {
         "metric": METRIC, "value": job_gbs, "unit": "GB/s", "n_gpus": dist.world,
         "steps": len(points), "warmup": 3, "ms_per_step": None, "higher_is_better": True,
@@ -829,7 +955,20 @@ def run_serve(args, dist):
                    "parallelism": "dp%d: independent servers, no collective" % dist.world},
         "serve": points,
         "served_vs_plain_equal_bytes": top["gbs"] / plain_gbs,
+        "served_vs_plain_definition": "whole span: all bytes of the top load point from its first "
+                                      "arrival to its last completion, over the plain kernels' rate "
+                                      "at equal bytes",
         "steady_vs_plain_equal_bytes": top["steady_gbs"] / plain_gbs,
+        "cost_model": {"rate_ps_per_op": [r * 1e12 for r in model.rate],
+                       "per_message_ns": [x * 1e9 for x in model.per_msg],
+                       "overhead_us": model.overhead * 1e6, "r2": model.r2,
+                       "chain_mops_per_s": [c / 1e6 for c in model.chain],
+                       "latency_t0_ms": model.latency_t0 * 1e3,
+                       "fitted_on": "12 fixed-length launches of the ragged kernel in the rounds' "
+                                    "shape (throughput terms), and a %d-request calibration run at "
+                                    "half load (chain terms)" % len(cal)},
+        "admission_control": shed_point,
+        "host_ingress": host_ingress,
         "device_budget_bytes": budget_used,
         "other_mode": dict(other_point, mode="staging copy" if in_place else "in place",
                            steady_vs_plain_equal_bytes=other_point["steady_gbs"] / plain_gbs),
@@ -968,6 +1107,14 @@ def main(argv=None):
                    help="serve through the staging copy instead of hashing segments where the "
                         "client's bytes are (c5)")
     p.add_argument("--pool-mib", type=int, default=2048, help="random-byte pool for requests (c5)")
+    p.add_argument("--align", type=int, default=16,
+                   help="messages start at multiples of this many bytes of the pool (c5; 1 = any)")
+    p.add_argument("--slo-ms", type=float, default=100.0,
+                   help="latency target of the admission-control point (c5)")
+    p.add_argument("--host-requests", type=int, default=2000,
+                   help="requests per load point of the host-ingress sweep (c5; 0 = skip)")
+    p.add_argument("--host-loads", type=float, nargs="+", default=[0.5, 0.9],
+                   help="host-ingress loads as fractions of the measured bus copy rate (c5)")
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--e2e-steps", type=int, default=10)
     p.add_argument("--e2e-slots", action="store_true",
@@ -987,6 +1134,8 @@ def main(argv=None):
     p.add_argument("--separate", action="store_true",
                    help="plain workloads: one kernel per algorithm instead of the fused kernel")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-extras", action="store_true",
+                   help="default run: skip the short long-message and ragged measurements")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--int-peak", action="store_true",
                    help="run the integer-issue microbenchmark instead of the hashing step")

@@ -61,6 +61,7 @@ class CostModel:
     r2: float             # coefficient of determination on the fitting set
     per_msg: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros(3))
     chain: np.ndarray | None = None   # ops per second of one serial chain, per algorithm
+    latency_t0: float = 0.0           # fixed latency of a served request (fit_chain)
 
     def predict(self, work: np.ndarray, msgs: np.ndarray | None = None) -> float:
         t = float(np.dot(self.rate, work) + self.overhead)
@@ -127,18 +128,27 @@ def fit(samples) -> CostModel:
 
 
 def fit_chain(model: CostModel, observations) -> CostModel:
-    """Calibrates the per-algorithm chain rate from requests that were bound
-    by their longest message: observations are (alg, longest message length,
-    latency seconds), typically every request of a lightly loaded run.  The
-    rate is the median over requests of ops / latency.  Latency beyond the
-    chain (admission, the rounds' cadence) lowers it, so the chain times it
-    predicts err long, by the fixed costs a light load still has.
-    Algorithms without observations keep no chain term."""
+    """Calibrates the per-algorithm chain rate from served requests:
+    observations are (alg, longest message length, latency seconds), e.g.
+    every request of a moderately loaded run, whose latency is mostly its
+    longest message's chain.  Fits latency = t0 + ops / chain_a by
+    non-negative least squares (one fixed cost t0 for all requests, stored
+    as `latency_t0`); algorithms without observations keep no chain term."""
+    obs = [(int(a), float(shard.message_costs(np.array([L]), alg=int(a))[0]), float(lat))
+           for a, L, lat in observations if lat > 0]
     chain = np.zeros(3)
-    obs = list(observations)
-    for a in range(3):
-        r = [float(shard.message_costs(np.array([L]), alg=a)[0]) / lat
-             for alg, L, lat in obs if alg == a and lat > 0]
-        if r:
-            chain[a] = float(np.median(r))
-    return dataclasses.replace(model, chain=chain)
+    t0 = 0.0
+    if obs:
+        algs_seen = sorted({a for a, _, _ in obs})
+        X = np.zeros((len(obs), len(algs_seen) + 1))
+        y = np.zeros(len(obs))
+        for i, (a, ops, lat) in enumerate(obs):
+            X[i, algs_seen.index(a)] = ops
+            X[i, -1] = 1.0
+            y[i] = lat
+        scale = np.maximum(np.abs(X).max(axis=0), 1e-30)
+        coef = _nnls(X / scale, y) / scale
+        for j, a in enumerate(algs_seen):
+            chain[a] = 1.0 / coef[j] if coef[j] > 0 else 0.0
+        t0 = float(coef[-1])
+    return dataclasses.replace(model, chain=chain, latency_t0=t0)
