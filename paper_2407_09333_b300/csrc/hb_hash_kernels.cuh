@@ -67,7 +67,9 @@ __global__ void __launch_bounds__(WARPS * 32) hb_mixed_kernel(KernelArgs a) {
   X(20, 1, 4, 2, true)   \
   X(21, 1, 2, 2, true)   \
   X(22, 1, 3, 2, true)   \
-  X(23, 2, 2, 2, true)
+  X(23, 2, 2, 2, true)   \
+  X(24, 4, 2, 4, true)   \
+  X(25, 2, 2, 4, true)
 
 struct ShapeDesc {
   int warps, stages, kb;

@@ -27,6 +27,11 @@ With `in_place=True` a round skips the copy and hashes each segment where
 the client's bytes are; the staging budget then only caps the bytes the
 rounds have claimed at a time (the server owns no copy of the payload).
 
+Host ingress: when the clients' pool is pinned host memory, the rounds'
+copy step brings each segment over the bus into the staging area as the
+segment's turn comes (the device never holds a whole request), so the
+device budget bounds the segments in flight and the bus bounds throughput.
+
 Host side (this module, plain Python): admission in arrival order while the
 ring and the request table have room (`RingBook`), one batch of metadata
 copies per loop for the newly admitted requests, round launches, and the
@@ -162,11 +167,11 @@ class Admission:
     """
 
     def __init__(self, model, cap_s: float | None = None, slo_s: float | None = None,
-                 t0: float = 0.0):
+                 t0: float | None = None):
         self.model = model
         self.cap_s = cap_s
         self.slo_s = slo_s
-        self.t0 = t0
+        self.t0 = float(getattr(model, "latency_t0", 0.0)) if t0 is None else t0
         self._backlog = 0.0
         self._t = 0.0
         self.inflight = 0
@@ -237,7 +242,8 @@ def prediction_stats(requests: list) -> dict:
 
 def device_bytes(capacity: int, req_capacity: int, rounds: int, max_msgs: int) -> int:
     """Device memory of everything but the staging areas."""
-    ws = 6272 + 4 * (max_msgs + 31 * 768)
+    groups = 3 * 32 * 16                        # (cost bucket, algorithm) groups
+    ws = 4 * (2 * groups + 32) + 4 * (max_msgs + 31 * groups)
     return capacity * RING_ENTRY_BYTES + req_capacity * 4 + rounds * (
         max_msgs * ROUND_ENTRY_BYTES + ws + 256)
 
@@ -268,7 +274,18 @@ class Server:
         import torch
         from . import api
         self.torch, self.api, self.device = torch, api, device
-        self.pool = pool                                     # device uint8 tensor
+        # the clients' bytes: a device tensor, or pinned host memory (host
+        # ingress: each round's copy step reads its segments over the bus, so
+        # only segments, never whole requests, occupy device memory)
+        self.pool = pool
+        self.host_ingress = not pool.is_cuda
+        if self.host_ingress:
+            if not pool.is_pinned():
+                raise ValueError("a host pool must be pinned memory")
+            if in_place:
+                raise ValueError("a host pool is served through the staging copy (in_place=False)")
+        # with unified addressing, pinned host memory has the same address on
+        # the device as on the host
         self.pool_addr = pool.data_ptr()
         self.max_msgs = max_msgs
         self.shape = shape

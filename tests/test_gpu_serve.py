@@ -249,6 +249,24 @@ def test_served_at_config5_shape_unaligned_equals_oracle(env, big_pool, oracle_m
     assert api.device_status() == 0
 
 
+def test_served_from_host_memory_equals_oracle(env, oracle_mod):
+    # host ingress: the clients' bytes stay in pinned host memory and each
+    # round's copy step brings its segments over the bus, at any byte offset
+    api, serve, pool_host, pool_dev, pool_bytes = env
+    host_pool = torch.from_numpy(np.ascontiguousarray(pool_host)).pin_memory()
+    reqs = serve.make_requests(80, 4000.0, seed=13, pool_bytes=pool_bytes, max_msgs=64,
+                               max_len=1 << 17, align=1)
+    srv = serve.Server(host_pool, budget=128 << 20, rounds=2, segment_bytes=(12288, 8192, 4096),
+                       max_msgs=4096, capacity=1 << 14, req_capacity=256, in_place=False)
+    assert srv.host_ingress
+    srv.run(reqs, keep_digests=True)
+    srv.close()
+    _check_requests(api, oracle_mod, reqs, pool_host, oracle_every=1)
+    assert api.device_status() == 0
+    with pytest.raises(ValueError):
+        serve.Server(host_pool, budget=128 << 20, in_place=True)
+
+
 def test_completion_flags_must_be_mapped_host_memory(env):
     api = env[0]
     plan = api.Plan(64)

@@ -221,7 +221,10 @@ def test_admission_without_chain_calibration_uses_work_alone():
     adm = Admission(m)
     w, c = adm.estimate(r)
     assert w == pytest.approx(3e-12 * (1 + 2) * 1412) and c == 0.0
-    m2 = costmodel.fit_chain(m, [(2, 16384, 257 * 1412 / 1e7), (2, 16384, 257 * 1412 / 2e7),
-                                 (2, 16384, 257 * 1412 / 3e7)])
-    assert m2.chain[2] == pytest.approx(2e7) and m2.chain[0] == 0
+    # latency = 1 ms + ops / 2e7 for SM3 and ops / 5e7 for MD5: both recovered
+    obs = [(2, L, 1e-3 + ((L + 72) // 64) * 1412 / 2e7) for L in (100, 5000, 16384, 70000)]
+    obs += [(0, L, 1e-3 + ((L + 72) // 64) * 324 / 5e7) for L in (300, 9000, 120000)]
+    m2 = costmodel.fit_chain(m, obs)
+    assert m2.chain[2] == pytest.approx(2e7, rel=1e-6) and m2.chain[0] == pytest.approx(5e7, rel=1e-6)
+    assert m2.chain[1] == 0 and m2.latency_t0 == pytest.approx(1e-3, rel=1e-6)
     assert m2.chain_time([100, 16384], 2) == pytest.approx(257 * 1412 / 2e7)
