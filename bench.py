@@ -466,7 +466,29 @@ def measure(args, dist):
     mean_len = batch.total_bytes / max(n, 1)
     fused = not mixed and not args.separate
     rec = torch.empty((n, 96), dtype=torch.uint8, device="cuda") if fused else None
+    items = fused and args.as_items
+    if items:
+        # the three-algorithm step as 3n (message, algorithm) items through
+        # the ragged kernel: item 3i + a is message i under algorithm a, and
+        # its 32-byte slot is slot a of record i
+        off3 = off.repeat_interleave(3).contiguous()
+        ln3 = ln.repeat_interleave(3).contiguous()
+        algs3 = torch.tensor([0, 1, 2], dtype=torch.uint8, device="cuda").repeat(n).contiguous()
+        out3 = rec.view(3 * n, 32)
     for a in ([None] if mixed else [0, 1, 2] + ([api.ALL] if fused else [])):
+        if items and a == api.ALL:
+            if args.shape is not None:
+                api.tune_set(api.TUNE_MIXED, args.shape)
+                if args.buckets:
+                    api.tune_buckets(*[int(x) for x in args.buckets.split(",")])
+                tuned["all_as_items"] = {"shape": args.shape, "fixed": True}
+                continue
+            r = autotune.tune(None, packed, off3, ln3, out3, algs=algs3, mean_len=mean_len)
+            tuned["all_as_items"] = {"warps": r["warps"], "stages": r["stages"],
+                                     "blocks_per_stage": r.get("blocks_per_stage", 1),
+                                     "cooperative": r.get("cooperative", False),
+                                     "cached": r["cached"], "warps_per_sm": r.get("warps_per_sm")}
+            continue
         if args.shape is not None:
             # fixed launch configuration (reproducible profiler captures)
             api.tune_set(api.TUNE_MIXED if a is None else a, args.shape)
@@ -501,6 +523,10 @@ def measure(args, dist):
         launches = [(None, lambda: plan.replay(n))]
         bytes_per_step = batch.total_bytes
         msgs_per_step = n
+    elif items:
+        launches = [(api.ALL, lambda: api.hash_batch_mixed(algs3, packed, off3, ln3, out=out3))]
+        bytes_per_step = 3 * batch.total_bytes
+        msgs_per_step = 3 * n
     elif fused:
         # every message with all three algorithms in one pass (hash_batch_all)
         launches = [(api.ALL, lambda: api.hash_batch_all(packed, off, ln, out=rec))]
@@ -611,9 +637,10 @@ def measure(args, dist):
     dom_ops = per_alg[dom_name]["alu_Tops"] * 1e12 * t_dom
     hbm_bytes_per_launch = hbm_of[dom_name]
     peak_alu = alu_peak_tops(sms, peaks["sm_max_mhz"])
-    kernel_key = "%s:%s" % (args.workload, dom_name)
+    kernel_key = "%s:%s" % (args.workload, "items" if items else dom_name)
     roofline = {
-        "bound": "alu", "kernel": "hb_%s_kernel<%s>" % ("mixed" if mixed else "plain", dom_name),
+        "bound": "alu", "kernel": "hb_%s_kernel<%s>" % ("mixed" if mixed or items else "plain",
+                                                      "3n items" if items else dom_name),
         "achieved": dom_ops / t_dom / 1e12, "peak": peak_alu, "unit": "Tops/s",
         "frac": dom_ops / t_dom / 1e12 / peak_alu,
         "peak_source": "derived: %d SMs x 4 sub-partitions x 32 lanes x %.0f MHz max SM clock "
@@ -633,6 +660,12 @@ def measure(args, dist):
         "higher_is_better": True, "scaling": args.scaling, "vs_baseline": None, "dtype": "u32",
         "data": "synthetic: uniform random bytes (numpy PCG64), shard seed per rank",
         "config": {"workload": desc, "messages_per_gpu": n, "bytes_per_gpu": batch.total_bytes,
+                   "value_counts": ("message bytes hashed, once per message" if mixed else
+                                    "byte-hashes over three algorithms: each message's bytes once "
+                                    "per algorithm (3 x %d bytes per step%s); per-algorithm rates "
+                                    "of the single-algorithm kernels are in per_alg_separate_kernels"
+                                    % (batch.total_bytes, ", one fused launch reading them once"
+                                       if fused else ", three launches")),
                    "l2": "no flush: inputs larger than the 126 MB L2",
                    "parallelism": "dp%d: disjoint message shards, no collective on the data path" % dist.world},
         "mhash_per_s": job_msgs / (ms * 1e-3) / 1e6,
@@ -643,7 +676,7 @@ def measure(args, dist):
         # plain: one fused kernel (or one per algorithm with --separate);
         # ragged graph: count-setter, group histogram, scan, scatter and the
         # persistent hashing kernel
-        "gpu_launches": args.steps * nl * (5 if mixed else 1),
+        "gpu_launches": args.steps * nl * (5 if mixed else 4 if items else 1),
         "clocks": clk,
     }
 
@@ -876,31 +909,45 @@ def run_serve(args, dist):
     # term and the fixed latency calibrated on a shorter run at half load;
     # every load point then predicts each request's completion at admission
     from paper_2407_09333_b300 import costmodel
-    model = fit_launch_model(api, torch, pool, shape=args.serve_shape)
-    _, cal = serve_point(srv, 0.5, shard_seed(4, dist.rank) + 991, serve.Admission(model),
-                         count=min(args.requests, 4000))
-    model = costmodel.fit_chain(model, [(r.alg, int(r.lengths.max()), r.done - r.arrival)
-                                        for r in cal if r.done >= 0])
+    model, cal, drain, shed_point = None, [], 1.0, None
+    if not args.no_admission:
+        model = fit_launch_model(api, torch, pool, shape=args.serve_shape)
+        _, cal = serve_point(srv, 0.5, shard_seed(4, dist.rank) + 991, serve.Admission(model),
+                             count=min(args.requests, 4000))
+        model = costmodel.fit_chain(model, [(r.alg, int(r.lengths.max()), r.done - r.arrival)
+                                            for r in cal if r.done >= 0])
+        # the served path's rate against the model's: a burst of requests
+        burst = serve.make_requests(min(args.requests, 3000), 1e9, shard_seed(4, dist.rank) + 993,
+                                    pool_bytes, align=args.align)
+        for r in burst:
+            r.arrival = 0.0
+        srv.run(burst)
+        drain = serve.calibrate_drain(model, burst)
+    adm = (lambda **kw: serve.Admission(model, drain=drain, **kw)) if model else (lambda **kw: None)
     with ClockSampler(torch.cuda.current_device()) as clocks:
         for k, load in enumerate(args.loads):
-            points.append(serve_point(srv, load, shard_seed(4, dist.rank) + 17 * k,
-                                      serve.Admission(model))[0])
-        # admission control at the top load: a request whose predicted
-        # completion lies more than --slo-ms after its arrival is shed there
-        shed_point = serve_point(srv, max(args.loads), shard_seed(4, dist.rank) + 17 * len(args.loads),
-                                 serve.Admission(model, slo_s=args.slo_ms * 1e-3))[0]
-        shed_point["slo_ms"] = args.slo_ms
-        shed_point["shed_fraction"] = shed_point.get("rejected", 0) / max(shed_point["requests"], 1)
+            points.append(serve_point(srv, load, shard_seed(4, dist.rank) + 17 * k, adm())[0])
+        if model is not None:
+            # admission control at the top load: a request whose predicted
+            # completion lies more than --slo-ms after its arrival is shed there
+            shed_point = serve_point(srv, max(args.loads),
+                                     shard_seed(4, dist.rank) + 17 * len(args.loads),
+                                     adm(slo_s=args.slo_ms * 1e-3))[0]
+            shed_point["slo_ms"] = args.slo_ms
+            shed_point["shed_fraction"] = shed_point.get("rejected", 0) / max(shed_point["requests"], 1)
     budget_used = {"ring_and_rounds": serve.device_bytes(srv.book.capacity, srv.book.req_capacity,
                                                          len(srv.slots), srv.max_msgs),
                    "staging": 0 if srv.in_place else srv.staging_per_round * len(srv.slots)}
     srv.close()
     del srv
     # the other mode at the highest offered load, for comparison
-    other = make_server(not in_place)
-    other_point = serve_point(other, max(args.loads), shard_seed(4, dist.rank) + 17 * len(args.loads))[0]
-    other.close()
-    del other
+    other_point = None
+    if not args.no_other_mode:
+        other = make_server(not in_place)
+        other_point = serve_point(other, max(args.loads),
+                                  shard_seed(4, dist.rank) + 17 * len(args.loads))[0]
+        other.close()
+        del other
     torch.cuda.empty_cache()
     host_ingress = None
     if args.host_requests > 0:
@@ -959,19 +1006,21 @@ def run_serve(args, dist):
                                       "arrival to its last completion, over the plain kernels' rate "
                                       "at equal bytes",
         "steady_vs_plain_equal_bytes": top["steady_gbs"] / plain_gbs,
-        "cost_model": {"rate_ps_per_op": [r * 1e12 for r in model.rate],
-                       "per_message_ns": [x * 1e9 for x in model.per_msg],
-                       "overhead_us": model.overhead * 1e6, "r2": model.r2,
-                       "chain_mops_per_s": [c / 1e6 for c in model.chain],
-                       "latency_t0_ms": model.latency_t0 * 1e3,
-                       "fitted_on": "12 fixed-length launches of the ragged kernel in the rounds' "
-                                    "shape (throughput terms), and a %d-request calibration run at "
-                                    "half load (chain terms)" % len(cal)},
+        "cost_model": None if model is None else {
+            "rate_ps_per_op": [r * 1e12 for r in model.rate],
+            "per_message_ns": [x * 1e9 for x in model.per_msg],
+            "overhead_us": model.overhead * 1e6, "r2": model.r2,
+            "chain_mops_per_s": [c / 1e6 for c in model.chain],
+            "latency_t0_ms": model.latency_t0 * 1e3, "served_over_model_rate": drain,
+            "fitted_on": "12 fixed-length launches of the ragged kernel in the rounds' shape "
+                         "(throughput terms), a %d-request run at half load (chain terms) and a "
+                         "burst of %d requests (served rate)" % (len(cal), min(args.requests, 3000))},
         "admission_control": shed_point,
         "host_ingress": host_ingress,
         "device_budget_bytes": budget_used,
-        "other_mode": dict(other_point, mode="staging copy" if in_place else "in place",
-                           steady_vs_plain_equal_bytes=other_point["steady_gbs"] / plain_gbs),
+        "other_mode": None if other_point is None else dict(
+            other_point, mode="staging copy" if in_place else "in place",
+            steady_vs_plain_equal_bytes=other_point["steady_gbs"] / plain_gbs),
         "plain_equal_bytes_gbs": plain_gbs, "plain_mean_length": plain_L,
         "p50_ms_at_top_load": top["p50_ms"], "p99_ms_at_top_load": top["p99_ms"],
         "clocks": clocks.summary(),
@@ -1111,6 +1160,10 @@ def main(argv=None):
                    help="messages start at multiples of this many bytes of the pool (c5; 1 = any)")
     p.add_argument("--slo-ms", type=float, default=100.0,
                    help="latency target of the admission-control point (c5)")
+    p.add_argument("--no-other-mode", action="store_true",
+                   help="c5: skip the comparison point in the other serving mode")
+    p.add_argument("--no-admission", action="store_true",
+                   help="c5: skip the cost model, its calibration and the admission-control point")
     p.add_argument("--host-requests", type=int, default=2000,
                    help="requests per load point of the host-ingress sweep (c5; 0 = skip)")
     p.add_argument("--host-loads", type=float, nargs="+", default=[0.5, 0.9],
@@ -1133,6 +1186,9 @@ def main(argv=None):
                    help="device memory the e2e host path may use (0 = whole batch on the device)")
     p.add_argument("--separate", action="store_true",
                    help="plain workloads: one kernel per algorithm instead of the fused kernel")
+    p.add_argument("--as-items", action="store_true",
+                   help="plain workloads: the three-algorithm step as (message, algorithm) items "
+                        "through the ragged kernel instead of the fused kernel")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-extras", action="store_true",
                    help="default run: skip the short long-message and ragged measurements")

@@ -117,16 +117,22 @@ __device__ __forceinline__ uint32_t segment_blocks(uint32_t len, uint64_t seg, i
 // the per-lane metadata of the next task already requested from memory.
 
 // Fixed algorithm, static grid-stride over tasks of 32 consecutive messages.
-template <int ALG>
+// The per-lane metadata (offset, length) of the next DEPTH tasks is in
+// flight while the warp issues the current one.  For one-block messages a
+// task lasts about one DRAM round trip, so the single-algorithm kernels look
+// two tasks ahead (one left them waiting on these loads); the fused kernel
+// spends three algorithms' work on each task and keeps one, which spares it
+// registers.
+template <int ALG, int DEPTH = (ALG == HB_ALL ? 1 : 2)>
 struct StaticSource {
   const uint8_t* packed;
   const uint64_t* offsets;
   const uint32_t* lengths;
   uint64_t n, ntasks, stride, next;  // warp-uniform
   uint32_t lane;
-  bool pf_ok;
-  uint64_t pf_msg, pf_off;
-  uint32_t pf_len;
+  bool pf_ok[DEPTH];
+  uint64_t pf_msg[DEPTH], pf_off[DEPTH];
+  uint32_t pf_len[DEPTH];
 
   __device__ StaticSource(const KernelArgs& args, uint64_t first, uint64_t stride_, uint32_t lane_)
       : packed(args.packed),
@@ -137,17 +143,18 @@ struct StaticSource {
         stride(stride_),
         next(first),
         lane(lane_) {
-    prefetch();
+#pragma unroll
+    for (int k = 0; k < DEPTH; ++k) prefetch(k);
   }
 
-  __device__ __forceinline__ void prefetch() {
-    pf_ok = next < ntasks;
-    pf_msg = next * 32 + lane;
-    pf_off = 0;
-    pf_len = 0;
-    if (pf_ok && pf_msg < n) {
-      pf_off = ldg_nc_u64(offsets + pf_msg);
-      pf_len = ldg_nc_u32(lengths + pf_msg);
+  __device__ __forceinline__ void prefetch(int k) {
+    pf_ok[k] = next < ntasks;
+    pf_msg[k] = next * 32 + lane;
+    pf_off[k] = 0;
+    pf_len[k] = 0;
+    if (pf_ok[k] && pf_msg[k] < n) {
+      pf_off[k] = ldg_nc_u64(offsets + pf_msg[k]);
+      pf_len[k] = ldg_nc_u32(lengths + pf_msg[k]);
     }
     next += stride;
   }
@@ -156,16 +163,23 @@ struct StaticSource {
 
   // Move to the next task; false when the source is exhausted.
   __device__ __forceinline__ bool take(LaneTask& t) {
-    if (!pf_ok) return false;
-    const bool valid = pf_msg < n;
-    t.msg = pf_msg;
-    t.addr = reinterpret_cast<uint64_t>(packed) + pf_off;
-    t.len = pf_len;
-    t.nb = valid ? padded_blocks(pf_len) : 0u;
+    if (!pf_ok[0]) return false;
+    const bool valid = pf_msg[0] < n;
+    t.msg = pf_msg[0];
+    t.addr = reinterpret_cast<uint64_t>(packed) + pf_off[0];
+    t.len = pf_len[0];
+    t.nb = valid ? padded_blocks(pf_len[0]) : 0u;
     t.alg = ALG;
     t.seg = 0;
     t.slot = 0;
-    prefetch();
+#pragma unroll
+    for (int k = 0; k + 1 < DEPTH; ++k) {
+      pf_ok[k] = pf_ok[k + 1];
+      pf_msg[k] = pf_msg[k + 1];
+      pf_off[k] = pf_off[k + 1];
+      pf_len[k] = pf_len[k + 1];
+    }
+    prefetch(DEPTH - 1);
     return true;
   }
 };

@@ -142,11 +142,14 @@ class Admission:
 
     The GPU is modelled as one work-conserving server: an admitted request
     adds its predicted GPU-seconds (`model.work_seconds`: the fitted
-    throughput and per-message terms) to a backlog that drains at one
-    GPU-second per second while requests are in flight.  A request admitted
+    throughput and per-message terms) to a backlog that drains at `drain`
+    GPU-seconds per second while requests are in flight -- 1 if serving ran
+    at the fitted launches' rate; the served path's own rate is lower
+    (rounds, segments, the tails of serial chains), and `drain` is that ratio
+    measured on a burst of requests (`calibrate_drain`).  A request admitted
     at time t is predicted to finish at
 
-        t + max(backlog(t) + work, chain) + t0
+        t + max(backlog(t) + work / drain, chain) + t0
 
     -- after the work admitted before it and its own, and not before its
     longest message's serial chain (`model.chain_time`); t0 is the fixed
@@ -167,10 +170,13 @@ class Admission:
     """
 
     def __init__(self, model, cap_s: float | None = None, slo_s: float | None = None,
-                 t0: float | None = None):
+                 t0: float | None = None, drain: float = 1.0):
+        if drain <= 0:
+            raise ValueError("drain must be positive")
         self.model = model
         self.cap_s = cap_s
         self.slo_s = slo_s
+        self.drain = drain
         self.t0 = float(getattr(model, "latency_t0", 0.0)) if t0 is None else t0
         self._backlog = 0.0
         self._t = 0.0
@@ -178,13 +184,14 @@ class Admission:
         self.waiting_s = 0.0       # predicted work of requests waiting to be admitted
 
     def estimate(self, req):
-        """(work seconds, chain seconds) of a request, also stored on it."""
-        req.work_s = self.model.work_seconds(req.lengths, req.alg)
+        """(work seconds at the served rate, chain seconds) of a request,
+        also stored on it."""
+        req.work_s = self.model.work_seconds(req.lengths, req.alg) / self.drain
         req.chain_s = self.model.chain_time(req.lengths, req.alg)
         return req.work_s, req.chain_s
 
     def backlog(self, now: float) -> float:
-        """Predicted GPU-seconds of admitted work not yet done at `now`."""
+        """Predicted seconds of admitted work not yet done at `now`."""
         if now > self._t:
             if self.inflight:
                 self._backlog = max(0.0, self._backlog - (now - self._t))
@@ -222,6 +229,26 @@ class Admission:
         self.inflight -= 1
         if self.inflight == 0:
             self._backlog = 0.0    # nothing in flight: the device is idle
+
+
+def calibrate_drain(model, requests: list) -> float:
+    """The served path's rate relative to the model's, from requests served
+    in one burst (all arriving at once, so the device never idles): bytes of
+    the requests finishing between the 10th and 90th percentile of finishing
+    times, over that interval, against the bytes per second the model's
+    throughput terms predict for the same requests."""
+    done = [r for r in requests if r.done >= 0]
+    if len(done) < 10:
+        raise ValueError("too few finished requests")
+    fin = np.array([r.done for r in done])
+    t10, t90 = np.percentile(fin, [10, 90])
+    mid = [r for r in done if t10 < r.done <= t90]
+    if t90 <= t10 or not mid:
+        raise ValueError("finishing times too close together")
+    served = sum(r.nbytes for r in mid) / (t90 - t10)
+    work = sum(model.work_seconds(r.lengths, r.alg) for r in done)
+    modelled = sum(r.nbytes for r in done) / work
+    return served / modelled
 
 
 def prediction_stats(requests: list) -> dict:

@@ -128,9 +128,11 @@ def _requests(n, rate_per_s, seed):
 
 def _serve(adm, reqs):
     """Event-driven fake server: admitted work is done first come first
-    served at one GPU-second per second; a request completes when its work
-    is done, and not before its longest chain has run since admission.
-    Drives `adm` with the simulated clock; returns the requests."""
+    served at adm.drain times the model's rate (req.work_s, which the policy
+    sets at arrival, is already in served seconds); a request completes when
+    its work is done, and not before its longest chain has run since
+    admission.  Drives `adm` with the simulated clock; returns the order of
+    admission."""
     import heapq
     pending, done_heap, order = [], [], []
     work_free = 0.0                        # when the FIFO server finishes the admitted work
@@ -158,9 +160,11 @@ def _serve(adm, reqs):
     return order
 
 
-def test_admission_predicts_completion_of_a_first_come_first_served_device():
-    reqs = _requests(400, 2000.0, seed=1)
-    adm = Admission(_Model(), t0=1e-4)
+@pytest.mark.parametrize("drain", [1.0, 0.8])
+def test_admission_predicts_completion_of_a_first_come_first_served_device(drain):
+    # the fake device serves admitted work at `drain` times the model's rate
+    reqs = _requests(400, 2000.0 * drain, seed=1)
+    adm = Admission(_Model(), t0=1e-4, drain=drain)
     order = _serve(adm, reqs)
     assert order == sorted(order)                       # admitted in arrival order
     for r in reqs:
@@ -211,6 +215,17 @@ def test_admission_sheds_requests_predicted_past_the_target():
     assert 0.25 < shed_work < 0.45
     assert 0 < sum(r.rejected for r in shed) < len(shed) * shed_work
     assert all(r.done < 0 for r in shed if r.rejected)
+
+
+def test_drain_is_calibrated_from_a_burst():
+    from paper_2407_09333_b300.serve import calibrate_drain
+    model = _Model()
+    reqs = _requests(3000, 1e9, seed=4)                  # a burst: all at once
+    for r in reqs:
+        r.arrival = 0.0
+    adm = Admission(model, drain=0.7)                    # the device's true rate
+    _serve(adm, reqs)
+    assert calibrate_drain(model, reqs) == pytest.approx(0.7, rel=0.1)
 
 
 def test_admission_without_chain_calibration_uses_work_alone():
