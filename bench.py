@@ -923,7 +923,9 @@ def run_serve(args, dist):
             r.arrival = 0.0
         srv.run(burst)
         drain = serve.calibrate_drain(model, burst)
-    adm = (lambda **kw: serve.Admission(model, drain=drain, **kw)) if model else (lambda **kw: None)
+    cap_s = args.cap_ms * 1e-3 if args.cap_ms > 0 else None
+    adm = ((lambda **kw: serve.Admission(model, drain=drain, cap_s=cap_s, **kw)) if model
+           else (lambda **kw: None))
     with ClockSampler(torch.cuda.current_device()) as clocks:
         for k, load in enumerate(args.loads):
             points.append(serve_point(srv, load, shard_seed(4, dist.rank) + 17 * k, adm())[0])
@@ -934,6 +936,7 @@ def run_serve(args, dist):
                                      shard_seed(4, dist.rank) + 17 * len(args.loads),
                                      adm(slo_s=args.slo_ms * 1e-3))[0]
             shed_point["slo_ms"] = args.slo_ms
+            shed_point["cap_ms"] = args.cap_ms
             shed_point["shed_fraction"] = shed_point.get("rejected", 0) / max(shed_point["requests"], 1)
     budget_used = {"ring_and_rounds": serve.device_bytes(srv.book.capacity, srv.book.req_capacity,
                                                          len(srv.slots), srv.max_msgs),
@@ -1160,6 +1163,9 @@ def main(argv=None):
                    help="messages start at multiples of this many bytes of the pool (c5; 1 = any)")
     p.add_argument("--slo-ms", type=float, default=100.0,
                    help="latency target of the admission-control point (c5)")
+    p.add_argument("--cap-ms", type=float, default=0.0,
+                   help="c5: hold requests on the host while the predicted in-flight work exceeds "
+                        "this many ms (0 = admit while the ring has room)")
     p.add_argument("--no-other-mode", action="store_true",
                    help="c5: skip the comparison point in the other serving mode")
     p.add_argument("--no-admission", action="store_true",
