@@ -926,7 +926,9 @@ def run_serve(args, dist):
     cap_s = args.cap_ms * 1e-3 if args.cap_ms > 0 else None
     adm = ((lambda **kw: serve.Admission(model, drain=drain, cap_s=cap_s, **kw)) if model
            else (lambda **kw: None))
-    with ClockSampler(torch.cuda.current_device()) as clocks:
+    # the serving loop polls the device from the host; a slow clock sampler
+    # (nvidia-smi takes driver locks on every poll) keeps out of its way
+    with ClockSampler(torch.cuda.current_device(), period_s=0.2) as clocks:
         for k, load in enumerate(args.loads):
             points.append(serve_point(srv, load, shard_seed(4, dist.rank) + 17 * k, adm())[0])
         if model is not None:

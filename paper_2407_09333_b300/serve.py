@@ -130,6 +130,7 @@ class Req:
     work_s: float = 0.0          # predicted GPU-seconds (Admission)
     chain_s: float = 0.0         # predicted longest serial chain (Admission)
     predicted_done: float = -1.0 # predicted completion time, set at admission
+    chain_bound: bool = False    # the prediction was set by the longest chain
 
     def __post_init__(self):
         self.lengths = np.asarray(self.lengths, dtype=np.uint32)
@@ -165,18 +166,27 @@ class Admission:
              requests still waiting ahead of it -- would exceed slo_s is
              rejected at once instead of queued.
 
+    The chain term follows the load: a chain shares its SM sub-partition with
+    more busy warps when the device is fuller, so every request that finishes
+    with a chain-bound prediction updates a running factor (`chain_scale`,
+    exponentially weighted, weight `adapt`) by its measured chain time over
+    the model's; later predictions use the model's chain times times that
+    factor.  adapt = 0 keeps the model's chain times.
+
     Time is whatever clock the caller passes (seconds), so the policy runs
     under a fake clock in tests.
     """
 
     def __init__(self, model, cap_s: float | None = None, slo_s: float | None = None,
-                 t0: float | None = None, drain: float = 1.0):
+                 t0: float | None = None, drain: float = 1.0, adapt: float = 0.05):
         if drain <= 0:
             raise ValueError("drain must be positive")
         self.model = model
         self.cap_s = cap_s
         self.slo_s = slo_s
         self.drain = drain
+        self.adapt = adapt
+        self.chain_scale = 1.0
         self.t0 = float(getattr(model, "latency_t0", 0.0)) if t0 is None else t0
         self._backlog = 0.0
         self._t = 0.0
@@ -201,7 +211,7 @@ class Admission:
     def predicted_latency(self, req, now: float) -> float:
         """Latency from arrival if the request joined the queue at `now`."""
         ahead = self.backlog(now) + self.waiting_s
-        return (now - req.arrival) + max(ahead + req.work_s, req.chain_s) + self.t0
+        return (now - req.arrival) + max(ahead + req.work_s, self.chain_scale * req.chain_s) + self.t0
 
     def arrive(self, req, now: float) -> bool:
         """False when the request is shed; otherwise it waits for admission."""
@@ -219,7 +229,9 @@ class Admission:
 
     def admit(self, req, now: float):
         b = self.backlog(now)
-        req.predicted_done = now + max(b + req.work_s, req.chain_s) + self.t0
+        chain = self.chain_scale * req.chain_s
+        req.predicted_done = now + max(b + req.work_s, chain) + self.t0
+        req.chain_bound = chain > b + req.work_s
         self._backlog = b + req.work_s
         self.waiting_s = max(0.0, self.waiting_s - req.work_s)
         self.inflight += 1
@@ -229,6 +241,10 @@ class Admission:
         self.inflight -= 1
         if self.inflight == 0:
             self._backlog = 0.0    # nothing in flight: the device is idle
+        if self.adapt > 0 and getattr(req, "chain_bound", False) and req.chain_s > 0:
+            seen = (now - req.admitted - self.t0) / req.chain_s
+            seen = min(max(seen, 0.25), 8.0)
+            self.chain_scale += self.adapt * (seen - self.chain_scale)
 
 
 def calibrate_drain(model, requests: list) -> float:

@@ -217,6 +217,34 @@ def test_admission_sheds_requests_predicted_past_the_target():
     assert all(r.done < 0 for r in shed if r.rejected)
 
 
+def test_chain_factor_follows_a_slower_device():
+    # the fake device runs every chain 1.6x longer than the model says: the
+    # running factor converges there and later predictions come out right
+    import heapq
+    model = _Model()
+    reqs = _requests(3000, 200.0, seed=5)              # light load: chain-bound requests
+    adm = Admission(model, t0=1e-4, adapt=0.05)
+    heap = []
+    for r in reqs:
+        while heap and heap[0][0] <= r.arrival:
+            td, _, q = heapq.heappop(heap)
+            q.done = td
+            adm.finish(q, td)
+        adm.arrive(r, r.arrival)
+        adm.admit(r, r.arrival)
+        r.admitted = r.arrival
+        real = 1.6 * model.chain_time(r.lengths, r.alg)
+        heapq.heappush(heap, (r.arrival + max(real, r.work_s) + adm.t0, r.rid, r))
+    while heap:
+        td, _, q = heapq.heappop(heap)
+        q.done = td
+        adm.finish(q, td)
+    assert adm.chain_scale == pytest.approx(1.6, rel=0.05)
+    late = [r for r in reqs[-500:] if r.chain_bound]
+    ratio = np.array([(r.done - r.arrival) / (r.predicted_done - r.arrival) for r in late])
+    assert np.median(ratio) == pytest.approx(1.0, abs=0.05)
+
+
 def test_drain_is_calibrated_from_a_burst():
     from paper_2407_09333_b300.serve import calibrate_drain
     model = _Model()
