@@ -51,6 +51,8 @@ from paper_2407_09333_b300 import shard  # noqa: E402
 # and the multi-GPU split (shard.OPS_PER_BLOCK: 324 / 613 / 1412 for MD5 /
 # SHA-1 / SM3, counted from the definitions).
 OPS_PER_BLOCK = {a: int(shard.OPS_PER_BLOCK[a]) for a in range(3)}
+# copy mapping of a launch shape (api.shapes()[i][3])
+COPY_MAPPING = {0: "per lane", 1: "cooperative"}
 
 
 def padded_blocks(lengths: np.ndarray) -> np.ndarray:
@@ -497,13 +499,14 @@ def measure(args, dist):
             w, st, kb, co = api.shapes()[args.shape]
             tuned["mixed" if a is None else ALG_NAMES[a]] = {"warps": w, "stages": st,
                                                               "blocks_per_stage": kb,
-                                                              "cooperative": bool(co), "fixed": True}
+                                                              "copies": COPY_MAPPING[co], "fixed": True}
             continue
         r = autotune.tune(a, packed, off, ln, rec if a == api.ALL else out, algs=algs,
                           mean_len=mean_len)
         tuned["mixed" if a is None else ALG_NAMES[a]] = {"warps": r["warps"], "stages": r["stages"],
                                                           "blocks_per_stage": r.get("blocks_per_stage", 1),
-                                                          "cooperative": r.get("cooperative", False),
+                                                          "copies": COPY_MAPPING[r.get("copy_mapping",
+                                                                                       int(r.get("cooperative", 0)))],
                                                           "cached": r["cached"]}
         if "buckets" in r:
             tuned["mixed"]["buckets_per_octave"] = 1 << r["buckets"][0]

@@ -156,7 +156,8 @@ def tune(alg, packed, offsets, lengths, out, algs=None, mean_len: float | None =
         ms = {str(k): v for k, v in timings.items()}
     api.tune_set(tune_alg, best)
     result.update({"shape": best, "warps": shapes[best][0], "stages": shapes[best][1],
-                   "blocks_per_stage": shapes[best][2], "cooperative": bool(shapes[best][3]),
+                   "blocks_per_stage": shapes[best][2], "cooperative": shapes[best][3] == 1,
+                   "copy_mapping": int(shapes[best][3]),
                    "ms": ms})
     if use_cache:
         cache = load_cache(path)
