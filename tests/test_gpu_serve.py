@@ -267,6 +267,36 @@ def test_served_from_host_memory_equals_oracle(env, oracle_mod):
         serve.Server(host_pool, budget=128 << 20, in_place=True)
 
 
+def test_served_under_admission_policy_equals_oracle(env, oracle_mod):
+    # the live server with the admission policy: a tight hold cap makes
+    # requests wait on the host, every admitted request gets a predicted
+    # completion time, and the digests are those of the oracle; a target of
+    # zero sheds every request at arrival and nothing reaches the device
+    api, serve, pool_host, pool_dev, pool_bytes = env
+    from paper_2407_09333_b300 import costmodel
+    model = costmodel.fit_chain(
+        costmodel.CostModel(np.array([1e-13, 1e-13, 1e-13]), 0.0, 1.0),
+        [(a, 1 << 16, 2e-3) for a in (0, 1, 2)])
+    reqs = serve.make_requests(90, 20000.0, seed=15, pool_bytes=pool_bytes, max_msgs=64,
+                               max_len=1 << 16, align=1)
+    srv = serve.Server(pool_dev, budget=128 << 20, rounds=2, segment_bytes=(12288, 8192, 4096),
+                       max_msgs=4096, capacity=1 << 14, req_capacity=256, in_place=True)
+    adm = serve.Admission(model, cap_s=1e-6, drain=0.9)
+    srv.run(reqs, keep_digests=True, admission=adm)
+    assert all(r.predicted_done >= r.admitted >= r.arrival for r in reqs)
+    assert any(r.admitted > r.arrival + 1e-4 for r in reqs)        # the cap held some back
+    _check_requests(api, oracle_mod, reqs, pool_host, oracle_every=1)
+    assert adm.inflight == 0
+    shed = serve.make_requests(30, 20000.0, seed=16, pool_bytes=pool_bytes, max_msgs=64,
+                               max_len=1 << 16)
+    segments = srv.segments
+    srv.run(shed, admission=serve.Admission(model, slo_s=0.0))
+    srv.close()
+    assert all(r.rejected and r.done < 0 for r in shed)
+    assert srv.segments == segments                                 # nothing was hashed
+    assert api.device_status() == 0
+
+
 def test_completion_flags_must_be_mapped_host_memory(env):
     api = env[0]
     plan = api.Plan(64)
