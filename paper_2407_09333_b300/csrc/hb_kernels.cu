@@ -125,25 +125,35 @@ __global__ void __launch_bounds__(kScanThreads) hb_scan_kernel(MixedArgs m) {
   }
 }
 
-__global__ void hb_scatter_kernel(MixedArgs m) {
-  const uint32_t lane = threadIdx.x & 31u;
+// Each block places a contiguous range of the messages: it counts its
+// messages per group in shared memory, reserves each group's places with one
+// global atomic (the group's cursor), and hands them out with shared-memory
+// atomics.  Any order within a group is as good as another; what matters is
+// that the global atomics are few (one per non-empty group per block, where
+// a warp-aggregated reservation still met about 31 distinct groups per warp).
+constexpr int kScatterThreads = 1024;
+
+__global__ void __launch_bounds__(kScatterThreads) hb_scatter_kernel(MixedArgs m) {
+  __shared__ uint32_t next[kGroups];
   const uint64_t n = batch_size(m);
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  const uint64_t n_up = (n + 31u) & ~31ull;
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_up; i += stride) {
-    uint32_t key = 0xFFFFFFFFu;
-    if (i < n) {
-      const uint32_t alg = m.algs[i];
-      if (alg <= HB_SM3) key = cost_group(m.lengths[i], alg, m.cfg);
-    }
-    // Warp-aggregated reservation: one atomic per distinct group in the warp.
-    const uint32_t peers = __match_any_sync(kFull, key);
-    const uint32_t leader = __ffs(peers) - 1u;
-    const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
-    uint32_t base = 0;
-    if (key != 0xFFFFFFFFu && lane == leader) base = atomicAdd(&m.ws->cursor[key], __popc(peers));
-    base = __shfl_sync(kFull, base, leader);
-    if (key != 0xFFFFFFFFu) m.perm[base + rank] = (uint32_t)i;
+  const uint64_t per = (n + gridDim.x - 1) / gridDim.x;
+  const uint64_t lo = (uint64_t)blockIdx.x * per;
+  const uint64_t hi = lo + per < n ? lo + per : n;
+  for (uint32_t g = threadIdx.x; g < kGroups; g += blockDim.x) next[g] = 0;
+  __syncthreads();
+  for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    const uint32_t alg = m.algs[i];
+    if (alg <= HB_SM3) atomicAdd(&next[cost_group(m.lengths[i], alg, m.cfg)], 1u);
+  }
+  __syncthreads();
+  for (uint32_t g = threadIdx.x; g < kGroups; g += blockDim.x) {
+    const uint32_t c = next[g];
+    if (c) next[g] = atomicAdd(&m.ws->cursor[g], c);
+  }
+  __syncthreads();
+  for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    const uint32_t alg = m.algs[i];
+    if (alg <= HB_SM3) m.perm[atomicAdd(&next[cost_group(m.lengths[i], alg, m.cfg)], 1u)] = (uint32_t)i;
   }
 }
 
@@ -481,7 +491,10 @@ cudaError_t launch_bucketing(const MixedArgs& m, int grid, cudaStream_t stream) 
   if (e != cudaSuccess) return e;
   hb_hist_kernel<<<grid, 256, 0, stream>>>(m);
   hb_scan_kernel<<<1, kScanThreads, 0, stream>>>(m);
-  hb_scatter_kernel<<<grid, 256, 0, stream>>>(m);
+  // `grid` is at most 8 blocks of 256 threads per SM: the scatter takes an
+  // eighth of it in 1024-thread blocks (at most one per SM), since the fewer
+  // blocks, the fewer global reservations
+  hb_scatter_kernel<<<(grid + 7) / 8, kScatterThreads, 0, stream>>>(m);
   return cudaGetLastError();
 }
 
