@@ -510,7 +510,7 @@ def measure(args, dist):
                                                           "cached": r["cached"]}
         if "buckets" in r:
             tuned["mixed"]["buckets_per_octave"] = 1 << r["buckets"][0]
-            tuned["mixed"]["algorithm_major"] = bool(r["buckets"][1])
+            tuned["mixed"]["algorithm_major"] = int(r["buckets"][1])
         if "warps_per_sm" in r:
             tuned["mixed"]["warps_per_sm"] = r["warps_per_sm"] or "occupancy"
         if a is None and "ms" in r:

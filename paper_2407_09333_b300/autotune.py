@@ -125,7 +125,7 @@ def tune(alg, packed, offsets, lengths, out, algs=None, mean_len: float | None =
         api.tune_mixed_warps(8)
         btimes = {}
         for sub in (2, 3, 4):
-            for major in (0, 1):
+            for major in (0, 1, 2):
                 api.tune_buckets(sub, major)
                 btimes[(sub, major)] = _time_ms(torch, run(api.tune_get(api.TUNE_MIXED)), reps)
         bbest = min(btimes, key=btimes.get)

@@ -195,6 +195,7 @@ int launch_mixed(Ctx* c, int shape, int grid, const uint8_t* algs, const uint8_t
   a.perm = m.perm;
   a.chunk_counter = &m.ws->chunk_counter;
   a.nchunks = &m.ws->nchunks;
+  a.early = m.ws->early;
   a.n = n;
   a.digests = digests;
   a.status = c->status;
@@ -844,7 +845,7 @@ int hash_tune_mixed_warps(int warps_per_sm) {
 }
 
 int hash_tune_buckets(int sub_log2, int alg_major) {
-  if (sub_log2 < 0 || sub_log2 > (int)hb::kMaxSubLog2 || (alg_major != 0 && alg_major != 1))
+  if (sub_log2 < 0 || sub_log2 > (int)hb::kMaxSubLog2 || alg_major < 0 || alg_major > 2)
     return HB_ERR_ARG;
   Ctx* c = nullptr;
   int rc = get_ctx(&c);

@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(WARPS * 32) hb_mixed_kernel(KernelArgs a) {
   const uint32_t warp = threadIdx.x >> 5;
   if (a.abort_flag && *a.abort_flag) return;
   uint8_t* wsm = smem + warp * WarpSmem<STAGES, KB, SEG>::kBytes;
-  DynamicSource<SEG> src(a, lane);
+  DynamicSource<SEG> src(a, lane, (uint64_t)blockIdx.x * WARPS + warp);
   warp_pipeline<STAGES, KB, COOP, HB_MD5, true, SEG>(src, wsm, a, lane);
 }
 

@@ -89,6 +89,8 @@ static_assert(kGroups % kScanThreads == 0, "scan covers every group");
 
 __global__ void __launch_bounds__(kScanThreads) hb_scan_kernel(MixedArgs m) {
   __shared__ uint32_t warp_sums[kScanThreads / 32];
+  __shared__ uint32_t gstart[kGroups + 1];
+  __shared__ uint32_t md5_top;  // first non-empty MD5 group (alg_major 2)
   const uint32_t t = threadIdx.x, lane = t & 31u, warp = t >> 5;
   uint32_t cnt[kScanPer], pad[kScanPer], own = 0;
 #pragma unroll
@@ -112,16 +114,33 @@ __global__ void __launch_bounds__(kScanThreads) hb_scan_kernel(MixedArgs m) {
     total += v;
   }
   uint32_t start = before + incl - own;
+  if (t == 0) md5_top = kGroups;
+  __syncthreads();
 #pragma unroll
   for (uint32_t k = 0; k < kScanPer; ++k) {
     const uint32_t g = t * kScanPer + k;
     m.ws->cursor[g] = start;
+    gstart[g] = start;
     for (uint32_t e = start + cnt[k]; e < start + pad[k]; ++e) m.perm[e] = 0xFFFFFFFFu;
+    if (cnt[k] && g >= 2 * kCostBuckets) atomicMin(&md5_top, g);  // MD5 groups, rank 2
     start += pad[k];
   }
+  if (t == 0) gstart[kGroups] = total;
+  __syncthreads();
   if (t == 0) {
     m.ws->nchunks = total / 32u;
     m.ws->chunk_counter = 0u;
+    uint32_t first = 0, count = 0;
+    if (m.cfg.alg_major == 2 && md5_top < kGroups) {
+      // one octave of MD5 cost buckets from its longest non-empty one
+      const uint32_t end = md5_top + (1u << m.cfg.sub_log2) < kGroups ? md5_top + (1u << m.cfg.sub_log2)
+                                                                     : kGroups;
+      first = gstart[md5_top] / 32u;
+      count = (gstart[end] - gstart[md5_top]) / 32u;
+    }
+    m.ws->early[0] = first;
+    m.ws->early[1] = count;
+    m.ws->early[2] = 0u;
   }
 }
 

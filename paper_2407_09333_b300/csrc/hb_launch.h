@@ -34,6 +34,7 @@ struct KernelArgs {
   const uint32_t* perm;       // mixed path only: chunk slot -> message index
   uint32_t* chunk_counter;    // mixed path only
   const uint32_t* nchunks;    // mixed path only
+  uint32_t* early;            // mixed path only: MixedWorkspace::early
   uint64_t n;
   uint8_t* digests;
   int* status;                // per-device status word (HB_DEV_* bits)
@@ -69,7 +70,8 @@ constexpr uint32_t kGroups = kCostBuckets * 3;
 
 struct BucketCfg {
   uint32_t sub_log2;   // 0..kMaxSubLog2
-  uint32_t alg_major;  // 0 or 1
+  uint32_t alg_major;  // 0 interleaved, 1 algorithm-major, 2 algorithm-major with MD5's
+                       // longest octave served early (MixedWorkspace::early)
 };
 
 constexpr BucketCfg kDefaultBuckets = {3u, 1u};
@@ -91,7 +93,12 @@ struct MixedWorkspace {
   uint32_t cursor[kGroups];
   uint32_t chunk_counter;
   uint32_t nchunks;
-  uint32_t pad[30];
+  // alg_major == 2: chunks [early[0], early[0] + early[1]) -- MD5's longest
+  // octave -- form a second queue (pop counter early[2]) that every other
+  // warp serves first, so those chains start with the SM3 phase instead of
+  // after every SM3 and SHA-1 chunk (where they would end the launch late)
+  uint32_t early[3];
+  uint32_t pad[27];
 };
 
 inline size_t mixed_workspace_bytes(uint64_t n) {

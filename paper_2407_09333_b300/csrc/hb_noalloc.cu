@@ -145,6 +145,7 @@ extern "C" int hash_batch_mixed_noalloc(const uint8_t* algs, const uint8_t* pack
   a.perm = perm;
   a.chunk_counter = &ws->chunk_counter;
   a.nchunks = &ws->nchunks;
+  a.early = ws->early;
   a.n = n;
   a.digests = digests_out;
   a.status = status;

@@ -201,7 +201,10 @@ struct DynamicSource {
   const uint32_t* slot_index;
   int* status;
   uint32_t* counter;
+  uint32_t* early_counter;
   uint32_t lane, nchunks;
+  uint32_t early_first, early_count;  // the early queue (bucketing mode 2)
+  bool early_ok;     // this warp serves the early queue first (lane 0's view)
   int stage;         // 0 nothing reserved, 1 popped, 2 perm loaded, 3 metadata loaded
   uint32_t chunk;    // reserved chunk id (stage >= 1)
   uint32_t msg;      // this lane's message in it (stage >= 2)
@@ -210,7 +213,9 @@ struct DynamicSource {
   uint64_t seg;      // stage 3, segments only
   uint32_t slot;     // stage 3, segments only
 
-  __device__ DynamicSource(const KernelArgs& args, uint32_t lane_)
+  // gwarp: the warp's index in the grid; odd warps serve the early queue
+  // first (the even ones start the main queue's longest work beside them).
+  __device__ DynamicSource(const KernelArgs& args, uint32_t lane_, uint64_t gwarp)
       : packed(args.packed),
         offsets(args.offsets),
         lengths(args.lengths),
@@ -220,16 +225,33 @@ struct DynamicSource {
         slot_index(args.slot_index),
         status(args.status),
         counter(args.chunk_counter),
+        early_counter(args.early + 2),
         lane(lane_),
         stage(0) {
     nchunks = *args.nchunks;
+    early_first = args.early[0];
+    early_count = args.early[1];
+    early_ok = early_count != 0 && (gwarp & 1u);
   }
 
   // One more step towards having the next chunk ready (warp-uniform).
   __device__ __forceinline__ void advance() {
     if (stage == 0) {
       uint32_t c = 0;
-      if (lane == 0) c = atomicAdd(counter, 1u);
+      if (lane == 0) {
+        bool got = false;
+        if (early_ok) {
+          const uint32_t e = atomicAdd(early_counter, 1u);
+          got = e < early_count;
+          if (got) c = early_first + e;
+          else early_ok = false;  // the early queue is empty: main queue from now on
+        }
+        if (!got) {
+          // the main queue holds every chunk outside the early range
+          const uint32_t v = atomicAdd(counter, 1u);
+          c = v < early_first ? v : v + early_count;
+        }
+      }
       chunk = __shfl_sync(kFull, c, 0);
       stage = 1;
     } else if (stage == 1) {

@@ -366,6 +366,7 @@ int hash_round_create(const hb_ring* ring, uint32_t max_msgs, uint8_t* staging,
   k.perm = m.perm;
   k.chunk_counter = &m.ws->chunk_counter;
   k.nchunks = &m.ws->nchunks;
+  k.early = m.ws->early;
   k.n = max_msgs;
   k.digests = ring->slots;
   k.status = status;

@@ -138,6 +138,29 @@ def test_mixed_all_shapes_and_invalid_codes(hb, oracle_mod):
         _assert_slots_equal(_gpu_slots(hb, b, None, shape=shape, mixed=True), want, "shape %d" % shape)
 
 
+@pytest.mark.parametrize("sub_log2,alg_major", [(0, 0), (2, 1), (3, 2), (4, 2), (4, 0)])
+def test_mixed_every_bucketing_matches_oracle(hb, oracle_mod, sub_log2, alg_major):
+    # bucket resolution and chunk order (including MD5's longest octave served
+    # early from its own queue) change the schedule, never a digest
+    lens = np.exp(np.random.default_rng(19).uniform(0, np.log(40000), size=6000)).astype(np.int64)
+    b = workloads.scattered(lens, seed=19, overlap=True, mixed=True)
+    want = _oracle_slots(oracle_mod, b, None)
+    hb.tune_buckets(sub_log2, alg_major)
+    try:
+        _assert_slots_equal(_gpu_slots(hb, b, None, mixed=True), want,
+                            "buckets %d,%d" % (sub_log2, alg_major))
+        plan = hb.Plan(b.n)
+        packed, off, ln, algs = hb.to_device(b)
+        out = torch.zeros((b.n, 32), dtype=torch.uint8, device="cuda")
+        plan.capture(algs, packed, off, ln, out)
+        plan.replay(b.n)
+        torch.cuda.synchronize()
+        _assert_slots_equal(out.cpu().numpy(), want, "replayed %d,%d" % (sub_log2, alg_major))
+        plan.close()
+    finally:
+        hb.tune_buckets(3, 1)
+
+
 def test_mixed_matches_single_algorithm_path(hb):
     b = workloads.ragged(5000, seed=8, max_len=4096)
     mixed = _gpu_slots(hb, b, None, mixed=True)
