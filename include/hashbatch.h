@@ -463,11 +463,11 @@ int hash_tune_occupancy(int alg, int shape_index);
  * 4; finer buckets give chunks of more equal length), and with alg_major = 1
  * the chunk order runs through all SM3 messages, then SHA-1, then MD5, each
  * longest first, instead of interleaving the algorithms.  alg_major = 2 is
- * that order with MD5's longest octave of messages taken out into a second
+ * that order with MD5's two longest octaves of messages taken out into a second
  * queue that every other warp serves first, so those chains run beside the
  * SM3 phase instead of starting after it and the SHA-1 phase (0 <= alg_major
  * <= 2).  Digests do not depend on any of these choices.  Defaults:
- * sub_log2 = 3, alg_major = 1.
+ * sub_log2 = 4, alg_major = 2.
  */
 int hash_tune_buckets(int sub_log2, int alg_major);
 

@@ -547,7 +547,7 @@ def tune_get(alg: int) -> int:
 def tune_buckets(sub_log2: int, alg_major: int):
     """Ragged-path bucketing (hash_tune_buckets): 2^sub_log2 cost buckets per
     octave; alg_major 0 interleaved, 1 algorithm-major, 2 algorithm-major with
-    MD5's longest octave served early."""
+    MD5's two longest octaves served early."""
     _check(lib().hash_tune_buckets(int(sub_log2), int(alg_major)), "hash_tune_buckets")
 
 

@@ -132,9 +132,9 @@ __global__ void __launch_bounds__(kScanThreads) hb_scan_kernel(MixedArgs m) {
     m.ws->chunk_counter = 0u;
     uint32_t first = 0, count = 0;
     if (m.cfg.alg_major == 2 && md5_top < kGroups) {
-      // one octave of MD5 cost buckets from its longest non-empty one
-      const uint32_t end = md5_top + (1u << m.cfg.sub_log2) < kGroups ? md5_top + (1u << m.cfg.sub_log2)
-                                                                     : kGroups;
+      // two octaves of MD5 cost buckets from its longest non-empty one
+      const uint32_t span = 2u << m.cfg.sub_log2;
+      const uint32_t end = md5_top + span < kGroups ? md5_top + span : kGroups;
       first = gstart[md5_top] / 32u;
       count = (gstart[end] - gstart[md5_top]) / 32u;
     }

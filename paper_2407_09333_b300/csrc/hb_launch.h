@@ -71,19 +71,18 @@ constexpr uint32_t kGroups = kCostBuckets * 3;
 struct BucketCfg {
   uint32_t sub_log2;   // 0..kMaxSubLog2
   uint32_t alg_major;  // 0 interleaved, 1 algorithm-major, 2 algorithm-major with MD5's
-                       // longest octave served early (MixedWorkspace::early)
+                       // two longest octaves served early (MixedWorkspace::early)
 };
 
-constexpr BucketCfg kDefaultBuckets = {3u, 1u};
+constexpr BucketCfg kDefaultBuckets = {4u, 2u};
 
-// Default launch of the persistent ragged kernel: shape 10 (4 warps, 3 stages
-// of 4 blocks, cooperative copies) with 8 resident warps per SM, i.e. two per
-// SM sub-partition.  A
-// long message is a serial chain of blocks; with more co-resident warps its
-// warp gets a smaller share of the sub-partition's issue slots and the
-// longest chains finish last (MD5 saturates a sub-partition at about four
-// warps, SHA-1 and SM3 at two).
-constexpr int kDefaultMixedShape = 10;
+// Default launch of the persistent ragged kernel: shape 19 (1-warp blocks, 2
+// stages of 4 blocks, cooperative copies) with 8 resident warps per SM, i.e.
+// two per SM sub-partition.  A long message is a serial chain of blocks; with
+// more co-resident warps its warp gets a smaller share of the sub-partition's
+// issue slots and the longest chains finish last (MD5 saturates a
+// sub-partition at about four warps, SHA-1 and SM3 at two).
+constexpr int kDefaultMixedShape = 19;
 constexpr int kDefaultMixedWarpsPerSm = 8;
 
 // Device scratch of the ragged path; followed in memory by the permutation
@@ -93,8 +92,8 @@ struct MixedWorkspace {
   uint32_t cursor[kGroups];
   uint32_t chunk_counter;
   uint32_t nchunks;
-  // alg_major == 2: chunks [early[0], early[0] + early[1]) -- MD5's longest
-  // octave -- form a second queue (pop counter early[2]) that every other
+  // alg_major == 2: chunks [early[0], early[0] + early[1]) -- MD5's two
+  // longest octaves -- form a second queue (pop counter early[2]) that every other
   // warp serves first, so those chains start with the SM3 phase instead of
   // after every SM3 and SHA-1 chunk (where they would end the launch late)
   uint32_t early[3];

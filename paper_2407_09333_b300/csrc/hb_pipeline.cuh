@@ -205,6 +205,8 @@ struct DynamicSource {
   uint32_t lane, nchunks;
   uint32_t early_first, early_count;  // the early queue (bucketing mode 2)
   bool early_ok;     // this warp serves the early queue first (lane 0's view)
+  bool main_ok;      // the main queue may still hold work (lane 0's view)
+  bool early_left;   // the early queue may still hold work (lane 0's view)
   int stage;         // 0 nothing reserved, 1 popped, 2 perm loaded, 3 metadata loaded
   uint32_t chunk;    // reserved chunk id (stage >= 1)
   uint32_t msg;      // this lane's message in it (stage >= 2)
@@ -232,6 +234,8 @@ struct DynamicSource {
     early_first = args.early[0];
     early_count = args.early[1];
     early_ok = early_count != 0 && (gwarp & 1u);
+    main_ok = true;
+    early_left = true;
   }
 
   // One more step towards having the next chunk ready (warp-uniform).
@@ -239,6 +243,9 @@ struct DynamicSource {
     if (stage == 0) {
       uint32_t c = 0;
       if (lane == 0) {
+        // odd warps serve the early queue first, even warps the main queue;
+        // each turns to the other queue once its own is empty, so no warp
+        // stops while either queue holds work
         bool got = false;
         if (early_ok) {
           const uint32_t e = atomicAdd(early_counter, 1u);
@@ -246,11 +253,20 @@ struct DynamicSource {
           if (got) c = early_first + e;
           else early_ok = false;  // the early queue is empty: main queue from now on
         }
-        if (!got) {
+        if (!got && main_ok) {
           // the main queue holds every chunk outside the early range
           const uint32_t v = atomicAdd(counter, 1u);
           c = v < early_first ? v : v + early_count;
+          got = c < nchunks;
+          if (!got) main_ok = false;
         }
+        if (!got && early_count != 0 && early_left) {
+          const uint32_t e = atomicAdd(early_counter, 1u);
+          got = e < early_count;
+          if (got) c = early_first + e;
+          else early_left = false;
+        }
+        if (!got) c = nchunks;  // both queues empty
       }
       chunk = __shfl_sync(kFull, c, 0);
       stage = 1;

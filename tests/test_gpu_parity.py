@@ -158,7 +158,7 @@ def test_mixed_every_bucketing_matches_oracle(hb, oracle_mod, sub_log2, alg_majo
         _assert_slots_equal(out.cpu().numpy(), want, "replayed %d,%d" % (sub_log2, alg_major))
         plan.close()
     finally:
-        hb.tune_buckets(3, 1)
+        hb.tune_buckets(4, 2)
 
 
 def test_mixed_matches_single_algorithm_path(hb):
@@ -561,8 +561,8 @@ def test_full_size_ragged_graph_replay_matches_oracle(hb, c3, tmp_path):
         assert hb.device_status() == 0
     finally:
         plan.close()
-        hb.tune_set(hb.TUNE_MIXED, 10)
-        hb.tune_buckets(3, 1)
+        hb.tune_set(hb.TUNE_MIXED, 19)
+        hb.tune_buckets(4, 2)
         hb.tune_mixed_warps(8)
 
 
