@@ -305,18 +305,40 @@ struct DynamicSource {
       return false;
     }
     const bool valid = msg != 0xFFFFFFFFu;
-    t.msg = msg;
-    t.addr = reinterpret_cast<uint64_t>(packed) + off;
-    t.len = len;
-    t.seg = seg;
-    t.slot = slot;
-    if constexpr (SEG)
-      t.nb = valid ? segment_blocks(len, seg, status) : 0u;
-    else
-      t.nb = valid ? padded_blocks(len) : 0u;
     // Codes outside {0,1,2} were excluded by the bucketing step; the chunk's
     // algorithm is that of lane 0 (every chunk starts with a real message).
     t.alg = __shfl_sync(kFull, alg, 0);
+    // Lane order: a lane reads its window at word (addr / 4) % 4 of its
+    // first 16-byte granule, and the slots of eight consecutive lanes start
+    // in eight different groups of four banks.  Lanes whose messages share
+    // that word offset are therefore put next to each other (messages in
+    // order of the offset, idle lanes last): up to eight of them read
+    // distinct banks, so a warp's shared loads take ceil(largest class / 8)
+    // wavefronts instead of colliding wherever two lanes eight apart share
+    // the offset.
+    const uint64_t addr = reinterpret_cast<uint64_t>(packed) + off;
+    const uint32_t cls = valid ? (uint32_t)(addr >> 2) & 3u : 4u;
+    const uint32_t b0 = __ballot_sync(kFull, cls == 0u), b1 = __ballot_sync(kFull, cls == 1u);
+    const uint32_t b2 = __ballot_sync(kFull, cls == 2u), b3 = __ballot_sync(kFull, cls == 3u);
+    const uint32_t s1 = __popc(b0), s2 = s1 + __popc(b1), s3 = s2 + __popc(b2);
+    const uint32_t s4 = s3 + __popc(b3);
+    // this lane takes the message of the k-th lane (in lane order) of its class
+    const uint32_t c = (lane >= s1) + (lane >= s2) + (lane >= s3) + (lane >= s4);
+    const uint32_t mask = c == 0 ? b0 : c == 1 ? b1 : c == 2 ? b2 : c == 3 ? b3 : ~(b0 | b1 | b2 | b3);
+    const uint32_t start = c == 0 ? 0u : c == 1 ? s1 : c == 2 ? s2 : c == 3 ? s3 : s4;
+    const uint32_t from = __fns(mask, 0u, (int)(lane - start) + 1);
+    const uint32_t nb = valid ? (SEG ? segment_blocks(len, seg, status) : padded_blocks(len)) : 0u;
+    t.msg = __shfl_sync(kFull, (uint64_t)msg, from);
+    t.addr = __shfl_sync(kFull, addr, from);
+    t.len = __shfl_sync(kFull, len, from);
+    t.nb = __shfl_sync(kFull, nb, from);
+    if constexpr (SEG) {
+      t.seg = __shfl_sync(kFull, seg, from);
+      t.slot = __shfl_sync(kFull, slot, from);
+    } else {
+      t.seg = 0;
+      t.slot = 0;
+    }
     return true;
   }
 };
