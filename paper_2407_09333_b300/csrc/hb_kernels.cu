@@ -79,10 +79,15 @@ __global__ void hb_hist_kernel(MixedArgs m) {
 }
 
 // One block of kScanThreads threads, kScanPer consecutive groups each.
-// Groups are laid out in group order, each padded to a multiple of 32 so
-// that every chunk holds a single algorithm and starts with a real message:
-// an exclusive prefix sum of the padded counts (per thread, then across the
-// block's warps) gives each group's first permutation entry.
+// Every chunk of 32 permutation entries must hold a single algorithm and start
+// with a real message.  In algorithm-major order (alg_major 1, 2) each
+// algorithm's groups are adjacent, so they are laid out back to back and
+// only each algorithm's end is padded to a multiple of 32: a chunk may hold
+// the cheapest messages of one cost bucket and the costliest of the next,
+// instead of a group's last chunk running part-empty.  With the algorithms
+// interleaved (alg_major 0) every group is padded.  An exclusive prefix sum
+// of the (padded) counts, per thread and then across the block's warps,
+// gives each group's first permutation entry.
 constexpr uint32_t kScanThreads = 512;
 constexpr uint32_t kScanPer = kGroups / kScanThreads;
 static_assert(kGroups % kScanThreads == 0, "scan covers every group");
@@ -92,11 +97,12 @@ __global__ void __launch_bounds__(kScanThreads) hb_scan_kernel(MixedArgs m) {
   __shared__ uint32_t gstart[kGroups + 1];
   __shared__ uint32_t md5_top;  // first non-empty MD5 group (alg_major 2)
   const uint32_t t = threadIdx.x, lane = t & 31u, warp = t >> 5;
+  const bool per_alg = m.cfg.alg_major != 0;
   uint32_t cnt[kScanPer], pad[kScanPer], own = 0;
 #pragma unroll
   for (uint32_t k = 0; k < kScanPer; ++k) {
     cnt[k] = m.ws->counts[t * kScanPer + k];
-    pad[k] = (cnt[k] + 31u) & ~31u;
+    pad[k] = per_alg ? cnt[k] : (cnt[k] + 31u) & ~31u;
     own += pad[k];
   }
   uint32_t incl = own;  // inclusive scan within the warp
@@ -114,29 +120,56 @@ __global__ void __launch_bounds__(kScanThreads) hb_scan_kernel(MixedArgs m) {
     total += v;
   }
   uint32_t start = before + incl - own;
+#pragma unroll
+  for (uint32_t k = 0; k < kScanPer; ++k) {
+    gstart[t * kScanPer + k] = start;
+    start += pad[k];
+  }
   if (t == 0) md5_top = kGroups;
   __syncthreads();
+  // Algorithm-major: algorithm rank r (groups [r, r + 1) * kCostBuckets)
+  // moves up by the padding of the ranks before it.
+  uint32_t all[3] = {0u, 0u, 0u}, shift[3] = {0u, 0u, 0u}, padded_total = total;
+  if (per_alg) {
+    const uint32_t e1 = gstart[kCostBuckets], e2 = gstart[2 * kCostBuckets];
+    all[0] = e1;
+    all[1] = e2 - e1;
+    all[2] = total - e2;
+    shift[1] = ((all[0] + 31u) & ~31u) - all[0];
+    shift[2] = shift[1] + ((all[1] + 31u) & ~31u) - all[1];
+    padded_total = total + shift[2] + ((all[2] + 31u) & ~31u) - all[2];
+  }
+  __syncthreads();  // every raw start has been read
 #pragma unroll
   for (uint32_t k = 0; k < kScanPer; ++k) {
     const uint32_t g = t * kScanPer + k;
-    m.ws->cursor[g] = start;
-    gstart[g] = start;
-    for (uint32_t e = start + cnt[k]; e < start + pad[k]; ++e) m.perm[e] = 0xFFFFFFFFu;
+    const uint32_t sg = gstart[g] + (per_alg ? shift[g / kCostBuckets] : 0u);
+    m.ws->cursor[g] = sg;
+    gstart[g] = sg;
+    if (!per_alg)
+      for (uint32_t e = sg + cnt[k]; e < sg + pad[k]; ++e) m.perm[e] = 0xFFFFFFFFu;
     if (cnt[k] && g >= 2 * kCostBuckets) atomicMin(&md5_top, g);  // MD5 groups, rank 2
-    start += pad[k];
   }
-  if (t == 0) gstart[kGroups] = total;
+  if (per_alg && t < 3) {
+    // the padding after algorithm rank t
+    const uint32_t first = t == 0 ? 0u : (t == 1 ? all[0] + shift[1] : all[0] + all[1] + shift[2]);
+    for (uint32_t e = first + all[t]; e < first + ((all[t] + 31u) & ~31u); ++e)
+      m.perm[e] = 0xFFFFFFFFu;
+  }
+  if (t == 0) gstart[kGroups] = padded_total;
   __syncthreads();
   if (t == 0) {
-    m.ws->nchunks = total / 32u;
+    m.ws->nchunks = padded_total / 32u;
     m.ws->chunk_counter = 0u;
     uint32_t first = 0, count = 0;
     if (m.cfg.alg_major == 2 && md5_top < kGroups) {
-      // two octaves of MD5 cost buckets from its longest non-empty one
+      // the chunks holding two octaves of MD5 cost buckets from its longest
+      // non-empty one (MD5's first chunk starts there: the groups before it
+      // are empty)
       const uint32_t span = 2u << m.cfg.sub_log2;
       const uint32_t end = md5_top + span < kGroups ? md5_top + span : kGroups;
       first = gstart[md5_top] / 32u;
-      count = (gstart[end] - gstart[md5_top]) / 32u;
+      count = (gstart[end] + 31u) / 32u - first;
     }
     m.ws->early[0] = first;
     m.ws->early[1] = count;
