@@ -70,19 +70,29 @@ def _time_ms(torch, fn, reps: int) -> float:
     return best
 
 
-def _final_round(torch, timings: dict, make, reps: int, finalists: int = 3):
+def _final_round(torch, timings: dict, make, reps: int, finalists: int = 3, keep=None,
+                 margin: float = 0.01):
     """The best of the first pass's `finalists` fastest candidates, timed
     again in turns (so that a drift of the clock hits all of them alike),
     by the median of several launches: one lucky launch in the first pass
-    does not decide."""
+    does not decide.  `keep` (the setting in force, when it was timed) always
+    takes part and stays unless another candidate's median is more than
+    `margin` below its own: candidates within a launch's noise of each other
+    do not displace a setting chosen on longer measurements."""
     cands = sorted(timings, key=timings.get)[:finalists]
+    if keep is not None and keep in timings and keep not in cands:
+        cands.append(keep)
     if len(cands) == 1:
         return cands[0]
     samples = {k: [] for k in cands}
     for _ in range(max(5, 2 * reps)):
         for k in cands:
             samples[k].append(_time_ms(torch, make(k), 1))
-    return min(cands, key=lambda k: sorted(samples[k])[len(samples[k]) // 2])
+    med = {k: sorted(samples[k])[len(samples[k]) // 2] for k in cands}
+    best = min(cands, key=med.get)
+    if keep in med and med[best] > med[keep] * (1.0 - margin):
+        return keep
+    return best
 
 
 def tune(alg, packed, offsets, lengths, out, algs=None, mean_len: float | None = None,
@@ -119,16 +129,22 @@ def tune(alg, packed, offsets, lengths, out, algs=None, mean_len: float | None =
         return lambda: api.hash_batch(alg, packed, offsets, lengths, out=out, shape=idx)
 
     result = {"key": key}
+    keep_shape = api.tune_get(tune_alg)  # the shape in force (the library's default at first)
     if alg is None:
         # Ragged path: bucket resolution and ordering first (default shape),
         # then the launch shape with the chosen bucketing.
-        api.tune_mixed_warps(8)
+        api.tune_mixed_warps(api.DEFAULT_MIXED_WARPS)
         btimes = {}
-        for sub in (2, 3, 4):
+        for sub in (3, 4, 5):
             for major in (0, 1, 2):
                 api.tune_buckets(sub, major)
-                btimes[(sub, major)] = _time_ms(torch, run(api.tune_get(api.TUNE_MIXED)), reps)
-        bbest = min(btimes, key=btimes.get)
+                btimes[(sub, major)] = _time_ms(torch, run(keep_shape), reps)
+
+        def with_buckets(k):
+            api.tune_buckets(*k)
+            return run(keep_shape)
+
+        bbest = _final_round(torch, btimes, with_buckets, reps, keep=api.DEFAULT_BUCKETS)
         api.tune_buckets(*bbest)
         result["buckets"] = list(bbest)
         result["bucket_ms"] = {"%d,%d" % k: v for k, v in btimes.items()}
@@ -145,14 +161,15 @@ def tune(alg, packed, offsets, lengths, out, algs=None, mean_len: float | None =
             api.tune_mixed_warps(k[1])
             return run(k[0])
 
-        (best, best_wps) = _final_round(torch, timings, with_warps, reps)
+        (best, best_wps) = _final_round(torch, timings, with_warps, reps,
+                                        keep=(keep_shape, api.DEFAULT_MIXED_WARPS))
         api.tune_mixed_warps(best_wps)
         result["warps_per_sm"] = best_wps
         ms = {"%d,%d" % k: v for k, v in timings.items()}
     else:
         for idx in range(len(shapes)):
             timings[idx] = _time_ms(torch, run(idx), reps)
-        best = _final_round(torch, timings, run, reps)
+        best = _final_round(torch, timings, run, reps, keep=keep_shape)
         ms = {str(k): v for k, v in timings.items()}
     api.tune_set(tune_alg, best)
     result.update({"shape": best, "warps": shapes[best][0], "stages": shapes[best][1],
