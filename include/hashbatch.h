@@ -177,7 +177,7 @@ int hash_batch_segments(const uint8_t *algs, const uint8_t *packed_bytes,
  * device memory belongs to another owner under a fixed budget, or a
  * latency-critical loop that must not meet the device-wide synchronisation
  * an allocation can cause.  This variant allocates nothing: its bucketing
- * scratch is a fixed array of about 4.60 MB compiled into the library, held
+ * scratch is a fixed array of about 5.01 MB compiled into the library, held
  * by every GPU that loads the library until the process exits.
  *   - n must be at most HB_NOALLOC_MAX_MESSAGES; larger batches return
  *     HB_ERR_TOO_LARGE without touching the GPU.  n == 0 is a no-op.
@@ -460,14 +460,14 @@ int hash_tune_occupancy(int alg, int shape_index);
  * hash_tune_buckets -- bucketing of the ragged path on the current device:
  * each octave of estimated per-message cost (padded blocks x relative cost of
  * the algorithm's block) is split into 2^sub_log2 buckets (0 <= sub_log2 <=
- * 5; finer buckets give chunks of more equal length), and with alg_major = 1
+ * 6; finer buckets give chunks of more equal length), and with alg_major = 1
  * the chunk order runs through all SM3 messages, then SHA-1, then MD5, each
  * longest first, instead of interleaving the algorithms.  alg_major = 2 is
  * that order with MD5's two longest octaves of messages taken out into a second
  * queue that every other warp serves first, so those chains run beside the
  * SM3 phase instead of starting after it and the SHA-1 phase (0 <= alg_major
  * <= 2).  Digests do not depend on any of these choices.  Defaults:
- * sub_log2 = 5, alg_major = 2.
+ * sub_log2 = 6, alg_major = 2.
  */
 int hash_tune_buckets(int sub_log2, int alg_major);
 

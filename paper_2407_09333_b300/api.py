@@ -19,7 +19,7 @@ ALL = 4                 # all three algorithms per message (hash_batch_all)
 # The library's defaults for the ragged path (hash_tune_buckets,
 # hash_tune_mixed_warps), which the autotuner keeps unless a candidate is
 # clearly faster.
-DEFAULT_BUCKETS = (5, 2)
+DEFAULT_BUCKETS = (6, 2)
 DEFAULT_MIXED_WARPS = 8
 ALL_RECORD_BYTES = 96
 ALL_DIGEST_BYTES = 68

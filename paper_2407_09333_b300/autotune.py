@@ -135,7 +135,7 @@ def tune(alg, packed, offsets, lengths, out, algs=None, mean_len: float | None =
         # then the launch shape with the chosen bucketing.
         api.tune_mixed_warps(api.DEFAULT_MIXED_WARPS)
         btimes = {}
-        for sub in (3, 4, 5):
+        for sub in (4, 5, 6):
             for major in (0, 1, 2):
                 api.tune_buckets(sub, major)
                 btimes[(sub, major)] = _time_ms(torch, run(keep_shape), reps)

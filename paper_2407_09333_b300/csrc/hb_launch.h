@@ -58,13 +58,13 @@ struct KernelArgs {
 // Ragged-path bucketing: groups are (cost bucket, algorithm) pairs ordered
 // from the most to the least expensive estimated work per message.  Cost
 // buckets split each octave of estimated cost into 2^sub_log2 parts
-// (sub_log2 <= 5, so at most 32 * 32 buckets): the finer the buckets, the
+// (sub_log2 <= 6, so at most 32 * 64 buckets): the finer the buckets, the
 // closer the lengths of a chunk's 32 messages, and the fewer lanes idle
 // while the chunk's longest message finishes.  With alg_major the order is
 // all SM3 groups, then SHA-1, then MD5 (each longest first), so that warps
 // running at the same time mostly run the same algorithm; otherwise the
 // algorithms interleave bucket by bucket (strict longest-first).
-constexpr uint32_t kMaxSubLog2 = 5;
+constexpr uint32_t kMaxSubLog2 = 6;
 constexpr uint32_t kCostBuckets = 32u << kMaxSubLog2;
 constexpr uint32_t kGroups = kCostBuckets * 3;
 
@@ -74,7 +74,7 @@ struct BucketCfg {
                        // two longest octaves served early (MixedWorkspace::early)
 };
 
-constexpr BucketCfg kDefaultBuckets = {5u, 2u};
+constexpr BucketCfg kDefaultBuckets = {6u, 2u};
 
 // Default launch of the persistent ragged kernel: shape 19 (1-warp blocks, 2
 // stages of 4 blocks, cooperative copies) with 8 resident warps per SM, i.e.

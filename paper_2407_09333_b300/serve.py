@@ -285,7 +285,7 @@ def prediction_stats(requests: list) -> dict:
 
 def device_bytes(capacity: int, req_capacity: int, rounds: int, max_msgs: int) -> int:
     """Device memory of everything but the staging areas."""
-    groups = 3 * 32 * 32                        # (cost bucket, algorithm) groups
+    groups = 3 * 32 * 64                        # (cost bucket, algorithm) groups
     ws = 4 * (2 * groups + 32) + 4 * (max_msgs + 31 * groups)
     return capacity * RING_ENTRY_BYTES + req_capacity * 4 + rounds * (
         max_msgs * ROUND_ENTRY_BYTES + ws + 256)

@@ -138,7 +138,7 @@ def test_mixed_all_shapes_and_invalid_codes(hb, oracle_mod):
         _assert_slots_equal(_gpu_slots(hb, b, None, shape=shape, mixed=True), want, "shape %d" % shape)
 
 
-@pytest.mark.parametrize("sub_log2,alg_major", [(0, 0), (2, 1), (3, 2), (4, 2), (5, 2), (5, 0)])
+@pytest.mark.parametrize("sub_log2,alg_major", [(0, 0), (2, 1), (3, 2), (4, 2), (5, 2), (6, 2), (6, 0)])
 def test_mixed_every_bucketing_matches_oracle(hb, oracle_mod, sub_log2, alg_major):
     # bucket resolution and chunk order (including MD5's longest octave served
     # early from its own queue) change the schedule, never a digest
@@ -158,7 +158,7 @@ def test_mixed_every_bucketing_matches_oracle(hb, oracle_mod, sub_log2, alg_majo
         _assert_slots_equal(out.cpu().numpy(), want, "replayed %d,%d" % (sub_log2, alg_major))
         plan.close()
     finally:
-        hb.tune_buckets(5, 2)
+        hb.tune_buckets(6, 2)
 
 
 def test_mixed_matches_single_algorithm_path(hb):
@@ -562,7 +562,7 @@ def test_full_size_ragged_graph_replay_matches_oracle(hb, c3, tmp_path):
     finally:
         plan.close()
         hb.tune_set(hb.TUNE_MIXED, 19)
-        hb.tune_buckets(5, 2)
+        hb.tune_buckets(6, 2)
         hb.tune_mixed_warps(8)
 
 
