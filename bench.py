@@ -464,6 +464,8 @@ def measure(args, dist):
     sms = props.multi_processor_count
 
     from paper_2407_09333_b300 import autotune
+    if args.relay_blocks is not None:
+        api.tune_relay(args.relay_blocks)
     tuned = {}
     mean_len = batch.total_bytes / max(n, 1)
     fused = not mixed and not args.separate
@@ -640,9 +642,11 @@ def measure(args, dist):
     dom_ops = per_alg[dom_name]["alu_Tops"] * 1e12 * t_dom
     hbm_bytes_per_launch = hbm_of[dom_name]
     peak_alu = alu_peak_tops(sms, peaks["sm_max_mhz"])
-    kernel_key = "%s:%s" % (args.workload, "items" if items else dom_name)
+    relay = dom_name == "all" and not items and api.all_uses_relay(n)
+    kernel_key = "%s:%s" % (args.workload, "items" if items else dom_name + ("_relay" if relay else ""))
     roofline = {
-        "bound": "alu", "kernel": "hb_%s_kernel<%s>" % ("mixed" if mixed or items else "plain",
+        "bound": "alu", "kernel": "hb_%s_kernel<%s>" % ("mixed" if mixed or items else
+                                                      "relay" if relay else "plain",
                                                       "3n items" if items else dom_name),
         "achieved": dom_ops / t_dom / 1e12, "peak": peak_alu, "unit": "Tops/s",
         "frac": dom_ops / t_dom / 1e12 / peak_alu,
@@ -1185,6 +1189,9 @@ def main(argv=None):
                    help="e2e copies back 32-byte slots instead of packed digests")
     p.add_argument("--shape", type=int, default=None,
                    help="fixed launch shape index instead of the autotuner's choice")
+    p.add_argument("--relay-blocks", type=int, default=None,
+                   help="segment blocks of the fused kernel's relay form for batches of few "
+                        "long messages (0 = grid-stride kernel only; default: the library's)")
     p.add_argument("--buckets", default="",
                    help="fixed ragged bucketing 'sub_log2,alg_major' (with --shape)")
     p.add_argument("--messages", type=int, default=0,

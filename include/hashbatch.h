@@ -118,6 +118,12 @@ int hash_batch(int alg, const uint8_t *packed_bytes, const uint64_t *offsets,
  * (16-byte aligned): record i holds message i's MD5, SHA-1 and SM3 slots, each
  * laid out as hash_batch writes it.  Same results as three hash_batch calls,
  * one read of the input instead of three.  Returns as hash_batch.
+ * A batch of between 2 and 8 x 32 messages per SM sub-partition (4 per SM)
+ * runs, outside stream capture, as a relay (hash_tune_relay): long messages
+ * are hashed in segments whose chains pass from warp to warp, so that every
+ * sub-partition gets the same share; between segments a message's chaining
+ * values are kept in its own record.  Such a call also uses 16 bytes of
+ * per-device scratch, ordered with other relay calls by an event.
  */
 int hash_batch_all(const uint8_t *packed_bytes, const uint64_t *offsets,
                    const uint32_t *lengths, uint64_t n, uint8_t *records_out, void *stream);
@@ -470,6 +476,24 @@ int hash_tune_occupancy(int alg, int shape_index);
  * sub_log2 = 6, alg_major = 2.
  */
 int hash_tune_buckets(int sub_log2, int alg_major);
+
+/*
+ * hash_tune_relay -- segment length, in 64-byte blocks, of hash_batch_all's
+ * relay form on the current device (0 = never relay; default 64).  Every
+ * message longer than one segment is hashed one segment per item; items are
+ * taken in order, segment by segment, by the warps of a persistent grid, and
+ * each waits (bounded by hash_set_wait_limit_ns, else HB_DEV_TIMEOUT) for
+ * its message's previous segment.  Digests do not depend on the choice.
+ * Returns HB_ERR_ARG outside [0, 2^20].
+ */
+int hash_tune_relay(int segment_blocks);
+
+/*
+ * hash_all_uses_relay -- 1 when hash_batch_all of n messages on the current
+ * device (default grid, outside stream capture) takes the relay form, else
+ * 0; or an HB_ERR_* code.
+ */
+int hash_all_uses_relay(uint64_t n);
 
 /*
  * hash_tune_mixed_warps -- resident warps per SM of the persistent ragged

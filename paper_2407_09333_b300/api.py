@@ -61,6 +61,8 @@ _SIGNATURES = {
     "hash_tune_occupancy": (_c_int, [_c_int, _c_int]),
     "hash_tune_buckets": (_c_int, [_c_int, _c_int]),
     "hash_tune_mixed_warps": (_c_int, [_c_int]),
+    "hash_tune_relay": (_c_int, [_c_int]),
+    "hash_all_uses_relay": (_c_int, [_c_u64]),
     "hash_batch_shape": (_c_int, [_c_int, _vp, _vp, _vp, _c_u64, _vp, _c_int, _c_int, _vp]),
     "hash_batch_mixed_shape": (_c_int, [_vp, _vp, _vp, _vp, _c_u64, _vp, _c_int, _c_int, _vp]),
     "hash_int_peak": (_c_int, [_c_int, _c_int, _c_int, _c_int, _vp, _vp, _vp]),
@@ -558,6 +560,19 @@ def tune_buckets(sub_log2: int, alg_major: int):
 
 def tune_mixed_warps(warps_per_sm: int):
     _check(lib().hash_tune_mixed_warps(int(warps_per_sm)), "hash_tune_mixed_warps")
+
+
+def tune_relay(segment_blocks: int):
+    """Segment length (64-byte blocks) of hash_batch_all's relay form for
+    batches of few long messages; 0 turns it off (hash_tune_relay)."""
+    _check(lib().hash_tune_relay(int(segment_blocks)), "hash_tune_relay")
+
+
+def all_uses_relay(n: int) -> bool:
+    """Whether hash_batch_all of n messages takes the relay form here."""
+    rc = int(lib().hash_all_uses_relay(int(n)))
+    _check(rc if rc < 0 else 0, "hash_all_uses_relay")
+    return rc == 1
 
 
 def tune_occupancy(alg: int, shape: int) -> int:

@@ -23,7 +23,7 @@ OBJ_DIR = os.path.join(PKG, "_build")
 # translation units so that they compile in parallel.
 SOURCES = ["hb_kernels.cu", "hb_capi.cu", "hb_noalloc.cu", "hb_stream.cu",
            "hb_inst_md5.cu", "hb_inst_sha1.cu", "hb_inst_sm3.cu", "hb_inst_all.cu",
-           "hb_inst_mixed.cu", "hb_inst_mixed_seg.cu"]
+           "hb_inst_mixed.cu", "hb_inst_mixed_seg.cu", "hb_inst_relay.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]

@@ -68,6 +68,13 @@ struct Ctx {
   DeviceBuf ws;                          // ragged-path scratch
   cudaEvent_t ws_event = nullptr;        // last use of `ws`
   bool ws_used = false;
+  // relay form of the fused kernel: item counter and longest length (16
+  // bytes, allocated with the context), its last use, segment blocks (0 = off)
+  uint32_t* relay = nullptr;
+  cudaEvent_t relay_event = nullptr;
+  bool relay_used = false;
+  int occ_relay[kMaxShapes] = {};
+  int relay_seg_blocks = (int)hb::kDefaultRelaySegBlocks;
   // host-buffer path
   DeviceBuf h_packed, h_off, h_len, h_algs, h_dig, h_flag, h_cmp;
   int* flag_host = nullptr;              // pinned: [0] bounds, [1] ends not monotone
@@ -104,7 +111,9 @@ int get_ctx(Ctx** out) {
     if (cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
         cudaMalloc(&c->status, sizeof(int)) != cudaSuccess ||
         cudaMemset(c->status, 0, sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&c->relay, 4 * sizeof(uint32_t)) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ws_event, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->relay_event, cudaEventDisableTiming) != cudaSuccess ||
         cudaHostAlloc(&c->flag_host, 2 * sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
       delete c;
       return cuda_fail(cudaGetLastError());
@@ -154,6 +163,47 @@ int launch_plain(Ctx* c, int alg, int shape, int grid, const KernelArgs& a, cuda
 int grid_for_elementwise(Ctx* c, uint64_t n) {
   const uint64_t need = (n + 255) / 256;
   return (int)std::max<uint64_t>(1, std::min<uint64_t>(need, (uint64_t)c->sms * 8));
+}
+
+// The relay form of the fused kernel (hb_pipeline.cuh, RelaySource) for a
+// batch of between half and eight times as many 32-message chunks as the GPU
+// has SM sub-partitions: too few for a grid-stride split to load them evenly.
+// Not inside a stream capture (the item counter is per-device scratch,
+// ordered between streams by an event).  Returns 1 when it launched, 0 when
+// the batch takes the grid-stride kernel, or an HB_ERR_* code.
+bool relay_window(const Ctx* c, uint64_t n) {
+  const uint64_t nchunks = (n + 31) / 32;
+  const uint64_t smsps = 4ull * (uint64_t)c->sms;
+  return c->relay_seg_blocks > 0 && nchunks * 2 >= smsps && nchunks <= 8 * smsps;
+}
+
+int launch_all_relay(Ctx* c, int shape, const KernelArgs& base, cudaStream_t s) {
+  if (shape < 0 || shape >= kMaxShapes || !relay_window(c, base.n)) return 0;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  if (cap != cudaStreamCaptureStatusNone) return 0;
+  int& occ = c->occ_relay[shape];
+  if (occ == 0) {
+    int b = 0;
+    cudaError_t e = hb::prepare_relay(shape, &b);
+    if (e != cudaSuccess) return cuda_fail(e);
+    occ = b > 0 ? b : 1;
+  }
+  if (c->relay_used && cudaStreamWaitEvent(s, c->relay_event, 0) != cudaSuccess)
+    return cuda_fail(cudaGetLastError());
+  KernelArgs a = base;
+  a.relay = c->relay;
+  a.relay_seg_blocks = (uint32_t)c->relay_seg_blocks;
+  cudaError_t e = hb::launch_relay_setup(base.lengths, base.n, a.relay_seg_blocks * 64u,
+                                         base.digests, c->relay, grid_for_elementwise(c, base.n), s);
+  if (e == cudaSuccess) e = hb::launch_relay(shape, c->sms * occ, a, s);
+  if (e == cudaSuccess) e = cudaEventRecord(c->relay_event, s);
+  if (e != cudaSuccess) return cuda_fail(e);
+  c->relay_used = true;
+  return 1;
 }
 
 // Ragged path on a given workspace (bucketing + persistent kernel).
@@ -309,7 +359,13 @@ int hash_batch_all_shape(const uint8_t* packed_bytes, const uint64_t* offsets,
   a.status = c->status;
   a.wait_limit_ns = g_wait_limit_ns;
   a.mc = hb::make_mul_consts();
-  return launch_plain(c, HB_ALL, shape_index, grid_blocks, a, static_cast<cudaStream_t>(stream));
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (grid_blocks <= 0) {
+    rc = launch_all_relay(c, shape_index, a, s);
+    if (rc < 0) return rc;
+    if (rc == 1) return HB_OK;
+  }
+  return launch_plain(c, HB_ALL, shape_index, grid_blocks, a, s);
 }
 
 int hash_batch_all(const uint8_t* packed_bytes, const uint64_t* offsets, const uint32_t* lengths,
@@ -782,7 +838,9 @@ int hash_release_device(void) {
   c->h_dig.release();
   c->h_flag.release();
   if (c->status) cudaFree(c->status);
+  if (c->relay) cudaFree(c->relay);
   if (c->ws_event) cudaEventDestroy(c->ws_event);
+  if (c->relay_event) cudaEventDestroy(c->relay_event);
   if (c->flag_host) cudaFreeHost(c->flag_host);
   if (c->host_hash) cudaStreamDestroy(c->host_hash);
   if (c->host_out) cudaStreamDestroy(c->host_out);
@@ -833,6 +891,22 @@ int hash_tune_get(int alg) {
   if (alg == HB_TUNE_MIXED) return c->tune_mixed;
   if (alg != HB_ALL && hash_digest_size(alg) == 0) return HB_ERR_INVALID_ALG;
   return c->tune_plain[alg];
+}
+
+int hash_all_uses_relay(uint64_t n) {
+  Ctx* c = nullptr;
+  int rc = get_ctx(&c);
+  if (rc) return rc;
+  return relay_window(c, n) ? 1 : 0;
+}
+
+int hash_tune_relay(int segment_blocks) {
+  if (segment_blocks < 0 || segment_blocks > (1 << 20)) return HB_ERR_ARG;
+  Ctx* c = nullptr;
+  int rc = get_ctx(&c);
+  if (rc) return rc;
+  c->relay_seg_blocks = segment_blocks;
+  return HB_OK;
 }
 
 int hash_tune_mixed_warps(int warps_per_sm) {

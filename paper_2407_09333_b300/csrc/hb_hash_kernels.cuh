@@ -28,6 +28,19 @@ __global__ void __launch_bounds__(WARPS * 32) hb_plain_kernel(KernelArgs a) {
   warp_pipeline<STAGES, KB, COOP, ALG, false, false>(src, wsm, a, lane);
 }
 
+// The fused kernel's relay form (few long messages): persistent; warps take
+// (segment, chunk) items and pass chains on between segments (RelaySource).
+template <int WARPS, int STAGES, int KB, bool COOP>
+__global__ void __launch_bounds__(WARPS * 32) hb_relay_kernel(KernelArgs a) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t warp = threadIdx.x >> 5;
+  if (a.abort_flag && *a.abort_flag) return;
+  uint8_t* wsm = smem + warp * WarpSmem<STAGES, KB, false, true>::kBytes;
+  RelaySource src(a, lane);
+  warp_pipeline<STAGES, KB, COOP, HB_ALL, false, false, true>(src, wsm, a, lane);
+}
+
 // SEG: messages arrive as segments (a.seg), see hb_pipeline.cuh.
 template <int WARPS, int STAGES, int KB, bool COOP, bool SEG>
 __global__ void __launch_bounds__(WARPS * 32) hb_mixed_kernel(KernelArgs a) {
@@ -91,6 +104,9 @@ KernelFn plain_fn(int shape) {
   }
 #undef HB_PLAIN_CASE
 }
+
+// The relay form of the fused kernel of launch shape `shape` (hb_inst_relay.cu).
+KernelFn relay_fn(int shape);
 
 // The persistent ragged kernel of launch shape `shape` (SEG: over segments).
 template <bool SEG>

@@ -508,6 +508,57 @@ bool shape_desc(int shape, int* warps, int* stages, int* kb, int* coop) {
 
 int shape_smem_bytes(int shape, bool seg) { return shape_smem(shape, seg); }
 
+static int shape_smem_relay(int shape) {
+#define HB_SMEM_RELAY_CASE(i, w, st, kb, co) \
+  case i: return w * WarpSmem<st, kb, false, true>::kBytes;
+  switch (shape) {
+    HB_SHAPES(HB_SMEM_RELAY_CASE)
+    default: return 0;
+  }
+#undef HB_SMEM_RELAY_CASE
+}
+
+cudaError_t prepare_relay(int shape, int* blocks_per_sm) {
+  KernelFn fn = relay_fn(shape);
+  if (!fn) return cudaErrorInvalidValue;
+  const int smem = shape_smem_relay(shape);
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, kShapes[shape].warps * 32,
+                                                       smem);
+}
+
+cudaError_t launch_relay(int shape, int grid, const KernelArgs& a, cudaStream_t stream) {
+  KernelFn fn = relay_fn(shape);
+  if (!fn || grid <= 0 || !a.relay) return cudaErrorInvalidValue;
+  fn<<<grid, kShapes[shape].warps * 32, shape_smem_relay(shape), stream>>>(a);
+  return cudaGetLastError();
+}
+
+// Before a relay: relay[2] = the longest length (relay[0..3] zeroed before),
+// and word 4 of every record whose message spans more than one segment
+// (the blocks-done count its later segments wait on) set to zero.
+__global__ void hb_relay_setup_kernel(const uint32_t* lengths, uint64_t n, uint32_t seg_bytes,
+                                      uint8_t* records, uint32_t* relay) {
+  uint32_t m = 0;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const uint32_t len = lengths[i];
+    m = max(m, len);
+    if (len > seg_bytes) *reinterpret_cast<uint32_t*>(records + i * HB_ALL_RECORD_BYTES + 16) = 0u;
+  }
+  m = __reduce_max_sync(0xFFFFFFFFu, m);
+  if ((threadIdx.x & 31u) == 0 && m) atomicMax(relay + 2, m);
+}
+
+cudaError_t launch_relay_setup(const uint32_t* lengths, uint64_t n, uint32_t seg_bytes,
+                               uint8_t* records, uint32_t* relay, int grid, cudaStream_t stream) {
+  cudaError_t e = cudaMemsetAsync(relay, 0, 4 * sizeof(uint32_t), stream);
+  if (e != cudaSuccess) return e;
+  hb_relay_setup_kernel<<<grid, 256, 0, stream>>>(lengths, n, seg_bytes, records, relay);
+  return cudaGetLastError();
+}
+
 static KernelFn pick(bool mixed, int alg, int shape, bool seg) {
   if (mixed) return seg ? mixed_fn<true>(shape) : mixed_fn<false>(shape);
   switch (alg) {

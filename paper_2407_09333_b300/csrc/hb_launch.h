@@ -53,6 +53,11 @@ struct KernelArgs {
   const uint64_t* seg;
   // Optional with segments: message i's slot is slot_index[i] instead of i.
   const uint32_t* slot_index;
+  // Relay (fused kernel, hb_pipeline.cuh): relay[0..1] is the 64-bit count of
+  // (segment, chunk) items taken, relay[2] the longest message length, both
+  // set before the launch; nullptr for the grid-stride kernels.
+  uint32_t* relay;
+  uint32_t relay_seg_blocks;  // blocks per segment (a multiple of the stage's blocks)
 };
 
 // Ragged-path bucketing: groups are (cost bucket, algorithm) pairs ordered
@@ -127,6 +132,15 @@ cudaError_t prepare_kernel(bool mixed, int alg, int shape, int* blocks_per_sm, b
 cudaError_t launch_hash(bool mixed, int alg, int shape, int grid, const KernelArgs& a,
                         cudaStream_t stream);
 cudaError_t launch_bucketing(const MixedArgs& m, int grid, cudaStream_t stream);
+// The fused kernel's relay form (a.relay set): shared-memory attribute and
+// occupancy, the launch, and the setup before it (item counter zeroed, the
+// longest length into relay[2], the blocks-done word of every record whose
+// message spans more than one segment zeroed).
+constexpr uint32_t kDefaultRelaySegBlocks = 64;
+cudaError_t prepare_relay(int shape, int* blocks_per_sm);
+cudaError_t launch_relay(int shape, int grid, const KernelArgs& a, cudaStream_t stream);
+cudaError_t launch_relay_setup(const uint32_t* lengths, uint64_t n, uint32_t seg_bytes,
+                               uint8_t* records, uint32_t* relay, int grid, cudaStream_t stream);
 cudaError_t launch_bounds(const uint64_t* offsets, const uint32_t* lengths, uint64_t n,
                           uint64_t packed_len, int* status_dev, int* ctx_status, int grid,
                           cudaStream_t stream);

@@ -56,14 +56,15 @@ constexpr int kItemBytes = 16;   // item record per lane per stage
 constexpr uint32_t kFull = 0xFFFFFFFFu;
 constexpr uint32_t kNoBlock = 0xFFFFFFFFu;
 
-template <int STAGES, int KB, bool SEG = false>
+template <int STAGES, int KB, bool SEG = false, bool RELAY = false>
 struct WarpSmem {
   static constexpr int kSlots = STAGES * 32 * Slot<KB>::kBytes;
   static constexpr int kItems = STAGES * 32 * kItemBytes;
   static constexpr int kTable = 32 * 16;  // per-lane copy descriptors (cooperative copies)
   // segments: a second item record (prior bytes, more flag) and a staged
-  // chaining value per lane per stage
-  static constexpr int kSegItems = SEG ? STAGES * 32 * kItemBytes : 0;
+  // chaining value per lane per stage (relay: the record only, the chaining
+  // value is read when the stage is consumed)
+  static constexpr int kSegItems = (SEG || RELAY) ? STAGES * 32 * kItemBytes : 0;
   static constexpr int kStates = SEG ? STAGES * 32 * HB_SLOT_BYTES : 0;
   static constexpr int kBytes = kSlots + kItems + kTable + kSegItems + kStates;  // multiple of 128
 };
@@ -343,6 +344,113 @@ struct DynamicSource {
   }
 };
 
+// Relay (fused kernel): few long messages.  Tasks of 32 consecutive messages
+// ("chunks") are cut into segments of seg_blocks blocks, and the warps of a
+// persistent grid take (segment, chunk) items from one counter, segment by
+// segment: item i is segment i / nchunks of chunk i % nchunks.  A chunk's
+// chains thus move from warp to warp between segments, so every SM
+// sub-partition ends up with the same share of the work even when the
+// chunks are fewer than four times the sub-partitions (a grid-stride split of
+// 2048 chunks over 592 sub-partitions leaves some with four and some with
+// three, and the step lasts as long as the fours).  A segment that is not its
+// message's last is pure message data (a whole number of blocks, no padding).
+// Between segments a message's chaining values wait in its own 96-byte
+// record (MD5's state in the first slot, SHA-1's in the second, SM3's in the
+// third), and word 4 of the record -- spare until the final digests
+// overwrite it with zeros -- counts the message's blocks done so far (zero
+// before the launch).  The next segment's lane waits for that count before
+// it reads the values.  Items are taken in order and each waits only on an
+// item taken before it, so the earliest unfinished item can always run.
+struct RelaySource {
+  const uint8_t* packed;
+  const uint64_t* offsets;
+  const uint32_t* lengths;
+  unsigned long long* counter;
+  uint64_t n, nitems;
+  uint32_t nchunks, seg_bytes, lane;
+
+  __device__ RelaySource(const KernelArgs& args, uint32_t lane_)
+      : packed(args.packed),
+        offsets(args.offsets),
+        lengths(args.lengths),
+        counter(reinterpret_cast<unsigned long long*>(args.relay)),
+        n(args.n),
+        nchunks((uint32_t)((args.n + 31) / 32)),
+        seg_bytes(args.relay_seg_blocks * 64u),
+        lane(lane_) {
+    // segments of the longest message: no chunk has more
+    const uint32_t longest = args.relay[2];
+    const uint64_t nseg = longest > seg_bytes ? ((uint64_t)longest + seg_bytes - 1) / seg_bytes : 1u;
+    nitems = nseg * nchunks;
+  }
+
+  __device__ __forceinline__ void hint(uint32_t) {}
+
+  __device__ __forceinline__ bool take(LaneTask& t) {
+    while (true) {
+      unsigned long long i = 0;
+      if (lane == 0) i = atomicAdd(counter, 1ull);
+      i = __shfl_sync(kFull, i, 0);
+      if (i >= nitems) return false;
+      const uint32_t chunk = (uint32_t)(i % nchunks);
+      const uint32_t segment = (uint32_t)(i / nchunks);
+      const uint64_t msg = (uint64_t)chunk * 32 + lane;
+      uint64_t off = 0;
+      uint32_t len = 0;
+      bool act = false;
+      if (msg < n) {
+        off = ldg_nc_u64(offsets + msg);
+        len = ldg_nc_u32(lengths + msg);
+        // segments of this message: ceil(len / seg_bytes), at least one
+        const uint32_t nseg =
+            len > seg_bytes ? (uint32_t)(((uint64_t)len + seg_bytes - 1) / seg_bytes) : 1u;
+        act = segment < nseg;
+      }
+      // an item no lane has part in (its messages are all shorter) is skipped
+      if (!__any_sync(kFull, act)) continue;
+      const uint64_t prior = (uint64_t)segment * seg_bytes;
+      const bool more = act && prior + seg_bytes < len;
+      t.msg = msg;
+      t.addr = reinterpret_cast<uint64_t>(packed) + off + prior;
+      t.len = act ? (more ? seg_bytes : len - (uint32_t)prior) : 0u;
+      t.nb = act ? (more ? seg_bytes >> 6 : padded_blocks(t.len)) : 0u;
+      t.alg = HB_ALL;
+      t.seg = prior | (more ? HB_SEG_MORE : 0ull);
+      t.slot = (uint32_t)msg;
+      return true;
+    }
+  }
+};
+
+// Relay: waits, warp-uniformly, until every lane with `need` sees its
+// message's block count (word 4 of its record) reach `blocks`; gives up
+// after limit_ns and records HB_DEV_TIMEOUT.  The counts are read with
+// acquire semantics, so the chaining values stored before them are visible.
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void relay_wait(const uint32_t* count, uint32_t blocks, bool need,
+                                           uint64_t limit_ns, int* status, uint32_t lane) {
+  bool ok = !need || ld_acquire_u32(count) >= blocks;
+  if (__all_sync(kFull, ok)) return;
+  const uint64_t t0 = global_timer_ns();
+  uint32_t ns = 32;
+  while (true) {
+    __nanosleep(ns);
+    if (ns < 1024) ns <<= 1;
+    if (!ok) ok = ld_acquire_u32(count) >= blocks;
+    if (__all_sync(kFull, ok)) return;
+    // one decision for the whole warp
+    if (__any_sync(kFull, global_timer_ns() - t0 > limit_ns)) {
+      if (lane == 0) atomicOr(status, HB_DEV_TIMEOUT);
+      return;
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Consuming side: one block of one message per lane.
 
@@ -391,18 +499,26 @@ struct SegCtx {
 
 // One block of a message for all three algorithms (HB_ALL): the staged
 // words feed MD5 as loaded and SHA-1 / SM3 byte-swapped; the final block
-// writes the message's 96-byte record.
+// writes the message's 96-byte record.  RELAY: the block belongs to a
+// segment starting `prior` bytes into its message; a segment followed by
+// more (`more`) has no padding and ends by storing the raw chaining values
+// in the record, then the message's blocks done in word 4 (release).
+template <bool RELAY = false>
 __device__ __forceinline__ void process_block_all(AllState& st, uint32_t slot, uint32_t s,
                                                   uint32_t len, uint32_t b, uint32_t nb,
                                                   uint64_t msg, uint8_t* records,
-                                                  const MulConsts& mc) {
-  if (b == (len >> 6)) sts8(slot + s + (len & 63u), 0x80u);
+                                                  const MulConsts& mc, bool more = false,
+                                                  uint64_t prior = 0) {
+  if (!(RELAY && more) && b == (len >> 6)) sts8(slot + s + (len & 63u), 0x80u);
   // One copy of the words is live at a time: MD5 takes them as loaded, then
   // they are byte-swapped in place for SHA-1 and SM3.
   uint32_t w[16];
   read_block_words<false>(slot, s, w);
-  const bool final_block = b + 1 == nb;
-  const uint32_t lo = len << 3, hi = len >> 29;  // bit length mod 2^64
+  const bool last = b + 1 == nb;
+  const bool final_block = last && !(RELAY && more);
+  // bit length of the whole message mod 2^64
+  const uint64_t bits = RELAY ? (prior + len) << 3 : (uint64_t)len << 3;
+  const uint32_t lo = (uint32_t)bits, hi = (uint32_t)(bits >> 32);
   if (final_block) {
     w[14] = lo;
     w[15] = hi;
@@ -440,6 +556,15 @@ __device__ __forceinline__ void process_block_all(AllState& st, uint32_t slot, u
     alg_digest_words<HB_SM3>(st.sm3, o);
     stg128_cs(dst + 64, o[0], o[1], o[2], o[3]);
     stg128_cs(dst + 80, o[4], o[5], o[6], o[7]);
+  } else if (RELAY && more && last) {
+    uint8_t* dst = records + msg * HB_ALL_RECORD_BYTES;
+    stg128_cs(dst, st.md5[0], st.md5[1], st.md5[2], st.md5[3]);
+    stg128_cs(dst + 32, st.sha1[0], st.sha1[1], st.sha1[2], st.sha1[3]);
+    stg128_cs(dst + 48, st.sha1[4], 0u, 0u, 0u);
+    stg128_cs(dst + 64, st.sm3[0], st.sm3[1], st.sm3[2], st.sm3[3]);
+    stg128_cs(dst + 80, st.sm3[4], st.sm3[5], st.sm3[6], st.sm3[7]);
+    const uint32_t done = (uint32_t)((prior + len) >> 6);
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(dst + 16), "r"(done) : "memory");
   }
 }
 
@@ -488,17 +613,30 @@ __device__ __forceinline__ void process_block(uint32_t (&st)[8], uint32_t slot, 
 // Consumes the KB blocks of one stage for one lane (blocks past the
 // message's padded length are skipped).  A message's chain starts in the
 // stage that holds its block 0: from the algorithm's initial value, or, for
-// a later segment, from the chaining value staged with it.
-template <int ALG, int KB, bool SEG = false>
+// a later segment, from the chaining value staged with it (SEG) or left in
+// the message's record by the warp that ran the previous segment (RELAY;
+// read through L2 after relay_wait).
+template <int ALG, int KB, bool SEG = false, bool RELAY = false>
 __device__ __forceinline__ void process_stage(typename StateFor<ALG>::type& st, uint32_t slot,
                                               uint32_t s, uint32_t len, uint32_t b0, uint64_t msg,
                                               const KernelArgs& a, const SegCtx& sc = SegCtx{}) {
-  const uint32_t nb = (SEG && sc.more) ? (len >> 6) : padded_blocks(len);
+  const uint32_t nb = ((SEG || RELAY) && sc.more) ? (len >> 6) : padded_blocks(len);
   if (b0 == 0) {
     if constexpr (ALG == HB_ALL) {
-      md5_init(st.md5);
-      sha1_init(st.sha1);
-      sm3_init(st.sm3);
+      if (RELAY && sc.prior != 0) {
+        const uint4* r = reinterpret_cast<const uint4*>(a.digests + msg * HB_ALL_RECORD_BYTES);
+        const uint4 m = __ldcg(r), h0 = __ldcg(r + 2), h1 = __ldcg(r + 3);
+        const uint4 s0 = __ldcg(r + 4), s1 = __ldcg(r + 5);
+        st.md5[0] = m.x; st.md5[1] = m.y; st.md5[2] = m.z; st.md5[3] = m.w;
+        st.sha1[0] = h0.x; st.sha1[1] = h0.y; st.sha1[2] = h0.z; st.sha1[3] = h0.w;
+        st.sha1[4] = h1.x;
+        st.sm3[0] = s0.x; st.sm3[1] = s0.y; st.sm3[2] = s0.z; st.sm3[3] = s0.w;
+        st.sm3[4] = s1.x; st.sm3[5] = s1.y; st.sm3[6] = s1.z; st.sm3[7] = s1.w;
+      } else {
+        md5_init(st.md5);
+        sha1_init(st.sha1);
+        sm3_init(st.sm3);
+      }
     } else if (SEG && sc.prior != 0) {
       const uint4 v0 = lds128(sc.state), v1 = lds128(sc.state + 16);
       st[0] = v0.x; st[1] = v0.y; st[2] = v0.z; st[3] = v0.w;
@@ -511,7 +649,8 @@ __device__ __forceinline__ void process_stage(typename StateFor<ALG>::type& st, 
 #pragma unroll 1
   for (uint32_t j = 0; j < nj; ++j) {
     if constexpr (ALG == HB_ALL)
-      process_block_all(st, slot + 64 * j, s, len, b0 + j, nb, msg, a.digests, a.mc);
+      process_block_all<RELAY>(st, slot + 64 * j, s, len, b0 + j, nb, msg, a.digests, a.mc,
+                               sc.more, sc.prior);
     else
       process_block<ALG, SEG>(st, slot + 64 * j, s, len, b0 + j, nb, msg, a.digests, a.mc, a, sc);
   }
@@ -524,16 +663,20 @@ __device__ __forceinline__ void process_stage(typename StateFor<ALG>::type& st, 
 // distinct pages per instruction when the messages lie far apart.  Lanes then
 // read windows that other lanes copied, so the warp synchronises after the
 // copy wait and before a stage is reused.
-template <int STAGES, int KB, bool COOP, int ALG, bool MIXED, bool SEG, class Source>
+// RELAY (with ALG == HB_ALL and a RelaySource): items are segments whose
+// chaining values come from other warps, see RelaySource.
+template <int STAGES, int KB, bool COOP, int ALG, bool MIXED, bool SEG, bool RELAY = false,
+          class Source>
 __device__ __forceinline__ void warp_pipeline(Source& src, uint8_t* wsm, const KernelArgs& a,
                                               uint32_t lane) {
-  using L = WarpSmem<STAGES, KB, SEG>;
+  static_assert(!RELAY || (ALG == HB_ALL && !MIXED && !SEG), "relay: fused kernel only");
+  using L = WarpSmem<STAGES, KB, SEG, RELAY>;
   constexpr int kSlotBytes = Slot<KB>::kBytes;
   constexpr int kGranules = 4 * KB + 1;
   const uint32_t slots = smem_addr(wsm);
   const uint32_t items = slots + L::kSlots;
   const uint32_t table = items + L::kItems;
-  const uint32_t seg_items = table + L::kTable;      // SEG only
+  const uint32_t seg_items = table + L::kTable;      // SEG or RELAY
   const uint32_t states = seg_items + L::kSegItems;  // SEG only
   const uint64_t safe_src = reinterpret_cast<uint64_t>(a.packed) & ~15ull;
 
@@ -557,11 +700,13 @@ __device__ __forceinline__ void warp_pipeline(Source& src, uint8_t* wsm, const K
     rec.z = t.len;
     rec.w = act ? ib : kNoBlock;
     sts128(items + (is * 32 + lane) * kItemBytes, rec);
-    if constexpr (SEG) {
+    if constexpr (SEG || RELAY) {
       sts128(seg_items + (is * 32 + lane) * kItemBytes,
              make_uint4((uint32_t)t.seg, (uint32_t)(t.seg >> 32), t.slot, 0u));
       // a continued message's first item also stages its chaining value
-      if (act && ib == 0 && (t.seg & ~HB_SEG_MORE) != 0) {
+      // (SEG: written by an earlier launch; a relay's comes from a warp of
+      // this launch and is read when the stage is consumed)
+      if (SEG && act && ib == 0 && (t.seg & ~HB_SEG_MORE) != 0) {
         const uint8_t* cv = a.digests + (uint64_t)t.slot * HB_SLOT_BYTES;
         const uint32_t dst = states + (is * 32 + lane) * HB_SLOT_BYTES;
         cp_async16_zfill(dst, cv, 16u);
@@ -670,6 +815,23 @@ __device__ __forceinline__ void warp_pipeline(Source& src, uint8_t* wsm, const K
     cp_async_wait<STAGES - 1>();  // this lane's copies of item `cs` have landed
     if constexpr (COOP) __syncwarp();  // ... and every other lane's
     const uint4 rec = lds128(items + (cs * 32 + lane) * kItemBytes);
+    uint64_t r_prior = 0;
+    bool r_more = false;
+    if constexpr (RELAY) {
+      // a continued segment's first stage: wait for the previous segment's
+      // chaining values (every lane of the warp takes part)
+      const uint4 r2 = lds128(seg_items + (cs * 32 + lane) * kItemBytes);
+      const uint64_t sg = (uint64_t)r2.x | ((uint64_t)r2.y << 32);
+      r_prior = sg & ~HB_SEG_MORE;
+      r_more = (sg & HB_SEG_MORE) != 0;
+      const bool need = rec.w == 0 && r_prior != 0;
+      if (__any_sync(kFull, need)) {
+        const uint64_t m = (uint64_t)rec.x | ((uint64_t)(rec.y & 0x00FFFFFFu) << 32);
+        const uint32_t* count =
+            reinterpret_cast<const uint32_t*>(a.digests + m * HB_ALL_RECORD_BYTES + 16);
+        relay_wait(count, (uint32_t)(r_prior >> 6), need, a.wait_limit_ns, a.status, lane);
+      }
+    }
     if (rec.w != kNoBlock) {
       const uint64_t msg = (uint64_t)rec.x | ((uint64_t)(rec.y & 0x00FFFFFFu) << 32);
       const uint32_t s = (rec.y >> 24) & 15u;
@@ -691,6 +853,11 @@ __device__ __forceinline__ void warp_pipeline(Source& src, uint8_t* wsm, const K
           process_stage<HB_SHA1, KB, SEG>(st, slot, s, rec.z, rec.w, msg, a, sc);
         else
           process_stage<HB_SM3, KB, SEG>(st, slot, s, rec.z, rec.w, msg, a, sc);
+      } else if constexpr (RELAY) {
+        SegCtx sc{};
+        sc.prior = r_prior;
+        sc.more = r_more;
+        process_stage<ALG, KB, false, true>(st, slot, s, rec.z, rec.w, msg, a, sc);
       } else {
         process_stage<ALG, KB>(st, slot, s, rec.z, rec.w, msg, a);
       }
