@@ -81,6 +81,21 @@ class CostModel:
         w = work_by_alg(lengths, alg=alg)
         return float(self.rate[alg] * w[alg] + self.per_msg[alg] * lengths.shape[0])
 
+    def request_costs(self, lengths, alg: int) -> tuple[float, float]:
+        """(work_seconds, chain_time) of one algorithm's messages in a single
+        pass over their lengths: what a server computes for every arriving
+        request, so it is kept to one array operation and two reductions."""
+        lengths = np.asarray(lengths)
+        n = lengths.shape[0]
+        if n == 0:
+            return 0.0, 0.0
+        nb = shard.padded_blocks(lengths)
+        ops = int(shard.OPS_PER_BLOCK[alg])
+        work = float(self.rate[alg]) * float(nb.sum()) * ops + float(self.per_msg[alg]) * n
+        if self.chain is None or self.chain[alg] <= 0:
+            return work, 0.0
+        return work, float(nb.max()) * ops / float(self.chain[alg])
+
     def chain_time(self, lengths, alg: int) -> float:
         """Time of the longest message's serial chain among `lengths` (one
         algorithm): the least time the set can take however many SMs are free

@@ -196,8 +196,8 @@ class Admission:
     def estimate(self, req):
         """(work seconds at the served rate, chain seconds) of a request,
         also stored on it."""
-        req.work_s = self.model.work_seconds(req.lengths, req.alg) / self.drain
-        req.chain_s = self.model.chain_time(req.lengths, req.alg)
+        work, req.chain_s = self.model.request_costs(req.lengths, req.alg)
+        req.work_s = work / self.drain
         return req.work_s, req.chain_s
 
     def backlog(self, now: float) -> float:

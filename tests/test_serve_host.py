@@ -114,6 +114,9 @@ class _Model:
     def chain_time(self, lengths, alg):
         return float(np.asarray(lengths, dtype=np.float64).max(initial=0) * self.CHAIN[alg])
 
+    def request_costs(self, lengths, alg):
+        return self.work_seconds(lengths, alg), self.chain_time(lengths, alg)
+
 
 def _requests(n, rate_per_s, seed):
     rng = np.random.default_rng(seed)
@@ -271,3 +274,21 @@ def test_admission_without_chain_calibration_uses_work_alone():
     assert m2.chain[2] == pytest.approx(2e7, rel=1e-6) and m2.chain[0] == pytest.approx(5e7, rel=1e-6)
     assert m2.chain[1] == 0 and m2.latency_t0 == pytest.approx(1e-3, rel=1e-6)
     assert m2.chain_time([100, 16384], 2) == pytest.approx(257 * 1412 / 2e7)
+
+
+def test_request_costs_equal_work_seconds_and_chain_time():
+    # the one-pass per-request estimate the admission policy uses equals the
+    # model's general work and chain functions
+    from paper_2407_09333_b300 import costmodel
+    rng = np.random.Generator(np.random.PCG64(5))
+    m = costmodel.CostModel(rate=np.array([7e-14, 5e-14, 4e-14]), overhead=3e-5, r2=1.0,
+                            per_msg=np.array([2e-11, 0.0, 1e-11]),
+                            chain=np.array([2.5e8, 3.1e8, 3.6e8]))
+    for alg in (0, 1, 2):
+        for n in (0, 1, 7, 4096):
+            lens = rng.integers(0, 1 << 20, size=n).astype(np.uint32)
+            work, chain = m.request_costs(lens, alg)
+            assert work == pytest.approx(m.work_seconds(lens, alg), rel=1e-12, abs=0.0)
+            assert chain == pytest.approx(m.chain_time(lens, alg), rel=1e-12, abs=0.0)
+    nochain = costmodel.CostModel(rate=m.rate, overhead=m.overhead, r2=1.0, per_msg=m.per_msg)
+    assert nochain.request_costs(np.array([100], np.uint32), 2)[1] == 0.0
