@@ -130,3 +130,30 @@ def test_relay_argument_checks(hb):
     with pytest.raises(HashBatchError):
         hb.tune_relay((1 << 20) + 1)
     hb.tune_relay(64)
+
+
+def test_relay_wait_limit_reports_a_timeout(hb):
+    # The relay's wait for a previous segment is bounded.  With a 1 ns limit
+    # and more warps than chunks (the smallest relay batch, one-block
+    # segments) some warp is bound to find its count not yet reached: the
+    # wait gives up, the launch still ends, and the device status carries
+    # HB_DEV_TIMEOUT (the digests are then not to be trusted).  Nothing here
+    # faults: every address the kernel touches stays valid.
+    lo, _ = _relay_window(hb)
+    b = workloads.fixed(lo, 8192, seed=17)
+    packed, off, ln, _ = hb.to_device(b)
+    rec = torch.empty((b.n, 96), dtype=torch.uint8, device="cuda")
+    assert hb.device_status() == 0
+    hb.tune_relay(1)
+    old = hb.set_wait_limit_ns(1)
+    try:
+        hb.hash_batch_all(packed, off, ln, out=rec)
+        torch.cuda.synchronize()
+    finally:
+        hb.set_wait_limit_ns(old)
+        hb.tune_relay(64)
+    assert hb.device_status() & hb.DEV_TIMEOUT          # read and cleared
+    assert hb.device_status() == 0
+    hb.hash_batch_all(packed, off, ln, out=rec)         # and the next call is clean
+    torch.cuda.synchronize()
+    assert hb.device_status() == 0
