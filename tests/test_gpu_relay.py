@@ -157,3 +157,24 @@ def test_relay_wait_limit_reports_a_timeout(hb):
     hb.hash_batch_all(packed, off, ln, out=rec)         # and the next call is clean
     torch.cuda.synchronize()
     assert hb.device_status() == 0
+
+
+@pytest.mark.parametrize("shape", [6, 11])
+def test_relay_with_four_block_stages(hb, oracle_mod, shape):
+    # the benchmark's relay shape (8 warps, 2 stages of 4 blocks, per-lane
+    # copies) and its cooperative-copy twin, with 3-block segments: every
+    # segment ends part-way through a stage
+    lo, _ = _relay_window(hb)
+    n = lo + 13
+    b = workloads.scattered(_lengths(3 * 64, n, seed=500 + shape), seed=21, overlap=True)
+    packed, off, ln, _ = hb.to_device(b)
+    want = _oracle_records(oracle_mod, b)
+    hb.tune_relay(3)
+    try:
+        rec = torch.full((b.n, 96), 0x3C, dtype=torch.uint8, device="cuda")
+        names = _kernel_names(lambda: hb.hash_batch_all(packed, off, ln, out=rec, shape=shape))
+        assert any("hb_relay_kernel" in k for k in names), sorted(names)
+        assert hb.device_status() == 0
+        _assert_records(rec.cpu().numpy(), want, "relay shape %d" % shape)
+    finally:
+        hb.tune_relay(64)
