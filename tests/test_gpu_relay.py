@@ -178,3 +178,25 @@ def test_relay_with_four_block_stages(hb, oracle_mod, shape):
         _assert_records(rec.cpu().numpy(), want, "relay shape %d" % shape)
     finally:
         hb.tune_relay(64)
+
+
+def test_relay_calls_on_two_streams_share_the_counter_in_order(hb, oracle_mod):
+    # two relay batches issued back to back on two streams without a host
+    # synchronisation: the per-device item counter is reset by each call's
+    # setup, so the second call must wait for the first (the library orders
+    # them with an event), and both must come out right
+    lo, _ = _relay_window(hb)
+    batches = [workloads.scattered(_lengths(64 * 64, lo + 5 + 7 * k, seed=600 + k), seed=30 + k,
+                                   overlap=True) for k in range(2)]
+    dev = [hb.to_device(b) for b in batches]
+    want = [_oracle_records(oracle_mod, b) for b in batches]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    recs = [torch.empty((b.n, 96), dtype=torch.uint8, device="cuda") for b in batches]
+    torch.cuda.synchronize()
+    for (packed, off, ln, _), rec, st in zip(dev, recs, streams):
+        with torch.cuda.stream(st):
+            hb.hash_batch_all(packed, off, ln, out=rec, stream=st)
+    torch.cuda.synchronize()
+    assert hb.device_status() == 0
+    for k, (rec, w) in enumerate(zip(recs, want)):
+        _assert_records(rec.cpu().numpy(), w, "stream %d" % k)
